@@ -1,0 +1,198 @@
+"""Oracle for the GFK helium walk: plain FP64 C on the CPU, loaded with ctypes.
+
+TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The oracle shares no code with the CUDA
+library (``paper_1703_08977_gb300``) and imports nothing from it.
+
+The C source (``gfk_oracle.c``) cites the paper passage each part follows.  This
+module only compiles it (gcc, ``-ffp-contract=off``) and marshals arrays.
+
+Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
+  philox4x32_10     pinned: an independent implementation (triton's Philox,
+                    run by its CPU interpreter) agrees bitwise.
+  normals6          pinned: Kolmogorov-Smirnov and moment tests against N(0,1).
+  trial_eval        pinned: closed-form eigenfunctions (E_L constant), 50-digit
+                    finite differences of ln|psi|, exchange (anti)symmetry.
+  run               pinned: exact weights for an exact eigenfunction, a
+                    hand-computed single step, the variational closed form
+                    <E_L> = Z^2 - 27 Z / 8 at stationarity, node invariants,
+                    the growth identity d ln z / dt = -(E - E_T) + O(dt).
+  neumaier_sum      pinned: math.fsum (exactly rounded) on cancelling inputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gfk_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KIND_JASTROW_PRODUCT = 0
+KIND_ORBITAL_PAIRS = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (plain gcc, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        c = ctypes
+        dp = c.POINTER(c.c_double)
+        lib.orc_philox4x32_10.argtypes = [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
+                                          c.POINTER(c.c_uint32)]
+        lib.orc_philox4x32_10.restype = None
+        lib.orc_uniform.argtypes = [c.c_uint32]
+        lib.orc_uniform.restype = c.c_double
+        lib.orc_normals6.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32,
+                                     c.c_uint32, dp]
+        lib.orc_normals6.restype = None
+        lib.orc_trial_eval.argtypes = [c.c_int, dp, c.c_int, c.c_int, dp,
+                                       c.POINTER(c.c_int), dp, dp, dp]
+        lib.orc_trial_eval.restype = c.c_int
+        lib.orc_neumaier_sum.argtypes = [dp, c.c_int64]
+        lib.orc_neumaier_sum.restype = c.c_double
+        lib.orc_run.argtypes = [c.c_int, dp, c.c_int, c.c_int,
+                                c.c_double, c.c_double, c.c_uint64, c.c_uint32, c.c_double,
+                                c.c_int64, c.POINTER(c.c_uint32),
+                                dp, dp, dp, c.POINTER(c.c_uint8), c.POINTER(c.c_int8),
+                                c.c_uint32, c.c_int64, c.c_int,
+                                dp, c.POINTER(c.c_int64)]
+        lib.orc_run.restype = c.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block: 4 counter words, 2 key words -> 4 output words."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                          _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def uniform(word: int) -> float:
+    return _load().orc_uniform(int(word))
+
+
+def normals6(seed: int, walker: int, step: int, inst: int, tag0: int = 0) -> np.ndarray:
+    """The six normals of (walker, step, inst) from Philox tags tag0, tag0+1."""
+    out = np.zeros(6)
+    _load().orc_normals6(int(seed), int(walker), int(step), int(inst), int(tag0),
+                         _ptr(out, ctypes.c_double))
+    return out
+
+
+def trial_eval(kind: int, params, x, ee_on: bool = True):
+    """(sign, drift b (6,), E_L, ln|psi|) of the trial function at X (6,)."""
+    lib = _load()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    assert xv.shape == (6,)
+    s = ctypes.c_int(0)
+    b = np.zeros(6)
+    el = ctypes.c_double(0.0)
+    lp = ctypes.c_double(0.0)
+    rc = lib.orc_trial_eval(int(kind), _ptr(p, ctypes.c_double), len(p), int(bool(ee_on)),
+                            _ptr(xv, ctypes.c_double), ctypes.byref(s),
+                            _ptr(b, ctypes.c_double), ctypes.byref(el), ctypes.byref(lp))
+    if rc != 0:
+        raise ValueError("oracle: malformed trial parameter vector")
+    return s.value, b, el.value, lp.value
+
+
+def neumaier_sum(v) -> float:
+    a = np.ascontiguousarray(v, dtype=np.float64)
+    return _load().orc_neumaier_sum(_ptr(a, ctypes.c_double), len(a))
+
+
+class Walk:
+    """Oracle walker population for one instance.
+
+    Holds (X, logw, E_L, alive, sign) for the walker ids given (default 0..n-1)
+    and advances them with the global step counter, so a subset of walker ids
+    replays exactly the trajectories those ids have in a full population.
+    """
+
+    def __init__(self, kind, params, *, n_walkers=None, ids=None, dt, e_trial, seed,
+                 inst=0, sigma=0.5, ee_on=True):
+        if ids is None:
+            ids = np.arange(int(n_walkers), dtype=np.uint32)
+        self.ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        n = len(self.ids)
+        self.kind = int(kind)
+        self.params = np.ascontiguousarray(params, dtype=np.float64)
+        self.dt, self.e_trial, self.seed = float(dt), float(e_trial), int(seed)
+        self.inst, self.sigma, self.ee_on = int(inst), float(sigma), bool(ee_on)
+        self.x = np.zeros((n, 6))
+        self.logw = np.zeros(n)
+        self.el = np.zeros(n)
+        self.alive = np.zeros(n, dtype=np.uint8)
+        self.sgn = np.zeros(n, dtype=np.int8)
+        self.step = 0
+        self.counters = np.zeros(3, dtype=np.int64)
+        self.rows = []          # per-step population sums {c, W, P, Q, R, n_alive}
+        self._call(0, do_init=True)
+
+    def _call(self, n_steps, do_init=False):
+        lib = _load()
+        n = len(self.ids)
+        nrows = n_steps + (1 if do_init else 0)
+        stats = np.zeros((max(nrows, 1), 6))
+        rc = lib.orc_run(self.kind, _ptr(self.params, ctypes.c_double), len(self.params),
+                         int(self.ee_on), self.dt, self.e_trial, self.seed, self.inst,
+                         self.sigma, n, _ptr(self.ids, ctypes.c_uint32),
+                         _ptr(self.x, ctypes.c_double), _ptr(self.logw, ctypes.c_double),
+                         _ptr(self.el, ctypes.c_double), _ptr(self.alive, ctypes.c_uint8),
+                         _ptr(self.sgn, ctypes.c_int8), self.step, int(n_steps), int(do_init),
+                         _ptr(stats, ctypes.c_double), _ptr(self.counters, ctypes.c_int64))
+        if rc != 0:
+            raise ValueError("oracle: bad walk parameters")
+        self.rows.extend(stats[:nrows])
+        self.step += int(n_steps)
+
+    def advance(self, n_steps: int):
+        self._call(int(n_steps))
+        return self
+
+    # --- space-averaged estimators from the per-step sums -------------------
+    def series(self):
+        """dict of per-step arrays: E (=P/W), ln_z (=ln(W e^c / N0)), ess (=W^2/Q),
+        var (=R/W - E^2), n_alive; index k = after k steps."""
+        r = np.array(self.rows)
+        c, W, P, Q, R, na = r.T
+        n0 = len(self.ids)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            E = P / W
+            return {"E": E, "ln_z": c + np.log(W) - np.log(n0), "ess": W * W / Q,
+                    "var": R / W - E * E, "n_alive": na, "W": W, "P": P, "Q": Q,
+                    "R": R, "c": c}
