@@ -1,0 +1,341 @@
+"""Benchmark: walker-steps per second of the GFK helium walk on one GB300.
+
+One bench step = one full run of the headline workload through the C ABI:
+initialise 2^20 walkers of the He 1^1S trial function
+exp(-2 r1 - 2 r2) exp(r12 / (2 (1 + 0.5 r12))) and advance them 20000 moves at
+dt = 0.005 on the mixed-precision path (FP32 drift / local energy / normals,
+FP64 log-weights and population sums), with the population sums of every move.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own
+population (its own Philox stream) -- weak scaling, no collective on the data
+path; the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-steps/sec on 1 GB300 (FP32-mixed vs FP64) at stated energy error vs FP64 oracle"
+UNIT = "walker-steps/s"
+N_WALKERS = 1 << 20
+N_MOVES = 20000
+DT = 0.005
+E_T = -2.9037
+SEED = 0
+TRIAL = (0, [2.0, 0.5, 0.5])           # GFK_TRIAL_JASTROW_PRODUCT: Z, a, beta
+WORKLOAD = ("He 1^1S ground state: 2^20 walkers x 20000 moves, dt=0.005, "
+            "trial exp(-2r1-2r2)exp(r12/(2(1+0.5r12))), E_T=-2.9037, Philox seed 0, "
+            "mixed FP32 physics / FP64 weights")
+
+# Algorithmic ALU work of one walker-step of the mixed path for the kind-0 trial
+# (counted from the method, FMA = 1 op): Philox4x32-10
+# x2 (200 integer ops), Box-Muller x3 (51), move (12), trial evaluation (77),
+# log-weight and weighted sums (12).
+OPS_PER_WALKER_STEP = 352
+# Lanes that can issue an ALU instruction per SM per clock (4 schedulers x 32).
+LANES_PER_SM_CLK = 128
+# DRAM traffic of the walk kernel per launch from an ncu capture, valid only for
+# the kernel sources it was taken on (sha256 prefix of csrc/*); None otherwise.
+WALK_TRAFFIC = {"src_sha": None, "bytes_per_walker_step": None}
+
+
+def _src_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1703_08977_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    """The oracle (plain FP64 C, one host thread) on a bounded sample of the workload."""
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    oracle.build()
+    n_sample, moves = 4096, 100
+    kind, params = TRIAL
+
+    def one():
+        w = oracle.Walk(kind, params, n_walkers=n_sample, dt=DT, e_trial=E_T, seed=SEED)
+        w.advance(moves)
+        return w
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt_s = time.perf_counter() - t0
+    value = n_sample * moves * args.steps / dt_s
+    sample = f"{n_sample} walkers x {moves} moves per step (a slice of the 2^20 x 20000 workload)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline():
+    import oracle
+    oracle.build()
+    n_sample, moves = 1 << 14, 600
+    kind, params = TRIAL
+    t0 = time.perf_counter()
+    w = oracle.Walk(kind, params, n_walkers=n_sample, dt=DT, e_trial=E_T, seed=SEED)
+    w.advance(moves)
+    el = time.perf_counter() - t0
+    return {"value": n_sample * moves / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"2^14 walkers x {moves} moves of the same workload, one host thread "
+                      f"({os.cpu_count()} cores on the host)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    from paper_1703_08977_gb300 import gfk
+
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    kind, params = TRIAL
+
+    def make_ctx(prec, n_walkers=N_WALKERS, launch=None):
+        d = gfk.InstanceDesc(n_walkers=n_walkers, dt=DT, e_trial=E_T, seed=SEED,
+                             prec=prec, rng_stream=rank)
+        return gfk.Context([d], trials=[(kind, params)], launch=launch)
+
+    launch = (args.threads, args.wpt)
+    ctx = make_ctx(gfk.GFK_PREC_MIXED, launch=launch)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
+    stream = torch.cuda.current_stream()
+
+    def device_step():
+        ctx.reset()
+        ctx.propagate(N_MOVES)
+
+    for _ in range(args.warmup):
+        device_step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K device-resident steps, L2 flushed between them ----
+    gfk.gfk_profile(ctx.handle, True)
+    gfk.gfk_profile_read(ctx.handle, reset=True)
+    clocks = Clocks(dev)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        device_step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    walk_ms, walk_launches, walk_ws = gfk.gfk_profile_read(ctx.handle, reset=True)
+    gfk.gfk_profile(ctx.handle, False)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    walker_steps_per_step = N_WALKERS * N_MOVES
+    value = walker_steps_per_step * ws * args.steps / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    cap = N_MOVES + 1
+    e_host = np.empty(cap)
+    lz_host = np.empty(cap)
+    ess_host = np.empty(cap)
+    h2d = 8 * len(params) + 1024          # trial parameters + the instance table upload
+    d2h = 3 * 8 * cap + 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        gfk.gfk_reset(ctx.handle)
+        gfk.gfk_set_trial(ctx.handle, 0, kind, params)
+        gfk.gfk_propagate(ctx.handle, N_MOVES)
+        gfk.gfk_energy(ctx.handle, 0, cap=cap, out=(e_host, lz_host, ess_host))
+    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    e_mixed = e_host.copy()
+    ctx.close()
+
+    out = None
+    if rank == 0:
+        # ---- the FP64 path on the same seeds, and the mixed path's energy error ----
+        n_cmp = args.fp64_moves
+        c64 = make_ctx(gfk.GFK_PREC_FP64)
+        c64.propagate(16)
+        torch.cuda.synchronize()
+        c64.reset()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c64.propagate(n_cmp)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = a.elapsed_time(b)
+        fp64_value = N_WALKERS * n_cmp / (fp64_ms / 1e3)
+        e64 = c64.energy(0)["E"]
+        c64.close()
+        diff = e_mixed[: n_cmp + 1] - e64
+        tail = diff[len(diff) // 2:]
+        avg_launch_ms = walk_ms / max(1, walk_launches)
+        ws_per_launch = walk_ws / max(1, walk_launches)
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak = n_sm * LANES_PER_SM_CLK * sm_max * 1e6 / 1e9      # Gop/s
+        achieved = OPS_PER_WALKER_STEP * ws_per_launch / (avg_launch_ms / 1e3) / 1e9
+        traffic = None
+        if WALK_TRAFFIC["src_sha"] == _src_sha() and WALK_TRAFFIC["bytes_per_walker_step"]:
+            traffic = WALK_TRAFFIC["bytes_per_walker_step"] * ws_per_launch
+        launches_per_step = 2 * walk_launches / args.steps + 2
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "walkers_per_gpu": N_WALKERS, "moves": N_MOVES,
+                       "dt": DT, "launch": {"threads": launch[0], "walkers_per_thread": launch[1]},
+                       "l2": "flushed (256 MB write) before every timed step; state 32 MB"},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "e2e": {"value": walker_steps_per_step * ws / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "walk_mixed_kernel",
+                         "peak_basis": f"{n_sm} SMs x {LANES_PER_SM_CLK} lanes x {sm_max:.0f} MHz "
+                                       "(issue limit; derived, no measured ALU peak)",
+                         "ops_per_walker_step": OPS_PER_WALKER_STEP,
+                         "avg_launch_ms": avg_launch_ms},
+            "fp64_path": {"value": fp64_value, "unit": UNIT, "moves": n_cmp,
+                          "mixed_over_fp64": value / ws / fp64_value},
+            "energy_error_vs_fp64": {
+                "moves": n_cmp, "max_abs_E_t": float(np.max(np.abs(diff))),
+                "mean_E_t_second_half": float(np.mean(tail)),
+                "final": float(diff[-1]),
+                "note": "mixed minus FP64 path, same seeds and walkers; the FP64 path "
+                        "matches the FP64 oracle to 1e-13 (tests)"},
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--wpt", type=int, default=2)
+    ap.add_argument("--fp64-moves", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * gfk.h -- C ABI of the GB300 generalized Feynman-Kac (GFK) walker library.
+ *
+ * The library advances large populations of independent 6-D two-electron
+ * walkers for helium by the importance-sampled diffusion of the GFK method
+ * (Datta, Rejcek, Fry, "The He atom revisited", arXiv:1703.08977) and forms
+ * the space-averaged energy after every step.  All arithmetic runs in CUDA
+ * kernels for sm_103a; the calls below only validate, allocate and launch.
+ *
+ * Conventions shared by every call:
+ *   - A walker's position is X = (x1, y1, z1, x2, y2, z2) in bohr.
+ *   - Pointers named host_* or documented "host" are ordinary CPU memory; no
+ *     call takes a device pointer unless it says so.
+ *   - Every call returns a gfk_status; none aborts, traps or exits.  A CUDA
+ *     failure returns GFK_ECUDA and gfk_last_error() gives CUDA's message.
+ *   - A context is used from one host thread at a time.
+ *   - Work is queued on the CUDA stream given to gfk_create (NULL = the
+ *     legacy default stream).  Calls that return data to the host synchronise
+ *     that stream; gfk_propagate does not.
+ */
+#ifndef GFK_H
+#define GFK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfk_ctx gfk_ctx;   /* opaque; owned by the library */
+
+typedef enum {
+    GFK_OK = 0,
+    GFK_EINVAL = 1,       /* an argument is out of range or malformed            */
+    GFK_ENOMEM = 2,       /* a device or host allocation failed                  */
+    GFK_ECUDA = 3,        /* a CUDA call failed; see gfk_last_error()            */
+    GFK_ESTATE = 4,       /* the call is not valid in the context's state        */
+    GFK_ENONFINITE = 5,   /* outputs were written, but some walkers were killed
+                             because their drift or local energy was not finite */
+    GFK_EOVERFLOW = 6,    /* a caller buffer is too small                        */
+    GFK_ETIMEOUT = 7      /* reserved: no call waits on a device-side flag       */
+} gfk_status;
+
+/* Symmetry of the state sought (the paper's three cases: the nodeless ground
+ * state, the 2^3S state whose node r1 = r2 is exact, and a P_z state handled
+ * by its necessary nodal condition).  Every state uses the same fixed-node
+ * rule: a walker whose trial function changes sign, or becomes exactly zero,
+ * is killed (its weight is zero from then on). */
+typedef enum { GFK_1S = 0, GFK_2S3 = 1, GFK_PZ = 2 } gfk_state;
+
+/* Arithmetic of the walk.
+ * GFK_PREC_FP64:  every operation in FP64.
+ * GFK_PREC_MIXED: positions, drift, local energy and random normals in FP32;
+ *                 each walker's log-weight is an FP64 base plus an FP32
+ *                 Kahan-compensated sum of increments folded into the base
+ *                 every 16 steps; population sums go FP32 within a warp,
+ *                 FP64 above it, compensated (TwoSum) across blocks. */
+typedef enum { GFK_PREC_FP64 = 0, GFK_PREC_MIXED = 1 } gfk_prec;
+
+/* Trial-function families, psi = Phi(r1_vec, r2_vec) * exp(u(r12)) with the
+ * Jastrow factor u(r) = a rho + sum_{k=1..4} c_k rho^(k+1), rho = r/(1+beta r).
+ *
+ * GFK_TRIAL_JASTROW_PRODUCT: Phi = exp(-Z r1 - Z r2).
+ *   params = [Z, a, beta, c1, c2, c3, c4]   (3 to 7 values; missing c_k = 0)
+ *   The benchmark ground-state function exp(-2 r1 - 2 r2) exp(r12/(2(1+0.5 r12)))
+ *   is [2, 0.5, 0.5].
+ * GFK_TRIAL_ORBITAL_PAIRS: Phi = sum_t s_t f_{A,t}(r1_vec) f_{B,t}(r2_vec) with
+ *   orbitals f(r_vec) = (c0 + c1 r + cz z) exp(-alpha r).
+ *   params = [a, beta, c1, c2, c3, c4, nterms,
+ *             then for each term: s, alphaA, c0A, c1A, czA, alphaB, c0B, c1B, czB]
+ *   (7 + 9 nterms values, 1 <= nterms <= GFK_MAX_TERMS).  This covers the
+ *   paper's trial functions 3, 4, 5 ((r0 - r) e^{-alpha r} orbitals,
+ *   antisymmetrised) and 7 ((z1 + z2) times a symmetric pair), and the
+ *   triplet and P_z functions of the benchmark workloads. */
+typedef enum { GFK_TRIAL_JASTROW_PRODUCT = 0, GFK_TRIAL_ORBITAL_PAIRS = 1 } gfk_trial_kind;
+
+#define GFK_MAX_TERMS 4
+#define GFK_MAX_PARAMS (7 + 9 * GFK_MAX_TERMS)
+#define GFK_MAX_INSTANCES 64
+
+/* One independent walk (an "instance"): the paper's statement of the problem
+ * -- a symmetry, the trial energy E_T (the paper's lambda_0 of the trial
+ * function), the time step dt, the number of replications N_rep and a seed.
+ * Random numbers are Philox4x32-10 with counter (walker id, step, rng_stream,
+ * tag) and key (seed low, seed high); the same (seed, rng_stream, walker id)
+ * gives the same trajectory in any context and any launch configuration. */
+typedef struct {
+    int32_t  state;          /* gfk_state                                         */
+    int32_t  prec;           /* gfk_prec; all instances of a context share it     */
+    int64_t  n_walkers;      /* N_rep, 1 .. 2^31 - 1                              */
+    double   dt;             /* time step (hartree^-1), > 0                       */
+    double   e_trial;        /* E_T, hartree                                      */
+    uint64_t seed;           /* Philox key                                        */
+    uint32_t rng_stream;     /* third Philox counter word                         */
+    int32_t  ee_on;          /* 1: V includes 1/r12; 0: drops it (test hook)      */
+    double   init_sigma;     /* initial positions: each coordinate ~ N(0, sigma^2) */
+} gfk_instance_desc;
+
+/* Create a context holding n_inst instances (1 .. GFK_MAX_INSTANCES).
+ * cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
+ * or NULL.  The context allocates and owns all device memory it uses.
+ * The current CUDA device at this call is the context's device.
+ * Returns GFK_EINVAL for a bad descriptor, GFK_ENOMEM / GFK_ECUDA on failure;
+ * *out is NULL unless GFK_OK. */
+gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_stream,
+                      gfk_ctx** out);
+
+/* Set instance inst's trial function (host params, copied).  Allowed before
+ * the first gfk_propagate, or after gfk_reset.  GFK_ESTATE otherwise;
+ * GFK_EINVAL for a malformed parameter vector. */
+gfk_status gfk_set_trial(gfk_ctx* ctx, int32_t inst, int32_t trial_kind,
+                         const double* params, int32_t n_params);
+
+/* Choose the launch shape of the walk kernels: threads per block
+ * (64, 128, 256 or 512) and walkers per thread (1, 2 or 4).  Results per
+ * walker do not depend on it; population sums differ only by rounding order
+ * (FP64 path) or by the FP32 rounding of the block shift (mixed path).
+ * Allowed at any time between calls. */
+gfk_status gfk_set_launch(gfk_ctx* ctx, int32_t threads_per_block, int32_t walkers_per_thread);
+
+/* Advance every instance by n_steps moves (asynchronous on the context's
+ * stream).  The first call after gfk_create / gfk_reset initialises the
+ * population (X0 = init_sigma * xi from Philox tags 2 and 3 at step 0,
+ * log-weight 0) and records the step-0 population sums.  Each move is
+ *   X <- X + b(X) dt + sqrt(dt) xi,   b = grad ln|psi|       (the SDE under Eq. 4)
+ *   logw <- logw - (E_L(X) - E_T) dt, E_L = -Delta(psi)/(2 psi) + V
+ * (the right-point Riemann sum of the Feynman-Kac exponent, Eq. 4), then the
+ * fixed-node test, then the population sums of that step.
+ * GFK_ESTATE if an instance has no trial function.  Step counts are
+ * cumulative; a run interrupted and resumed at a multiple of 16 steps is
+ * bitwise identical to an uninterrupted one. */
+gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps);
+
+/* Number of moves made so far (all instances move together). */
+gfk_status gfk_steps(gfk_ctx* ctx, int64_t* n_steps);
+
+/* Space-averaged estimators of instance inst for steps 0..S (S = gfk_steps),
+ * written to host arrays of cap >= S + 1 doubles (any of them may be NULL):
+ *   e_mixed[k] = sum_i w_i E_L(X_i) / sum_i w_i     after k moves
+ *   ln_z[k]    = ln( sum_i w_i / N_rep )            (Eq. 4: lambda ~ E_T - ln z / t)
+ *   ess[k]     = (sum_i w_i)^2 / sum_i w_i^2        (effective sample size)
+ * and *e_final = e_mixed[S] (may be NULL).  Dead walkers have w = 0.
+ * Synchronises the stream.  GFK_EOVERFLOW if cap < S + 1 (nothing written);
+ * GFK_ENONFINITE (outputs written) if any walker was killed for a non-finite
+ * drift or local energy. */
+gfk_status gfk_energy(gfk_ctx* ctx, int32_t inst, double* e_mixed, double* ln_z,
+                      double* ess, int64_t cap, double* e_final);
+
+/* Raw population sums of instance inst, 6 doubles per step for steps 0..S:
+ * { c, W, P, Q, R, n_alive } with W = sum e^{logw - c}, P = sum w E_L,
+ * Q = sum w^2, R = sum w E_L^2 (w = e^{logw - c}).  host_rows holds cap rows.
+ * Synchronises the stream.  GFK_EOVERFLOW if cap < S + 1. */
+gfk_status gfk_sums(gfk_ctx* ctx, int32_t inst, double* host_rows, int64_t cap);
+
+/* Copy instance inst's walkers to host memory (any pointer may be NULL):
+ * x6 (n_walkers * 6 doubles, walker-major), logw (n_walkers doubles, -inf for
+ * dead walkers), alive (n_walkers bytes).  Mixed-precision positions are
+ * widened exactly from FP32.  Synchronises the stream.  GFK_ESTATE before the
+ * population exists. */
+gfk_status gfk_get_walkers(gfk_ctx* ctx, int32_t inst, double* x6, double* logw,
+                           uint8_t* alive);
+
+/* Per-instance event counters (host int64[3]): walkers killed for a non-finite
+ * drift or local energy, walkers killed at the node, and moves that landed an
+ * electron within 1e-10 (FP64) or 1e-5 (mixed) bohr of the nucleus or of the
+ * other electron (a diagnostic only: nothing is changed). */
+gfk_status gfk_counters(gfk_ctx* ctx, int32_t inst, int64_t* host_counts3);
+
+/* Checkpoint: the whole walk state (population planes, step counter, per-step
+ * sums, counters) as an opaque host blob of gfk_checkpoint_size bytes.
+ * gfk_restore loads a blob written by a context created with the same
+ * descriptors and trial functions; resuming from it is bitwise identical to
+ * never having stopped (when the step count is a multiple of 16).
+ * GFK_EINVAL if the blob does not match the context. */
+gfk_status gfk_checkpoint_size(gfk_ctx* ctx, int64_t* bytes);
+gfk_status gfk_checkpoint(gfk_ctx* ctx, void* host_blob, int64_t bytes);
+gfk_status gfk_restore(gfk_ctx* ctx, const void* host_blob, int64_t bytes);
+
+/* Kernel timing.  While enabled, CUDA events on the context's stream bracket
+ * every walk-kernel launch.  gfk_profile_read synchronises the stream and
+ * returns the summed device time of those launches (ms), their number and the
+ * walker-steps they advanced (sum over launches of live-or-dead walkers x
+ * steps), then clears the tallies if reset != 0.  Any pointer may be NULL. */
+gfk_status gfk_profile(gfk_ctx* ctx, int32_t enable);
+gfk_status gfk_profile_read(gfk_ctx* ctx, double* walk_ms, int64_t* launches,
+                            double* walker_steps, int32_t reset);
+
+/* Forget the population: the next gfk_propagate re-initialises it (step 0). */
+gfk_status gfk_reset(gfk_ctx* ctx);
+
+/* Free the context and everything it allocated.  NULL is ignored. */
+void gfk_destroy(gfk_ctx* ctx);
+
+/* Static description of a status code. */
+const char* gfk_status_string(gfk_status s);
+
+/* The last CUDA error message recorded by ctx ("" if none). */
+const char* gfk_last_error(gfk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFK_H */

@@ -262,7 +262,7 @@ static void orc_eval(const orc_trial* t, int ee_on, const double x[6],
     double u, up, upp;
     orc_jastrow(t, r12, &u, &up, &upp);
 
-    if (Phi == 0.0) {
+    if (!(Phi > 0.0 || Phi < 0.0)) {      /* exactly zero (or not a number) */
         *sign = 0;
         for (int d = 0; d < 6; ++d) b[d] = NAN;
         *el = NAN;

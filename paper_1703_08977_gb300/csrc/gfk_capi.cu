@@ -1,0 +1,824 @@
+// C ABI of the GFK walker library (declared in include/gfk.h): argument
+// checking, device memory, launch shapes and the order of kernel launches.
+// All arithmetic of the walk runs in the kernels of gfk_fp64.cu, gfk_mixed.cu
+// and gfk_reduce.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gfk_types.h"
+
+namespace gfk {
+cudaError_t launch_init_fp64(int kind, int threads, int nblk, const InstDev* insts,
+                             const BlockMap& bm, const StateF64& st, PartialRec* part,
+                             unsigned long long* counters, cudaStream_t stream);
+cudaError_t launch_walk_fp64(int kind, int threads, int nblk, const InstDev* insts,
+                             const BlockMap& bm, const StateF64& st, uint32_t step0, int nsteps,
+                             PartialRec* part, unsigned long long* counters, cudaStream_t stream);
+cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
+                              const BlockMap& bm, const StateMixed& st, PartialRec* part,
+                              unsigned long long* counters, cudaStream_t stream);
+cudaError_t launch_walk_mixed(int kind, int wpt, int threads, int nblk, const InstDev* insts,
+                              const BlockMap& bm, const StateMixed& st, uint32_t step0,
+                              int nsteps, PartialRec* part, unsigned long long* counters,
+                              cudaStream_t stream);
+cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
+                               SeriesRow* series, int64_t series_cap, int64_t row_base,
+                               cudaStream_t stream);
+cudaError_t launch_finalize(const SeriesRow* rows, int64_t n, double n0, double* e, double* lnz,
+                            double* ess, cudaStream_t stream);
+cudaError_t launch_export(bool mixed, const StateF64& s64, const StateMixed& smx, int64_t off,
+                          int64_t n, double* x6, double* logw, uint8_t* alive,
+                          cudaStream_t stream);
+}  // namespace gfk
+
+using namespace gfk;
+
+struct gfk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int prec = GFK_PREC_FP64;
+    int n_inst = 0;
+    std::vector<gfk_instance_desc> desc;
+    std::vector<TrialHost> trial;
+    std::vector<int> has_trial;
+    std::vector<int64_t> off;     // first slot per instance
+    int64_t n_slots = 0;
+    InstDev* d_inst = nullptr;
+    // state
+    StateF64 s64{};
+    StateMixed smx{};
+    // per-step block records for one chunk
+    PartialRec* part = nullptr;
+    int64_t part_records = 0;     // capacity in records
+    // merged per-step sums, [inst][series_cap]
+    SeriesRow* series = nullptr;
+    int64_t series_cap = 0;
+    unsigned long long* counters = nullptr;
+    // output staging for gfk_energy / gfk_get_walkers, grown on demand
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // launch shape
+    int threads = 128;
+    int wpt = 1;
+    int64_t part_budget_bytes = 256ll << 20;
+    // kernel timing (gfk_profile)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;     // pairs: [2k] start, [2k+1] stop
+    int64_t ev_used = 0;                  // pairs recorded since the last read
+    int64_t prof_launches = 0;
+    double prof_ms = 0.0;
+    double prof_walker_steps = 0.0;
+    // progress
+    bool initialized = false;
+    bool params_dirty = true;
+    int64_t steps = 0;
+    std::string last_error;
+};
+
+namespace {
+
+int g_fault_alloc_countdown = -1;   // GFK_FAULT_ALLOC=n: the n-th allocation fails
+
+void read_fault_env() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    const char* v = std::getenv("GFK_FAULT_ALLOC");
+    if (v && *v) g_fault_alloc_countdown = std::atoi(v);
+}
+
+gfk_status cuda_fail(gfk_ctx* ctx, cudaError_t e, const char* what) {
+    if (ctx) {
+        ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return GFK_ECUDA;
+}
+
+#define GFK_CK(ctx, call)                                    \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Device allocation with the host-side fault-injection hook.
+gfk_status dev_alloc(gfk_ctx* ctx, void** p, size_t bytes) {
+    read_fault_env();
+    *p = nullptr;
+    if (g_fault_alloc_countdown > 0 && --g_fault_alloc_countdown == 0) {
+        ctx->last_error = "allocation failure injected by GFK_FAULT_ALLOC";
+        return GFK_ENOMEM;
+    }
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        ctx->last_error = "cudaMalloc: out of device memory";
+        return GFK_ENOMEM;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    return GFK_OK;
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+gfk_status ensure_scratch(gfk_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->scratch_bytes) return GFK_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    dev_free(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    gfk_status st = dev_alloc(ctx, &ctx->scratch, bytes);
+    if (st == GFK_OK) ctx->scratch_bytes = bytes;
+    return st;
+}
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_d(double v) { return std::isfinite(v); }
+
+gfk_status parse_trial(int kind, const double* p, int np, TrialHost* t) {
+    std::memset(t, 0, sizeof(*t));
+    if (!p) return GFK_EINVAL;
+    for (int i = 0; i < np; ++i)
+        if (!finite_d(p[i])) return GFK_EINVAL;
+    t->kind = kind;
+    if (kind == GFK_TRIAL_JASTROW_PRODUCT) {
+        if (np < 3 || np > 7) return GFK_EINVAL;
+        t->Z = p[0];
+        t->a = p[1];
+        t->beta = p[2];
+        for (int k = 0; k < 4; ++k) t->ck[k] = (3 + k < np) ? p[3 + k] : 0.0;
+        t->nterms = 1;
+        if (!(t->Z > 0.0) || t->beta < 0.0) return GFK_EINVAL;
+        return GFK_OK;
+    }
+    if (kind == GFK_TRIAL_ORBITAL_PAIRS) {
+        if (np < 7) return GFK_EINVAL;
+        t->a = p[0];
+        t->beta = p[1];
+        for (int k = 0; k < 4; ++k) t->ck[k] = p[2 + k];
+        const double ntd = p[6];
+        const int nt = (int)ntd;
+        if ((double)nt != ntd || nt < 1 || nt > GFK_MAX_TERMS || np != 7 + 9 * nt) return GFK_EINVAL;
+        if (t->beta < 0.0) return GFK_EINVAL;
+        t->nterms = nt;
+        for (int i = 0; i < nt; ++i) {
+            const double* q = p + 7 + 9 * i;
+            t->s[i] = q[0];
+            t->alpha[i][0] = q[1]; t->c0[i][0] = q[2]; t->c1[i][0] = q[3]; t->cz[i][0] = q[4];
+            t->alpha[i][1] = q[5]; t->c0[i][1] = q[6]; t->c1[i][1] = q[7]; t->cz[i][1] = q[8];
+            if (t->alpha[i][0] < 0.0 || t->alpha[i][1] < 0.0) return GFK_EINVAL;
+        }
+        return GFK_OK;
+    }
+    return GFK_EINVAL;
+}
+
+int64_t blocks_for(int64_t n, int threads, int wpt) {
+    const int64_t per = (int64_t)threads * wpt;
+    return (n + per - 1) / per;
+}
+
+BlockMap make_block_map(const gfk_ctx* ctx, int64_t* nblk_total) {
+    BlockMap bm;
+    std::memset(&bm, 0, sizeof(bm));
+    bm.n_inst = ctx->n_inst;
+    bm.wpt = ctx->wpt;
+    int64_t b = 0;
+    for (int i = 0; i < ctx->n_inst; ++i) {
+        bm.begin[i] = (int32_t)b;
+        b += blocks_for(ctx->desc[i].n_walkers, ctx->threads, ctx->wpt);
+    }
+    bm.begin[ctx->n_inst] = (int32_t)b;
+    *nblk_total = b;
+    return bm;
+}
+
+int launch_kind(const gfk_ctx* ctx) {
+    int k = ctx->trial[0].kind;
+    for (int i = 1; i < ctx->n_inst; ++i)
+        if (ctx->trial[i].kind != k) return 2;
+    return k;
+}
+
+gfk_status upload_instances(gfk_ctx* ctx) {
+    std::vector<InstDev> h(ctx->n_inst);
+    for (int i = 0; i < ctx->n_inst; ++i) {
+        const gfk_instance_desc& d = ctx->desc[i];
+        InstDev& v = h[i];
+        std::memset(&v, 0, sizeof(v));
+        v.n = d.n_walkers;
+        v.off = ctx->off[i];
+        v.dt = d.dt;
+        v.sqrt_dt = std::sqrt(d.dt);
+        v.e_trial = d.e_trial;
+        v.sigma = d.init_sigma;
+        v.k0 = (uint32_t)(d.seed & 0xffffffffull);
+        v.k1 = (uint32_t)(d.seed >> 32);
+        v.stream = d.rng_stream;
+        v.ee_on = d.ee_on ? 1 : 0;
+        v.trial = ctx->trial[i];
+    }
+    GFK_CK(ctx, cudaMemcpyAsync(ctx->d_inst, h.data(), sizeof(InstDev) * ctx->n_inst,
+                                cudaMemcpyHostToDevice, ctx->stream));
+    // the host vector dies at return: wait for the copy
+    GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->params_dirty = false;
+    return GFK_OK;
+}
+
+// Ensures room for `rows` chunk rows of block records; returns the rows that fit.
+gfk_status ensure_partials(gfk_ctx* ctx, int64_t nblk, int64_t* rows_fit) {
+    int64_t rows = ctx->part_budget_bytes / (int64_t)(nblk * sizeof(PartialRec));
+    rows = std::max<int64_t>(kRing, std::min<int64_t>(rows, 1024));
+    rows = (rows / kRing) * kRing;
+    const int64_t need = rows * nblk;
+    if (need > ctx->part_records) {
+        // the old buffer may still be read by queued kernels
+        GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
+        dev_free(ctx->part);
+        ctx->part = nullptr;
+        ctx->part_records = 0;
+        void* p = nullptr;
+        gfk_status st = dev_alloc(ctx, &p, sizeof(PartialRec) * (size_t)need);
+        if (st != GFK_OK) return st;
+        ctx->part = (PartialRec*)p;
+        ctx->part_records = need;
+    }
+    *rows_fit = rows;
+    return GFK_OK;
+}
+
+gfk_status ensure_series(gfk_ctx* ctx, int64_t rows_needed) {
+    if (rows_needed <= ctx->series_cap) return GFK_OK;
+    int64_t cap = std::max<int64_t>(rows_needed, std::max<int64_t>(2 * ctx->series_cap, 1024));
+    void* p = nullptr;
+    gfk_status st = dev_alloc(ctx, &p, sizeof(SeriesRow) * (size_t)cap * ctx->n_inst);
+    if (st != GFK_OK) return st;
+    SeriesRow* ns = (SeriesRow*)p;
+    if (ctx->series && ctx->series_cap > 0) {
+        for (int i = 0; i < ctx->n_inst; ++i) {
+            cudaError_t e = cudaMemcpyAsync(ns + (int64_t)i * cap, ctx->series + (int64_t)i * ctx->series_cap,
+                                            sizeof(SeriesRow) * ctx->series_cap,
+                                            cudaMemcpyDeviceToDevice, ctx->stream);
+            if (e != cudaSuccess) { dev_free(ns); return cuda_fail(ctx, e, "cudaMemcpyAsync(series)"); }
+        }
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) { dev_free(ns); return cuda_fail(ctx, e, "cudaStreamSynchronize"); }
+        dev_free(ctx->series);
+    }
+    ctx->series = ns;
+    ctx->series_cap = cap;
+    return GFK_OK;
+}
+
+gfk_status initialise_population(gfk_ctx* ctx) {
+    for (int i = 0; i < ctx->n_inst; ++i)
+        if (!ctx->has_trial[i]) return GFK_ESTATE;
+    if (ctx->params_dirty) {
+        gfk_status st = upload_instances(ctx);
+        if (st != GFK_OK) return st;
+    }
+    int64_t nblk = 0;
+    BlockMap bm = make_block_map(ctx, &nblk);
+    int64_t rows_fit = 0;
+    gfk_status st = ensure_partials(ctx, nblk, &rows_fit);
+    if (st != GFK_OK) return st;
+    st = ensure_series(ctx, 1);
+    if (st != GFK_OK) return st;
+    GFK_CK(ctx, cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * ctx->n_inst,
+                                ctx->stream));
+    const int kind = launch_kind(ctx);
+    if (ctx->prec == GFK_PREC_FP64) {
+        GFK_CK(ctx, launch_init_fp64(kind, ctx->threads, (int)nblk, ctx->d_inst, bm, ctx->s64,
+                                     ctx->part, ctx->counters, ctx->stream));
+    } else {
+        GFK_CK(ctx, launch_init_mixed(kind, ctx->threads, (int)nblk, ctx->d_inst, bm, ctx->smx,
+                                      ctx->part, ctx->counters, ctx->stream));
+    }
+    GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, 1, ctx->series, ctx->series_cap, 0,
+                                   ctx->stream));
+    ctx->initialized = true;
+    ctx->steps = 0;
+    return GFK_OK;
+}
+
+gfk_status check_inst(gfk_ctx* ctx, int32_t inst) {
+    if (!ctx) return GFK_EINVAL;
+    if (inst < 0 || inst >= ctx->n_inst) return GFK_EINVAL;
+    return GFK_OK;
+}
+
+void free_all(gfk_ctx* ctx) {
+    dev_free(ctx->d_inst);
+    dev_free(ctx->s64.x);
+    dev_free(ctx->s64.logw);
+    dev_free(ctx->smx.p0);
+    dev_free(ctx->smx.p1);
+    dev_free(ctx->s64.sgn);
+    dev_free(ctx->smx.sgn);
+    dev_free(ctx->part);
+    dev_free(ctx->scratch);
+    dev_free(ctx->series);
+    dev_free(ctx->counters);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    ctx->ev_pool.clear();
+}
+
+// Harvests recorded event pairs into the running tallies.
+gfk_status profile_harvest(gfk_ctx* ctx) {
+    if (ctx->ev_used == 0) return GFK_OK;
+    GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t k = 0; k < ctx->ev_used; ++k) {
+        float ms = 0.f;
+        GFK_CK(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[2 * k], ctx->ev_pool[2 * k + 1]));
+        ctx->prof_ms += ms;
+    }
+    ctx->ev_used = 0;
+    return GFK_OK;
+}
+
+// Event pair for the next walk launch (NULLs when profiling is off).
+gfk_status profile_pair(gfk_ctx* ctx, cudaEvent_t* a, cudaEvent_t* b) {
+    *a = *b = nullptr;
+    if (!ctx->profiling) return GFK_OK;
+    if (ctx->ev_used >= 4096) {
+        gfk_status st = profile_harvest(ctx);
+        if (st != GFK_OK) return st;
+    }
+    while ((int64_t)ctx->ev_pool.size() < 2 * (ctx->ev_used + 1)) {
+        cudaEvent_t e;
+        GFK_CK(ctx, cudaEventCreate(&e));
+        ctx->ev_pool.push_back(e);
+    }
+    *a = ctx->ev_pool[2 * ctx->ev_used];
+    *b = ctx->ev_pool[2 * ctx->ev_used + 1];
+    ++ctx->ev_used;
+    return GFK_OK;
+}
+
+// Checkpoint blob header.
+struct BlobHeader {
+    char magic[8];
+    int32_t version, n_inst, prec, initialized;
+    int64_t n_slots, steps, series_rows;
+    uint64_t desc_hash;
+};
+
+uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char* c = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+uint64_t desc_hash(const gfk_ctx* ctx) {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < ctx->n_inst; ++i) {
+        const gfk_instance_desc& d = ctx->desc[i];
+        h = fnv1a(&d.state, sizeof(d.state), h);
+        h = fnv1a(&d.prec, sizeof(d.prec), h);
+        h = fnv1a(&d.n_walkers, sizeof(d.n_walkers), h);
+        h = fnv1a(&d.dt, sizeof(d.dt), h);
+        h = fnv1a(&d.e_trial, sizeof(d.e_trial), h);
+        h = fnv1a(&d.seed, sizeof(d.seed), h);
+        h = fnv1a(&d.rng_stream, sizeof(d.rng_stream), h);
+        h = fnv1a(&d.ee_on, sizeof(d.ee_on), h);
+        h = fnv1a(&d.init_sigma, sizeof(d.init_sigma), h);
+        h = fnv1a(&ctx->trial[i], sizeof(TrialHost), h);
+    }
+    return h;
+}
+
+size_t state_bytes(const gfk_ctx* ctx) {
+    if (ctx->prec == GFK_PREC_FP64) return (size_t)ctx->n_slots * (7 * sizeof(double) + 1);
+    return (size_t)ctx->n_slots * (2 * sizeof(float4) + 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gfk_status_string(gfk_status s) {
+    switch (s) {
+        case GFK_OK: return "ok";
+        case GFK_EINVAL: return "invalid argument";
+        case GFK_ENOMEM: return "out of memory";
+        case GFK_ECUDA: return "CUDA error";
+        case GFK_ESTATE: return "call not valid in the current state";
+        case GFK_ENONFINITE: return "walkers killed for non-finite drift or local energy";
+        case GFK_EOVERFLOW: return "caller buffer too small";
+        case GFK_ETIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+const char* gfk_last_error(gfk_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_stream,
+                      gfk_ctx** out) {
+    if (!out) return GFK_EINVAL;
+    *out = nullptr;
+    if (!inst || n_inst < 1 || n_inst > GFK_MAX_INSTANCES) return GFK_EINVAL;
+    int64_t total = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const gfk_instance_desc& d = inst[i];
+        if (d.state < GFK_1S || d.state > GFK_PZ) return GFK_EINVAL;
+        if (d.prec != GFK_PREC_FP64 && d.prec != GFK_PREC_MIXED) return GFK_EINVAL;
+        if (d.prec != inst[0].prec) return GFK_EINVAL;
+        if (d.n_walkers < 1 || d.n_walkers > 0x7fffffffll) return GFK_EINVAL;
+        if (!(d.dt > 0.0) || !finite_d(d.dt)) return GFK_EINVAL;
+        if (!finite_d(d.e_trial)) return GFK_EINVAL;
+        if (!(d.init_sigma > 0.0) || !finite_d(d.init_sigma)) return GFK_EINVAL;
+        if (d.ee_on != 0 && d.ee_on != 1) return GFK_EINVAL;
+        total += (d.n_walkers + 31) / 32 * 32;
+    }
+    if (total > (1ll << 34)) return GFK_EINVAL;
+
+    gfk_ctx* ctx = new (std::nothrow) gfk_ctx();
+    if (!ctx) return GFK_ENOMEM;
+    ctx->n_inst = n_inst;
+    ctx->prec = inst[0].prec;
+    ctx->desc.assign(inst, inst + n_inst);
+    ctx->trial.assign(n_inst, TrialHost());
+    ctx->has_trial.assign(n_inst, 0);
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->threads = ctx->prec == GFK_PREC_FP64 ? 128 : 256;
+    ctx->wpt = ctx->prec == GFK_PREC_FP64 ? 1 : 2;
+    int64_t o = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        ctx->off.push_back(o);
+        o += (inst[i].n_walkers + 31) / 32 * 32;
+    }
+    ctx->n_slots = o;
+
+    gfk_status st = GFK_OK;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) {
+        st = cuda_fail(ctx, e, "cudaGetDevice");
+        delete ctx;
+        return st;
+    }
+    void* p = nullptr;
+#define ALLOC(field, type, bytes)                      \
+    do {                                               \
+        st = dev_alloc(ctx, &p, (bytes));              \
+        if (st != GFK_OK) goto fail;                   \
+        field = (type)p;                               \
+    } while (0)
+    ALLOC(ctx->d_inst, InstDev*, sizeof(InstDev) * n_inst);
+    ALLOC(ctx->counters, unsigned long long*, sizeof(unsigned long long) * kNumCounters * n_inst);
+    if (ctx->prec == GFK_PREC_FP64) {
+        ALLOC(ctx->s64.x, double*, sizeof(double) * 6 * ctx->n_slots);
+        ALLOC(ctx->s64.logw, double*, sizeof(double) * ctx->n_slots);
+        ALLOC(ctx->s64.sgn, int8_t*, ctx->n_slots);
+        ctx->s64.stride = ctx->n_slots;
+    } else {
+        ALLOC(ctx->smx.p0, float4*, sizeof(float4) * ctx->n_slots);
+        ALLOC(ctx->smx.p1, float4*, sizeof(float4) * ctx->n_slots);
+        ALLOC(ctx->smx.sgn, int8_t*, ctx->n_slots);
+    }
+#undef ALLOC
+    e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * n_inst, ctx->stream);
+    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaMemsetAsync"); goto fail; }
+    *out = ctx;
+    return GFK_OK;
+fail:
+    free_all(ctx);
+    delete ctx;
+    return st;
+}
+
+gfk_status gfk_set_trial(gfk_ctx* ctx, int32_t inst, int32_t trial_kind, const double* params,
+                         int32_t n_params) {
+    gfk_status st = check_inst(ctx, inst);
+    if (st != GFK_OK) return st;
+    if (ctx->initialized) return GFK_ESTATE;
+    TrialHost t;
+    st = parse_trial(trial_kind, params, n_params, &t);
+    if (st != GFK_OK) return st;
+    ctx->trial[inst] = t;
+    ctx->has_trial[inst] = 1;
+    ctx->params_dirty = true;
+    return GFK_OK;
+}
+
+gfk_status gfk_set_launch(gfk_ctx* ctx, int32_t threads_per_block, int32_t walkers_per_thread) {
+    if (!ctx) return GFK_EINVAL;
+    if (threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256 &&
+        threads_per_block != 512)
+        return GFK_EINVAL;
+    if (walkers_per_thread != 1 && walkers_per_thread != 2 && walkers_per_thread != 4)
+        return GFK_EINVAL;
+    if (ctx->prec == GFK_PREC_FP64 && walkers_per_thread != 1) return GFK_EINVAL;
+    ctx->threads = threads_per_block;
+    ctx->wpt = walkers_per_thread;
+    return GFK_OK;
+}
+
+gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
+    if (!ctx || n_steps < 0) return GFK_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    if (!ctx->initialized) {
+        gfk_status st = initialise_population(ctx);
+        if (st != GFK_OK) return st;
+    }
+    if (n_steps == 0) return GFK_OK;
+    if (ctx->steps + n_steps > 0xffffffffll) return GFK_EINVAL;
+    gfk_status st = ensure_series(ctx, ctx->steps + n_steps + 1);
+    if (st != GFK_OK) return st;
+    int64_t nblk = 0;
+    BlockMap bm = make_block_map(ctx, &nblk);
+    if (nblk > 0x7fffffffll) return GFK_EINVAL;
+    int64_t rows_fit = 0;
+    st = ensure_partials(ctx, nblk, &rows_fit);
+    if (st != GFK_OK) return st;
+    const int kind = launch_kind(ctx);
+    int64_t left = n_steps;
+    int64_t walkers = 0;
+    for (int i = 0; i < ctx->n_inst; ++i) walkers += ctx->desc[i].n_walkers;
+    while (left > 0) {
+        const int chunk = (int)std::min<int64_t>(left, rows_fit);
+        const uint32_t step0 = (uint32_t)ctx->steps;
+        cudaEvent_t ev0, ev1;
+        st = profile_pair(ctx, &ev0, &ev1);
+        if (st != GFK_OK) return st;
+        if (ev0) GFK_CK(ctx, cudaEventRecord(ev0, ctx->stream));
+        if (ctx->prec == GFK_PREC_FP64) {
+            GFK_CK(ctx, launch_walk_fp64(kind, ctx->threads, (int)nblk, ctx->d_inst, bm, ctx->s64,
+                                         step0, chunk, ctx->part, ctx->counters, ctx->stream));
+        } else {
+            GFK_CK(ctx, launch_walk_mixed(kind, ctx->wpt, ctx->threads, (int)nblk, ctx->d_inst, bm,
+                                          ctx->smx, step0, chunk, ctx->part, ctx->counters,
+                                          ctx->stream));
+        }
+        if (ev1) {
+            GFK_CK(ctx, cudaEventRecord(ev1, ctx->stream));
+            ctx->prof_launches += 1;
+            ctx->prof_walker_steps += (double)walkers * chunk;
+        }
+        GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
+                                       ctx->series_cap, ctx->steps + 1, ctx->stream));
+        ctx->steps += chunk;
+        left -= chunk;
+    }
+    return GFK_OK;
+}
+
+gfk_status gfk_steps(gfk_ctx* ctx, int64_t* n_steps) {
+    if (!ctx || !n_steps) return GFK_EINVAL;
+    *n_steps = ctx->steps;
+    return GFK_OK;
+}
+
+gfk_status gfk_sums(gfk_ctx* ctx, int32_t inst, double* host_rows, int64_t cap) {
+    gfk_status st = check_inst(ctx, inst);
+    if (st != GFK_OK) return st;
+    if (!host_rows) return GFK_EINVAL;
+    if (!ctx->initialized) return GFK_ESTATE;
+    const int64_t n = ctx->steps + 1;
+    if (cap < n) return GFK_EOVERFLOW;
+    DeviceGuard g(ctx->device);
+    GFK_CK(ctx, cudaMemcpyAsync(host_rows, ctx->series + (int64_t)inst * ctx->series_cap,
+                                sizeof(SeriesRow) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return GFK_OK;
+}
+
+gfk_status gfk_energy(gfk_ctx* ctx, int32_t inst, double* e_mixed, double* ln_z, double* ess,
+                      int64_t cap, double* e_final) {
+    gfk_status st = check_inst(ctx, inst);
+    if (st != GFK_OK) return st;
+    if (!ctx->initialized) return GFK_ESTATE;
+    const int64_t n = ctx->steps + 1;
+    if ((e_mixed || ln_z || ess) && cap < n) return GFK_EOVERFLOW;
+    DeviceGuard g(ctx->device);
+    st = ensure_scratch(ctx, sizeof(double) * 3 * n);
+    if (st != GFK_OK) return st;
+    double* d = (double*)ctx->scratch;
+    cudaError_t e = launch_finalize(ctx->series + (int64_t)inst * ctx->series_cap, n,
+                                    (double)ctx->desc[inst].n_walkers, d, d + n, d + 2 * n,
+                                    ctx->stream);
+    std::vector<double> h(3 * n);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    unsigned long long cnt[kNumCounters] = {0, 0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cnt, ctx->counters + (int64_t)inst * kNumCounters, sizeof(cnt),
+                            cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gfk_energy");
+    if (e_mixed) std::memcpy(e_mixed, h.data(), sizeof(double) * n);
+    if (ln_z) std::memcpy(ln_z, h.data() + n, sizeof(double) * n);
+    if (ess) std::memcpy(ess, h.data() + 2 * n, sizeof(double) * n);
+    if (e_final) *e_final = h[n - 1];
+    return cnt[0] > 0 ? GFK_ENONFINITE : GFK_OK;
+}
+
+gfk_status gfk_get_walkers(gfk_ctx* ctx, int32_t inst, double* x6, double* logw, uint8_t* alive) {
+    gfk_status st = check_inst(ctx, inst);
+    if (st != GFK_OK) return st;
+    if (!ctx->initialized) return GFK_ESTATE;
+    DeviceGuard g(ctx->device);
+    const int64_t n = ctx->desc[inst].n_walkers;
+    st = ensure_scratch(ctx, (size_t)n * (7 * sizeof(double) + 1));
+    if (st != GFK_OK) return st;
+    double* dx = (double*)ctx->scratch;
+    double* dl = dx + 6 * n;
+    uint8_t* da = (uint8_t*)(dl + n);
+    cudaError_t e = launch_export(ctx->prec == GFK_PREC_MIXED, ctx->s64, ctx->smx, ctx->off[inst], n,
+                                  dx, dl, da, ctx->stream);
+    if (e == cudaSuccess && x6)
+        e = cudaMemcpyAsync(x6, dx, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && logw)
+        e = cudaMemcpyAsync(logw, dl, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && alive)
+        e = cudaMemcpyAsync(alive, da, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gfk_get_walkers");
+    return GFK_OK;
+}
+
+gfk_status gfk_counters(gfk_ctx* ctx, int32_t inst, int64_t* host_counts3) {
+    gfk_status st = check_inst(ctx, inst);
+    if (st != GFK_OK) return st;
+    if (!host_counts3) return GFK_EINVAL;
+    DeviceGuard g(ctx->device);
+    unsigned long long cnt[kNumCounters];
+    GFK_CK(ctx, cudaMemcpyAsync(cnt, ctx->counters + (int64_t)inst * kNumCounters, sizeof(cnt),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < kNumCounters; ++j) host_counts3[j] = (int64_t)cnt[j];
+    return GFK_OK;
+}
+
+gfk_status gfk_checkpoint_size(gfk_ctx* ctx, int64_t* bytes) {
+    if (!ctx || !bytes) return GFK_EINVAL;
+    const int64_t rows = ctx->initialized ? ctx->steps + 1 : 0;
+    *bytes = (int64_t)(sizeof(BlobHeader) + state_bytes(ctx) +
+                       sizeof(SeriesRow) * rows * ctx->n_inst +
+                       sizeof(unsigned long long) * kNumCounters * ctx->n_inst);
+    return GFK_OK;
+}
+
+gfk_status gfk_checkpoint(gfk_ctx* ctx, void* host_blob, int64_t bytes) {
+    if (!ctx || !host_blob) return GFK_EINVAL;
+    int64_t need = 0;
+    gfk_checkpoint_size(ctx, &need);
+    if (bytes < need) return GFK_EOVERFLOW;
+    DeviceGuard g(ctx->device);
+    BlobHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "GFKCKPT1", 8);
+    h.version = 1;
+    h.n_inst = ctx->n_inst;
+    h.prec = ctx->prec;
+    h.initialized = ctx->initialized ? 1 : 0;
+    h.n_slots = ctx->n_slots;
+    h.steps = ctx->steps;
+    h.series_rows = ctx->initialized ? ctx->steps + 1 : 0;
+    h.desc_hash = desc_hash(ctx);
+    char* o = (char*)host_blob;
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    const int64_t ns = ctx->n_slots;
+    if (ctx->prec == GFK_PREC_FP64) {
+        GFK_CK(ctx, cudaMemcpyAsync(o, ctx->s64.x, sizeof(double) * 6 * ns, cudaMemcpyDeviceToHost, ctx->stream));
+        o += sizeof(double) * 6 * ns;
+        GFK_CK(ctx, cudaMemcpyAsync(o, ctx->s64.logw, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+        o += sizeof(double) * ns;
+        GFK_CK(ctx, cudaMemcpyAsync(o, ctx->s64.sgn, (size_t)ns, cudaMemcpyDeviceToHost, ctx->stream));
+        o += ns;
+    } else {
+        GFK_CK(ctx, cudaMemcpyAsync(o, ctx->smx.p0, sizeof(float4) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+        o += sizeof(float4) * ns;
+        GFK_CK(ctx, cudaMemcpyAsync(o, ctx->smx.p1, sizeof(float4) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+        o += sizeof(float4) * ns;
+        GFK_CK(ctx, cudaMemcpyAsync(o, ctx->smx.sgn, (size_t)ns, cudaMemcpyDeviceToHost, ctx->stream));
+        o += ns;
+    }
+    for (int i = 0; i < ctx->n_inst && h.series_rows > 0; ++i) {
+        GFK_CK(ctx, cudaMemcpyAsync(o, ctx->series + (int64_t)i * ctx->series_cap,
+                                    sizeof(SeriesRow) * h.series_rows, cudaMemcpyDeviceToHost, ctx->stream));
+        o += sizeof(SeriesRow) * h.series_rows;
+    }
+    GFK_CK(ctx, cudaMemcpyAsync(o, ctx->counters, sizeof(unsigned long long) * kNumCounters * ctx->n_inst,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return GFK_OK;
+}
+
+gfk_status gfk_restore(gfk_ctx* ctx, const void* host_blob, int64_t bytes) {
+    if (!ctx || !host_blob || bytes < (int64_t)sizeof(BlobHeader)) return GFK_EINVAL;
+    BlobHeader h;
+    std::memcpy(&h, host_blob, sizeof(h));
+    if (std::memcmp(h.magic, "GFKCKPT1", 8) != 0 || h.version != 1 || h.n_inst != ctx->n_inst ||
+        h.prec != ctx->prec || h.n_slots != ctx->n_slots || h.desc_hash != desc_hash(ctx))
+        return GFK_EINVAL;
+    for (int i = 0; i < ctx->n_inst; ++i)
+        if (!ctx->has_trial[i]) return GFK_ESTATE;
+    const int64_t need = (int64_t)(sizeof(BlobHeader) + state_bytes(ctx) +
+                                   sizeof(SeriesRow) * h.series_rows * ctx->n_inst +
+                                   sizeof(unsigned long long) * kNumCounters * ctx->n_inst);
+    if (bytes < need || (h.initialized && h.series_rows != h.steps + 1)) return GFK_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (ctx->params_dirty) {
+        gfk_status st = upload_instances(ctx);
+        if (st != GFK_OK) return st;
+    }
+    if (h.initialized) {
+        gfk_status st = ensure_series(ctx, h.series_rows);
+        if (st != GFK_OK) return st;
+    }
+    const char* o = (const char*)host_blob + sizeof(h);
+    const int64_t ns = ctx->n_slots;
+    if (ctx->prec == GFK_PREC_FP64) {
+        GFK_CK(ctx, cudaMemcpyAsync(ctx->s64.x, o, sizeof(double) * 6 * ns, cudaMemcpyHostToDevice, ctx->stream));
+        o += sizeof(double) * 6 * ns;
+        GFK_CK(ctx, cudaMemcpyAsync(ctx->s64.logw, o, sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->stream));
+        o += sizeof(double) * ns;
+        GFK_CK(ctx, cudaMemcpyAsync(ctx->s64.sgn, o, (size_t)ns, cudaMemcpyHostToDevice, ctx->stream));
+        o += ns;
+    } else {
+        GFK_CK(ctx, cudaMemcpyAsync(ctx->smx.p0, o, sizeof(float4) * ns, cudaMemcpyHostToDevice, ctx->stream));
+        o += sizeof(float4) * ns;
+        GFK_CK(ctx, cudaMemcpyAsync(ctx->smx.p1, o, sizeof(float4) * ns, cudaMemcpyHostToDevice, ctx->stream));
+        o += sizeof(float4) * ns;
+        GFK_CK(ctx, cudaMemcpyAsync(ctx->smx.sgn, o, (size_t)ns, cudaMemcpyHostToDevice, ctx->stream));
+        o += ns;
+    }
+    for (int i = 0; i < ctx->n_inst && h.series_rows > 0; ++i) {
+        GFK_CK(ctx, cudaMemcpyAsync(ctx->series + (int64_t)i * ctx->series_cap, o,
+                                    sizeof(SeriesRow) * h.series_rows, cudaMemcpyHostToDevice, ctx->stream));
+        o += sizeof(SeriesRow) * h.series_rows;
+    }
+    GFK_CK(ctx, cudaMemcpyAsync(ctx->counters, o, sizeof(unsigned long long) * kNumCounters * ctx->n_inst,
+                                cudaMemcpyHostToDevice, ctx->stream));
+    GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->initialized = h.initialized != 0;
+    ctx->steps = h.steps;
+    return GFK_OK;
+}
+
+gfk_status gfk_profile(gfk_ctx* ctx, int32_t enable) {
+    if (!ctx) return GFK_EINVAL;
+    ctx->profiling = enable != 0;
+    return GFK_OK;
+}
+
+gfk_status gfk_profile_read(gfk_ctx* ctx, double* walk_ms, int64_t* launches,
+                            double* walker_steps, int32_t reset) {
+    if (!ctx) return GFK_EINVAL;
+    DeviceGuard g(ctx->device);
+    gfk_status st = profile_harvest(ctx);
+    if (st != GFK_OK) return st;
+    if (walk_ms) *walk_ms = ctx->prof_ms;
+    if (launches) *launches = ctx->prof_launches;
+    if (walker_steps) *walker_steps = ctx->prof_walker_steps;
+    if (reset) {
+        ctx->prof_ms = 0.0;
+        ctx->prof_launches = 0;
+        ctx->prof_walker_steps = 0.0;
+    }
+    return GFK_OK;
+}
+
+gfk_status gfk_reset(gfk_ctx* ctx) {
+    if (!ctx) return GFK_EINVAL;
+    ctx->initialized = false;
+    ctx->steps = 0;
+    return GFK_OK;
+}
+
+void gfk_destroy(gfk_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

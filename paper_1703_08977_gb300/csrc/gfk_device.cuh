@@ -1,0 +1,331 @@
+// Device-side building blocks of the GFK walk: counter-based normals, trial
+// functions with their drift and local energy, and warp-level sums.
+//
+// Method: importance-sampled generalized Feynman-Kac for helium (Datta,
+// Rejcek, Fry, arXiv:1703.08977).  The walk is the drifted diffusion written
+// under Eq. 4, dY = grad(psi)/psi dt + dX, and the weight is exp(-int V_P)
+// with V_P = E_L - E_T, E_L = -Delta(psi)/(2 psi) + V (the GFK split H = H0 +
+// V_P of the "Path Integral Theory" section, with the 1/2 that H0 psi =
+// lambda0 psi requires).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gfk_types.h"
+
+namespace gfk {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter
+// (walker id, step, rng stream, tag), key (seed low word, seed high word).
+// ---------------------------------------------------------------------------
+struct Words4 { uint32_t w[4]; };
+
+__device__ __forceinline__ Words4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           uint32_t k0, uint32_t k1) {
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    constexpr uint32_t kBumpA = 0x9E3779B9u, kBumpB = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hiA = __umulhi(kMulA, c0), loA = kMulA * c0;
+        uint32_t hiB = __umulhi(kMulB, c2), loB = kMulB * c2;
+        uint32_t n0 = hiB ^ c1 ^ k0;
+        uint32_t n2 = hiA ^ c3 ^ k1;
+        c0 = n0; c1 = loB; c2 = n2; c3 = loA;
+        k0 += kBumpA; k1 += kBumpB;
+    }
+    Words4 o;
+    o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+    return o;
+}
+
+// Six N(0,1) variates for one (walker, step): words 0..3 of the call with tag
+// `tag0` and words 0..1 of the call with tag0+1 form the Box-Muller pairs
+// (w0,w1), (w2,w3), (w4,w5); xi_a = sqrt(-2 ln u_a) cos(2 pi u_b),
+// xi_b = sqrt(-2 ln u_a) sin(2 pi u_b).
+//
+// FP64: u = (w + 1/2) 2^-32 and library log/sqrt/sin/cos.
+__device__ __forceinline__ void normals6_f64(uint32_t walker, uint32_t step, uint32_t stream,
+                                             uint32_t tag0, uint32_t k0, uint32_t k1,
+                                             double xi[6]) {
+    Words4 a = philox10(walker, step, stream, tag0, k0, k1);
+    Words4 b = philox10(walker, step, stream, tag0 + 1u, k0, k1);
+    const uint32_t w[6] = {a.w[0], a.w[1], a.w[2], a.w[3], b.w[0], b.w[1]};
+    constexpr double kTwoPi = 6.283185307179586476925286766559;
+    constexpr double kInv32 = 1.0 / 4294967296.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double ua = ((double)w[2 * j] + 0.5) * kInv32;
+        double ub = ((double)w[2 * j + 1] + 0.5) * kInv32;
+        double rho = sqrt(-2.0 * log(ua));
+        double ang = kTwoPi * ub;
+        xi[2 * j] = rho * cos(ang);
+        xi[2 * j + 1] = rho * sin(ang);
+    }
+}
+
+// FP32: the same words, u = ((w >> 8) + 1/2) 2^-24 (exact in FP32), the hardware
+// log2 / reciprocal square root / sine / cosine.  The angle is taken as
+// 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine are most
+// accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
+__device__ __forceinline__ void normals6_f32(uint32_t walker, uint32_t step, uint32_t stream,
+                                             uint32_t k0, uint32_t k1, float xi[6]) {
+    Words4 a = philox10(walker, step, stream, 0u, k0, k1);
+    Words4 b = philox10(walker, step, stream, 1u, k0, k1);
+    const uint32_t w[6] = {a.w[0], a.w[1], a.w[2], a.w[3], b.w[0], b.w[1]};
+    constexpr float kInv24 = 1.0f / 16777216.0f;
+    constexpr float kMinus2Ln2 = -1.3862943611198906f;   // -2 ln 2
+    constexpr float kTwoPi = 6.2831853071795865f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float ua = ((float)(w[2 * j] >> 8) + 0.5f) * kInv24;
+        float ubc = ((float)(w[2 * j + 1] >> 8) + 0.5f) * kInv24 - 0.5f;   // exact
+        float r2 = kMinus2Ln2 * __log2f(ua);                               // -2 ln u > 0
+        float rho = r2 * rsqrtf(r2);
+        float s, c;
+        __sincosf(kTwoPi * ubc, &s, &c);
+        xi[2 * j] = -rho * c;
+        xi[2 * j + 1] = -rho * s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Precision helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float expn(float x) { return __expf(x); }
+__device__ __forceinline__ double expn(double x) { return exp(x); }
+__device__ __forceinline__ bool finite_(float x) { return isfinite(x); }
+__device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
+
+// ---------------------------------------------------------------------------
+// Trial parameters in the working precision (derived from TrialHost).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct TrialDev {
+    int kind, nterms;
+    R Z, Zm2, Z2;                  // kind 0: Z, Z - 2, Z^2
+    R a, beta, ee, eem2a, eebeta;  // Jastrow: a, beta, ee (0/1), ee - 2a, ee*beta
+    R c2, c3, c4, c5;              // 2c1, 3c2, 4c3, 5c4 (du/drho coefficients)
+    R d2, d6, d12, d20;            // 2c1, 6c2, 12c3, 20c4 (d2u/drho2 coefficients)
+    R s[GFK_MAX_TERMS];
+    R al[GFK_MAX_TERMS][2], c0[GFK_MAX_TERMS][2], c1[GFK_MAX_TERMS][2], cz[GFK_MAX_TERMS][2];
+    R km2[GFK_MAX_TERMS][2];       // alpha - 2
+    R hal2[GFK_MAX_TERMS][2];      // alpha^2 / 2
+};
+
+template <typename R>
+__device__ __forceinline__ void load_trial(const TrialHost& h, int ee_on, TrialDev<R>& t) {
+    t.kind = h.kind;
+    t.nterms = h.nterms;
+    t.Z = (R)h.Z;
+    t.Zm2 = (R)(h.Z - 2.0);
+    t.Z2 = (R)(h.Z * h.Z);
+    t.a = (R)h.a;
+    t.beta = (R)h.beta;
+    t.ee = ee_on ? R(1) : R(0);
+    t.eem2a = (R)((ee_on ? 1.0 : 0.0) - 2.0 * h.a);
+    t.eebeta = ee_on ? (R)h.beta : R(0);
+    t.c2 = (R)(2.0 * h.ck[0]);
+    t.c3 = (R)(3.0 * h.ck[1]);
+    t.c4 = (R)(4.0 * h.ck[2]);
+    t.c5 = (R)(5.0 * h.ck[3]);
+    t.d2 = (R)(2.0 * h.ck[0]);
+    t.d6 = (R)(6.0 * h.ck[1]);
+    t.d12 = (R)(12.0 * h.ck[2]);
+    t.d20 = (R)(20.0 * h.ck[3]);
+    for (int i = 0; i < GFK_MAX_TERMS; ++i) {
+        t.s[i] = (R)h.s[i];
+        for (int e = 0; e < 2; ++e) {
+            t.al[i][e] = (R)h.alpha[i][e];
+            t.c0[i][e] = (R)h.c0[i][e];
+            t.c1[i][e] = (R)h.c1[i][e];
+            t.cz[i][e] = (R)h.cz[i][e];
+            t.km2[i][e] = (R)(h.alpha[i][e] - 2.0);
+            t.hal2[i][e] = (R)(0.5 * h.alpha[i][e] * h.alpha[i][e]);
+        }
+    }
+}
+
+// Result of one trial evaluation.
+template <typename R>
+struct EvalOut {
+    R b[6];        // drift grad ln|psi|
+    R el;          // local energy
+    int sign;      // sign of psi (0: exactly zero)
+    R rmin;        // min(r1, r2, r12), for the coalescence diagnostic
+};
+
+// Jastrow factor u(r12) = a rho + sum c_k rho^{k+1}, rho = r/(1+beta r): returns
+// u', u'' and the combination (ee - 2u')/r12 written without the 1/r12
+// cancellation:  (ee - 2 a rho')/r = [(ee - 2a)/r + ee beta (2 + beta r)] rho',
+// and 2 rho h rho'/r = 2 h rho' / (1 + beta r) with h = (du/drho - a)/rho.
+template <typename R>
+struct JastrowOut { R up, upp, jee; };
+
+template <typename R>
+__device__ __forceinline__ JastrowOut<R> jastrow(const TrialDev<R>& t, R r12, R i12) {
+    R q = R(1) + t.beta * r12;
+    R iq = rcp(q);
+    R rho = r12 * iq;
+    R drho = iq * iq;                          // d rho / dr
+    R d2rho = R(-2) * t.beta * drho * iq;      // d2 rho / dr2
+    R h = t.c2 + rho * (t.c3 + rho * (t.c4 + rho * t.c5));   // (du/drho - a) / rho
+    R du = t.a + rho * h;                                   // du / drho
+    R d2u = t.d2 + rho * (t.d6 + rho * (t.d12 + rho * t.d20));
+    JastrowOut<R> o;
+    o.up = du * drho;
+    o.upp = d2u * drho * drho + du * d2rho;
+    o.jee = (t.eem2a * i12 + t.eebeta * (R(2) + t.beta * r12)) * drho - R(2) * h * drho * iq;
+    return o;
+}
+
+// Kind 0: psi = exp(-Z r1 - Z r2 + u(r12)).
+//   b_1 = -Z r1_hat + u' e12,  b_2 = -Z r2_hat - u' e12   (e12 = (r1 - r2)/r12)
+//   E_L = (Z - 2)(1/r1 + 1/r2) - Z^2 + (ee - 2u')/r12 - u'' - u'^2
+//         + Z u' (r1_hat - r2_hat) . e12
+// (the nuclear 1/r terms cancel exactly for Z = 2).
+template <typename R>
+__device__ __forceinline__ void eval_kind0(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
+    R s1 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
+    R dx = x[0] - x[3], dy = x[1] - x[4], dz = x[2] - x[5];
+    R s12 = dx * dx + dy * dy + dz * dz;
+    R i1 = rsq(s1), i2 = rsq(s2), i12 = rsq(s12);
+    R r12 = s12 * i12;
+    R ex = dx * i12, ey = dy * i12, ez = dz * i12;
+    JastrowOut<R> j = jastrow(t, r12, i12);
+    R h1x = x[0] * i1, h1y = x[1] * i1, h1z = x[2] * i1;
+    R h2x = x[3] * i2, h2y = x[4] * i2, h2z = x[5] * i2;
+    o.b[0] = -t.Z * h1x + j.up * ex;
+    o.b[1] = -t.Z * h1y + j.up * ey;
+    o.b[2] = -t.Z * h1z + j.up * ez;
+    o.b[3] = -t.Z * h2x - j.up * ex;
+    o.b[4] = -t.Z * h2y - j.up * ey;
+    o.b[5] = -t.Z * h2z - j.up * ez;
+    R proj = (h1x - h2x) * ex + (h1y - h2y) * ey + (h1z - h2z) * ez;
+    o.el = t.Zm2 * (i1 + i2) - t.Z2 + j.jee - j.upp - j.up * j.up + t.Z * j.up * proj;
+    o.sign = finite_(s1 + s2) ? 1 : 0;   // psi > 0 wherever X is finite
+    R r1 = s1 * i1, r2 = s2 * i2;
+    o.rmin = fmin(fmin(r1, r2), r12);
+}
+
+// Kind 1: psi = Phi exp(u(r12)), Phi = sum_t s_t f_A(r1) f_B(r2), orbitals
+// f = p e^{-alpha r}, p = c0 + c1 r + cz z.  Each term is evaluated with the
+// largest exponent factored out (ratios are unchanged; no underflow).
+// Per orbital, with g = e^{-alpha r}:
+//   grad f / g          = c1 r_hat + cz z_hat - alpha p r_hat
+//   (-lap f / 2 - 2 f / r) / g
+//                       = -c1/r + alpha (c1 + cz z / r) - alpha^2 p / 2 + (alpha - 2) p / r
+// (the second line folds the nuclear attraction into the kinetic term so the
+// 1/r singularities cancel exactly when the orbital meets the cusp).  Then
+//   b_1 = grad_1 Phi / Phi + u' e12,  b_2 = grad_2 Phi / Phi - u' e12
+//   E_L = T / Phi - u' (grad_1 Phi - grad_2 Phi) . e12 / Phi - u'' - u'^2
+//         + (ee - 2u')/r12,
+//   T = sum_t s_t [K_A p_B + p_A K_B] g_A g_B.
+template <typename R>
+__device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
+    R s1 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
+    R dx = x[0] - x[3], dy = x[1] - x[4], dz = x[2] - x[5];
+    R s12 = dx * dx + dy * dy + dz * dz;
+    R i1 = rsq(s1), i2 = rsq(s2), i12 = rsq(s12);
+    R r1 = s1 * i1, r2 = s2 * i2, r12 = s12 * i12;
+    R ex = dx * i12, ey = dy * i12, ez = dz * i12;
+    R h1[3] = {x[0] * i1, x[1] * i1, x[2] * i1};
+    R h2[3] = {x[3] * i2, x[4] * i2, x[5] * i2};
+    const R rr[2] = {r1, r2};
+    const R ir[2] = {i1, i2};
+    const R zz[2] = {x[2], x[5]};
+
+    // largest exponent -(alphaA r1 + alphaB r2) over the terms
+    R emax = -(t.al[0][0] * r1 + t.al[0][1] * r2);
+    for (int k = 1; k < t.nterms; ++k) emax = fmax(emax, -(t.al[k][0] * r1 + t.al[k][1] * r2));
+
+    R Phi = R(0), T = R(0);
+    R G1[3] = {R(0), R(0), R(0)}, G2[3] = {R(0), R(0), R(0)};
+    for (int k = 0; k < t.nterms; ++k) {
+        R g = expn(-(t.al[k][0] * r1 + t.al[k][1] * r2) - emax);
+        R p[2], K[2], gr[2][3];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const R* hh = e == 0 ? h1 : h2;
+            R al = t.al[k][e], c1 = t.c1[k][e], cz = t.cz[k][e];
+            R pe = t.c0[k][e] + c1 * rr[e] + cz * zz[e];
+            R radial = c1 - al * pe;                      // coefficient of r_hat
+            gr[e][0] = radial * hh[0];
+            gr[e][1] = radial * hh[1];
+            gr[e][2] = radial * hh[2] + cz;
+            K[e] = -c1 * ir[e] + al * (c1 + cz * zz[e] * ir[e]) - t.hal2[k][e] * pe +
+                   t.km2[k][e] * pe * ir[e];
+            p[e] = pe;
+        }
+        R sg = t.s[k] * g;
+        Phi += sg * p[0] * p[1];
+        T += sg * (K[0] * p[1] + p[0] * K[1]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            G1[d] += sg * gr[0][d] * p[1];
+            G2[d] += sg * p[0] * gr[1][d];
+        }
+    }
+    JastrowOut<R> j = jastrow(t, r12, i12);
+    R iP = rcp(Phi);
+    o.b[0] = G1[0] * iP + j.up * ex;
+    o.b[1] = G1[1] * iP + j.up * ey;
+    o.b[2] = G1[2] * iP + j.up * ez;
+    o.b[3] = G2[0] * iP - j.up * ex;
+    o.b[4] = G2[1] * iP - j.up * ey;
+    o.b[5] = G2[2] * iP - j.up * ez;
+    R cross = (G1[0] - G2[0]) * ex + (G1[1] - G2[1]) * ey + (G1[2] - G2[2]) * ez;
+    o.el = (T - j.up * cross) * iP - j.upp - j.up * j.up + j.jee;
+    o.sign = Phi > R(0) ? 1 : (Phi < R(0) ? -1 : 0);
+    o.rmin = fmin(fmin(r1, r2), r12);
+}
+
+// KIND 0 / 1 select the family at compile time; KIND 2 dispatches on t.kind
+// (used when one launch covers instances of both families).
+template <int KIND, typename R>
+__device__ __forceinline__ void eval_trial(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
+    if (KIND == 0) eval_kind0<R>(t, x, o);
+    else if (KIND == 1) eval_kind1<R>(t, x, o);
+    else if (t.kind == 0) eval_kind0<R>(t, x, o);
+    else eval_kind1<R>(t, x, o);
+}
+
+template <typename R>
+__device__ __forceinline__ bool eval_finite(const EvalOut<R>& o) {
+    bool f = finite_(o.el);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) f = f && finite_(o.b[d]);
+    return f;
+}
+
+// ---------------------------------------------------------------------------
+// Warp sums
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+    s = __dadd_rn(a, b);
+    double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+}  // namespace gfk

@@ -1,0 +1,325 @@
+// Mixed-precision walk: FP32 positions, drift, local energy and normals; FP64
+// log-weights and FP64 population sums above the warp.
+//
+// Each thread advances WPT walkers (ids tid, tid + T, ... within the block's
+// range, so every load and store is coalesced) for a whole chunk of steps with
+// the state in registers.  Per step and walker (the discretised Eq. 4 and the
+// drifted diffusion under it):
+//   xi     <- six N(0,1): Philox4x32-10 words, FP32 Box-Muller on the hardware
+//             log2 / rsqrt / sin / cos
+//   X      <- X + b dt + sqrt(dt) xi                    (FP32, fused multiply-add)
+//   b, E_L <- trial function at X in the cusp-cancelled form (FP32)
+//   node   :  sign psi changed or psi = 0 -> killed
+//   S      <- S + (E_L - E_T)            (FP32 Kahan sum since the last fold)
+//   w      =  2^{(d - S dt) log2 e}      (d = FP64 base minus the block shift)
+// Every kRing steps the FP32 sums are folded into the FP64 base,
+//   L <- L - (S + kRing (E_T,fp32 - E_T)) dt            (FP64),
+// the block shift c is reset to the block's largest L and d = (float)(L - c).
+// Per step each warp adds its (w, w E_L, w^2, w E_L^2, alive) in FP32; the
+// block adds its warps in FP64 every kRing steps and writes one PartialRec per
+// step; a deferred kernel merges blocks with compensated FP64 sums.
+#include <cuda_runtime.h>
+
+#include "gfk_block.cuh"
+#include "gfk_device.cuh"
+#include "gfk_types.h"
+
+namespace gfk {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void store_mixed(const StateMixed& st, int64_t slot, const float x[6],
+                                            double logw, int sg) {
+    const long long bits = __double_as_longlong(logw);
+    st.p0[slot] = make_float4(x[0], x[1], x[2], x[3]);
+    st.p1[slot] = make_float4(x[4], x[5], __int_as_float((int)(bits & 0xffffffffLL)),
+                              __int_as_float((int)(bits >> 32)));
+    st.sgn[slot] = (int8_t)sg;
+}
+
+__device__ __forceinline__ void load_mixed(const StateMixed& st, int64_t slot, float x[6],
+                                           double& logw, int& sg) {
+    const float4 a = st.p0[slot];
+    const float4 b = st.p1[slot];
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y;
+    const long long lo = (unsigned)__float_as_int(b.z);
+    const long long hi = (long long)__float_as_int(b.w);
+    logw = __longlong_as_double((hi << 32) | lo);
+    sg = st.sgn[slot];
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kMaxThreads)
+init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
+                  PartialRec* __restrict__ part, int nblk,
+                  unsigned long long* __restrict__ counters) {
+    __shared__ TrialDev<float> s_trial;
+    __shared__ double s_red[5][kMaxWarps];
+    const int blk = blockIdx.x;
+    const int inst = block_instance(bm, blk);
+    const InstDev& I = insts[inst];
+    if (threadIdx.x == 0) load_trial<float>(I.trial, I.ee_on, s_trial);
+    __syncthreads();
+    const int T = blockDim.x;
+    double q[5] = {0, 0, 0, 0, 0};
+    unsigned n_nonfinite = 0, n_node = 0;
+    for (int k = 0; k < bm.wpt; ++k) {
+        const int64_t id = (int64_t)(blk - bm.begin[inst]) * T * bm.wpt + (int64_t)k * T + threadIdx.x;
+        if (id >= I.n) continue;
+        // the initial positions are drawn in FP64, exactly as on the FP64 path,
+        // then rounded: both paths start from the same population
+        double xi[6];
+        normals6_f64((uint32_t)id, 0u, I.stream, 2u, I.k0, I.k1, xi);
+        float x[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) x[d] = (float)(I.sigma * xi[d]);
+        EvalOut<float> ev;
+        eval_trial<KIND, float>(s_trial, x, ev);
+        int sg = ev.sign;
+        if (sg == 0) {
+            ++n_node;
+        } else if (!eval_finite(ev)) {
+            sg = 0;
+            ++n_nonfinite;
+        }
+        double logw = -INFINITY;
+        if (sg != 0) {
+            logw = 0.0;
+            q[0] += 1.0;
+            q[1] += (double)ev.el;
+            q[2] += 1.0;
+            q[3] += (double)ev.el * (double)ev.el;
+            q[4] += 1.0;
+        }
+        store_mixed(st, I.off + id, x, logw, sg);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double v = warp_sum(q[k]);
+        if (lane == 0) s_red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[5] = {0, 0, 0, 0, 0};
+        for (int w = 0; w < (T >> 5); ++w)
+            for (int k = 0; k < 5; ++k) r[k] += s_red[k][w];
+        PartialRec rec;
+        rec.c = 0.0;
+        rec.W = r[0]; rec.P = r[1]; rec.Q = r[2]; rec.R = r[3]; rec.n = r[4];
+        part[blk] = rec;
+    }
+    flush_counters(counters, inst, n_nonfinite, n_node, 0u);
+}
+
+template <int KIND, int WPT>
+__global__ void __launch_bounds__(kMaxThreads)
+walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
+                  uint32_t step0, int nsteps, PartialRec* __restrict__ part, int nblk,
+                  unsigned long long* __restrict__ counters) {
+    __shared__ TrialDev<float> s_trial;
+    __shared__ float s_ring[kRing][5][kMaxWarps];
+    __shared__ double s_red[kMaxWarps];
+    const int blk = blockIdx.x;
+    const int inst = block_instance(bm, blk);
+    const InstDev& I = insts[inst];
+    if (threadIdx.x == 0) load_trial<float>(I.trial, I.ee_on, s_trial);
+    __syncthreads();
+    TrialDev<float> t_local;
+    if (KIND == 0) t_local = s_trial;
+    const TrialDev<float>& t = (KIND == 0) ? t_local : s_trial;
+
+    const float dt = (float)I.dt, sdt = (float)I.sqrt_dt;
+    const float et = (float)I.e_trial;
+    const double dt64 = I.dt;
+    // per-step E_T rounding, restored in FP64 at each fold
+    const double et_fix = ((double)et - I.e_trial);
+    constexpr float kLog2e = 1.4426950408889634f;
+    const float dt_log2e = dt * kLog2e;
+    const uint32_t k0 = I.k0, k1 = I.k1, stream = I.stream;
+    const int T = blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = T >> 5;
+
+    uint32_t wid[WPT];
+    int64_t slot[WPT];
+    bool valid[WPT];
+    float x[WPT][6], b[WPT][6];
+    double L[WPT];
+    float dsh[WPT], S[WPT], comp[WPT];
+    int sg[WPT];
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) {
+        const int64_t id = (int64_t)(blk - bm.begin[inst]) * T * WPT + (int64_t)k * T + threadIdx.x;
+        valid[k] = id < I.n;
+        wid[k] = (uint32_t)id;
+        slot[k] = I.off + id;
+        sg[k] = 0;
+        L[k] = -INFINITY;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) { x[k][d] = 0.f; b[k][d] = 0.f; }
+        if (valid[k]) load_mixed(st, slot[k], x[k], L[k], sg[k]);
+        if (sg[k] != 0) {
+            EvalOut<float> ev;
+            eval_trial<KIND, float>(t, x[k], ev);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) b[k][d] = ev.b[d];
+        }
+        S[k] = 0.f;
+        comp[k] = 0.f;
+    }
+    unsigned n_nonfinite = 0, n_node = 0, n_coal = 0;
+    double lmax = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < WPT; ++k)
+        if (sg[k] != 0) lmax = fmax(lmax, L[k]);
+    double c = block_max_shift(lmax, s_red);
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) : 0.f;
+    int fold_len = 0;
+
+    for (int s = 0; s < nsteps; ++s) {
+        const uint32_t step = step0 + (uint32_t)s;
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f;
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            if (sg[k] == 0) continue;
+            float xi[6];
+            normals6_f32(wid[k], step, stream, k0, k1, xi);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) x[k][d] = fmaf(sdt, xi[d], fmaf(b[k][d], dt, x[k][d]));
+            EvalOut<float> ev;
+            eval_trial<KIND, float>(t, x[k], ev);
+            if (ev.rmin < 1e-5f) ++n_coal;
+            if (ev.sign != sg[k]) {
+                sg[k] = 0;
+                L[k] = -INFINITY;
+                ++n_node;
+                continue;
+            }
+            if (!eval_finite(ev)) {
+                sg[k] = 0;
+                L[k] = -INFINITY;
+                ++n_nonfinite;
+                continue;
+            }
+#pragma unroll
+            for (int d = 0; d < 6; ++d) b[k][d] = ev.b[d];
+            // Kahan: S accumulates E_L - E_T since the last fold
+            const float y = (ev.el - et) - comp[k];
+            const float tsum = S[k] + y;
+            comp[k] = (tsum - S[k]) - y;
+            S[k] = tsum;
+            const float w = ex2_approx(fmaf(-S[k], dt_log2e, dsh[k] * kLog2e));
+            const float we = w * ev.el;
+            q0 += w;
+            q1 += we;
+            q2 += w * w;
+            q3 += we * ev.el;
+            q4 += 1.f;
+        }
+        q0 = warp_sum(q0);
+        q1 = warp_sum(q1);
+        q2 = warp_sum(q2);
+        q3 = warp_sum(q3);
+        q4 = warp_sum(q4);
+        const int r = s % kRing;
+        if (lane == 0) {
+            s_ring[r][0][warp] = q0;
+            s_ring[r][1][warp] = q1;
+            s_ring[r][2][warp] = q2;
+            s_ring[r][3][warp] = q3;
+            s_ring[r][4][warp] = q4;
+        }
+        ++fold_len;
+        if (r == kRing - 1 || s == nsteps - 1) {
+            __syncthreads();
+            const int rows = r + 1;
+            if ((int)threadIdx.x < rows) {
+                const int rr = threadIdx.x;
+                double acc[5] = {0, 0, 0, 0, 0};
+                for (int w = 0; w < nwarps; ++w)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) acc[k] += (double)s_ring[rr][k][w];
+                PartialRec rec;
+                rec.c = c;
+                rec.W = acc[0]; rec.P = acc[1]; rec.Q = acc[2]; rec.R = acc[3]; rec.n = acc[4];
+                part[(int64_t)(s - r + rr) * nblk + blk] = rec;
+            }
+            // fold the FP32 increments into the FP64 base
+            lmax = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < WPT; ++k) {
+                if (sg[k] != 0) {
+                    L[k] = L[k] - (((double)S[k] - (double)comp[k]) + (double)fold_len * et_fix) * dt64;
+                    lmax = fmax(lmax, L[k]);
+                }
+                S[k] = 0.f;
+                comp[k] = 0.f;
+            }
+            fold_len = 0;
+            c = block_max_shift(lmax, s_red);
+#pragma unroll
+            for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) : 0.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < WPT; ++k)
+        if (valid[k]) store_mixed(st, slot[k], x[k], sg[k] != 0 ? L[k] : -INFINITY, sg[k]);
+    flush_counters(counters, inst, n_nonfinite, n_node, n_coal);
+}
+
+cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
+                              const BlockMap& bm, const StateMixed& st, PartialRec* part,
+                              unsigned long long* counters, cudaStream_t stream) {
+    if (kind == 0)
+        init_mixed_kernel<0><<<nblk, threads, 0, stream>>>(insts, bm, st, part, nblk, counters);
+    else if (kind == 1)
+        init_mixed_kernel<1><<<nblk, threads, 0, stream>>>(insts, bm, st, part, nblk, counters);
+    else
+        init_mixed_kernel<2><<<nblk, threads, 0, stream>>>(insts, bm, st, part, nblk, counters);
+    return cudaGetLastError();
+}
+
+template <int KIND>
+static void launch_walk_mixed_k(int wpt, int threads, int nblk, const InstDev* insts,
+                                const BlockMap& bm, const StateMixed& st, uint32_t step0,
+                                int nsteps, PartialRec* part, unsigned long long* counters,
+                                cudaStream_t stream) {
+    switch (wpt) {
+        case 1:
+            walk_mixed_kernel<KIND, 1><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
+                                                                     part, nblk, counters);
+            break;
+        case 2:
+            walk_mixed_kernel<KIND, 2><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
+                                                                     part, nblk, counters);
+            break;
+        default:
+            walk_mixed_kernel<KIND, 4><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
+                                                                     part, nblk, counters);
+            break;
+    }
+}
+
+cudaError_t launch_walk_mixed(int kind, int wpt, int threads, int nblk, const InstDev* insts,
+                              const BlockMap& bm, const StateMixed& st, uint32_t step0,
+                              int nsteps, PartialRec* part, unsigned long long* counters,
+                              cudaStream_t stream) {
+    if (kind == 0)
+        launch_walk_mixed_k<0>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part, counters,
+                               stream);
+    else if (kind == 1)
+        launch_walk_mixed_k<1>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part, counters,
+                               stream);
+    else
+        launch_walk_mixed_k<2>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part, counters,
+                               stream);
+    return cudaGetLastError();
+}
+
+}  // namespace gfk

@@ -1,0 +1,169 @@
+// Deferred population reduction (space averaging over the replications) and
+// small output kernels.
+//
+// reduce_rows_kernel: for one instance and one step, merges the instance's
+// block records {c_b, W_b, P_b, Q_b, R_b, n_b} into
+//   C = max_b c_b,  W = sum_b W_b e^{c_b - C},  P = sum_b P_b e^{c_b - C},
+//   Q = sum_b Q_b e^{2 (c_b - C)},  R = sum_b R_b e^{c_b - C},  n = sum_b n_b,
+// with every sum carried as an unevaluated double-double (TwoSum), so the
+// merged value is the correctly rounded sum of the block values up to O(2^-100).
+// finalize_kernel turns merged rows into E(t) = P/W, ln z(t) = C + ln W - ln N
+// and ESS = W^2/Q (Eq. 4's z(t) and the space-averaged energy).
+#include <cuda_runtime.h>
+
+#include "gfk_device.cuh"
+#include "gfk_types.h"
+
+namespace gfk {
+
+struct DD { double hi, lo; };
+
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+    double s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __dadd_rn(e, __dadd_rn(a.lo, b.lo));
+    double hi = __dadd_rn(s, e);
+    double lo = __dsub_rn(e, __dsub_rn(hi, s));
+    DD r = {hi, lo};
+    return r;
+}
+
+__device__ __forceinline__ DD dd_shfl_xor(DD v, int o) {
+    DD r;
+    r.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    r.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    return r;
+}
+
+constexpr int kReduceThreads = 256;
+
+__global__ void __launch_bounds__(kReduceThreads)
+reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
+                   SeriesRow* __restrict__ series, int64_t series_cap, int64_t row_base) {
+    __shared__ double s_max[kReduceThreads / 32];
+    __shared__ DD s_acc[5][kReduceThreads / 32];
+    const int row = blockIdx.x;
+    const int inst = blockIdx.y;
+    const int b0 = bm.begin[inst], b1 = bm.begin[inst + 1];
+    const PartialRec* rp = part + (int64_t)row * nblk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    double m = -INFINITY;
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+        if (rp[b].n > 0.0) m = fmax(m, rp[b].c);
+    m = warp_max(m);
+    if (lane == 0) s_max[warp] = m;
+    __syncthreads();
+    double C = s_max[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) C = fmax(C, s_max[w]);
+    if (!isfinite(C)) C = 0.0;
+
+    DD acc[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] = DD{0.0, 0.0};
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+        const PartialRec r = rp[b];
+        if (!(r.n > 0.0)) continue;
+        const double f = exp(r.c - C);
+        const double v[5] = {r.W * f, r.P * f, r.Q * f * f, r.R * f, r.n};
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[k] = dd_add(acc[k], DD{v[k], 0.0});
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[k] = dd_add(acc[k], dd_shfl_xor(acc[k], o));
+        if (lane == 0) s_acc[k][warp] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DD tot[5];
+        for (int k = 0; k < 5; ++k) {
+            tot[k] = s_acc[k][0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot[k] = dd_add(tot[k], s_acc[k][w]);
+        }
+        SeriesRow out;
+        out.c = C;
+        out.W = tot[0].hi + tot[0].lo;
+        out.P = tot[1].hi + tot[1].lo;
+        out.Q = tot[2].hi + tot[2].lo;
+        out.R = tot[3].hi + tot[3].lo;
+        out.n = tot[4].hi + tot[4].lo;
+        series[(int64_t)inst * series_cap + row_base + row] = out;
+    }
+}
+
+__global__ void finalize_kernel(const SeriesRow* __restrict__ rows, int64_t n, double n0,
+                                double* __restrict__ e, double* __restrict__ lnz,
+                                double* __restrict__ ess) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const SeriesRow r = rows[i];
+    if (r.W > 0.0) {
+        e[i] = r.P / r.W;
+        lnz[i] = r.c + log(r.W) - log(n0);
+        ess[i] = r.W * r.W / r.Q;
+    } else {
+        e[i] = NAN;
+        lnz[i] = -INFINITY;
+        ess[i] = 0.0;
+    }
+}
+
+// Walkers of one instance to walker-major FP64 (x6, logw, alive).
+__global__ void export_fp64_kernel(StateF64 st, int64_t off, int64_t n, double* __restrict__ x6,
+                                   double* __restrict__ logw, uint8_t* __restrict__ alive) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t slot = off + i;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) x6[6 * i + d] = st.x[d * st.stride + slot];
+    const int sg = st.sgn[slot];
+    logw[i] = sg != 0 ? st.logw[slot] : -INFINITY;
+    alive[i] = sg != 0 ? 1 : 0;
+}
+
+__global__ void export_mixed_kernel(StateMixed st, int64_t off, int64_t n, double* __restrict__ x6,
+                                    double* __restrict__ logw, uint8_t* __restrict__ alive) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t slot = off + i;
+    const float4 a = st.p0[slot];
+    const float4 b = st.p1[slot];
+    x6[6 * i + 0] = a.x; x6[6 * i + 1] = a.y; x6[6 * i + 2] = a.z;
+    x6[6 * i + 3] = a.w; x6[6 * i + 4] = b.x; x6[6 * i + 5] = b.y;
+    const long long lo = (unsigned)__float_as_int(b.z);
+    const long long hi = (long long)__float_as_int(b.w);
+    const int sg = st.sgn[slot];
+    logw[i] = sg != 0 ? __longlong_as_double((hi << 32) | lo) : -INFINITY;
+    alive[i] = sg != 0 ? 1 : 0;
+}
+
+cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
+                               SeriesRow* series, int64_t series_cap, int64_t row_base,
+                               cudaStream_t stream) {
+    dim3 grid(rows, bm.n_inst);
+    reduce_rows_kernel<<<grid, kReduceThreads, 0, stream>>>(part, nblk, bm, series, series_cap,
+                                                             row_base);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const SeriesRow* rows, int64_t n, double n0, double* e, double* lnz,
+                            double* ess, cudaStream_t stream) {
+    const int th = 256;
+    const int nb = (int)((n + th - 1) / th);
+    finalize_kernel<<<nb, th, 0, stream>>>(rows, n, n0, e, lnz, ess);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(bool mixed, const StateF64& s64, const StateMixed& smx, int64_t off,
+                          int64_t n, double* x6, double* logw, uint8_t* alive,
+                          cudaStream_t stream) {
+    const int th = 256;
+    const int nb = (int)((n + th - 1) / th);
+    if (mixed) export_mixed_kernel<<<nb, th, 0, stream>>>(smx, off, n, x6, logw, alive);
+    else export_fp64_kernel<<<nb, th, 0, stream>>>(s64, off, n, x6, logw, alive);
+    return cudaGetLastError();
+}
+
+}  // namespace gfk

@@ -1,0 +1,77 @@
+// Plain structs shared by the host launch code and the kernels of the GFK
+// library (device memory layouts and kernel arguments).
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/gfk.h"
+
+namespace gfk {
+
+// Trial function in FP64 as given by the caller (see gfk_set_trial).
+struct TrialHost {
+    int32_t kind;       // gfk_trial_kind
+    int32_t nterms;     // kind 1: number of orbital-pair terms
+    double Z;           // kind 0: orbital exponent
+    double a, beta;     // Jastrow a rho + sum c_k rho^{k+1}, rho = r/(1+beta r)
+    double ck[4];
+    double s[GFK_MAX_TERMS];                 // kind 1: term signs / weights
+    double alpha[GFK_MAX_TERMS][2];          // [term][electron]
+    double c0[GFK_MAX_TERMS][2];
+    double c1[GFK_MAX_TERMS][2];
+    double cz[GFK_MAX_TERMS][2];
+};
+
+// One instance as the kernels see it.
+struct InstDev {
+    int64_t n;          // walkers
+    int64_t off;        // first slot of this instance in the state planes
+    double dt, sqrt_dt, e_trial, sigma;
+    uint32_t k0, k1;    // Philox key = seed
+    uint32_t stream;    // third Philox counter word
+    int32_t ee_on;
+    TrialHost trial;
+};
+
+// Block ranges per instance for one launch shape (passed by value).
+struct BlockMap {
+    int32_t n_inst;
+    int32_t wpt;                        // walkers per thread
+    int32_t begin[GFK_MAX_INSTANCES + 1];
+};
+
+// Population sums of one block for one step, relative to the block's shift c:
+// W = sum e^{logw - c}, P = sum w E_L, Q = sum w^2, R = sum w E_L^2, n = alive.
+struct PartialRec {
+    double c, W, P, Q, R, n;
+};
+
+// Per-step population sums of one instance (same fields, merged over blocks).
+typedef PartialRec SeriesRow;
+
+// FP64 walker state, structure of arrays over slots.
+struct StateF64 {
+    double* x;          // 6 planes of `stride` doubles: x1, y1, z1, x2, y2, z2
+    double* logw;       // -inf for dead walkers
+    int8_t* sgn;        // sign of psi at the start; 0 = dead
+    int64_t stride;
+};
+
+// Mixed-precision walker state: two float4 planes per slot,
+// p0 = (x1, y1, z1, x2), p1 = (y2, z2, logw bits low, logw bits high).
+struct StateMixed {
+    float4* p0;
+    float4* p1;
+    int8_t* sgn;
+};
+
+// Steps between flushes of the per-step block sums; also the mixed path's
+// fold period of the FP32 log-weight increments into the FP64 base.
+constexpr int kRing = 16;
+constexpr int kMaxThreads = 512;
+constexpr int kMaxWarps = kMaxThreads / 32;
+
+// Counters per instance: [0] non-finite kills, [1] node kills, [2] coalescences.
+constexpr int kNumCounters = 3;
+
+}  // namespace gfk

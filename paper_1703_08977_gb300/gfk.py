@@ -1,0 +1,329 @@
+"""Python binding of the GFK walker library (``include/gfk.h``), by ctypes.
+
+Argument marshalling only: every step of the walk runs in the CUDA kernels of
+``libgfk.so``.  The functions below carry the C names; ``Context`` wraps them
+for convenience.  PyTorch is used only to hand the library the current CUDA
+stream.  If the library cannot be built or loaded the import of any entry
+point raises: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+# enums of include/gfk.h
+GFK_OK, GFK_EINVAL, GFK_ENOMEM, GFK_ECUDA, GFK_ESTATE, GFK_ENONFINITE, GFK_EOVERFLOW, \
+    GFK_ETIMEOUT = range(8)
+GFK_1S, GFK_2S3, GFK_PZ = 0, 1, 2
+GFK_PREC_FP64, GFK_PREC_MIXED = 0, 1
+GFK_TRIAL_JASTROW_PRODUCT, GFK_TRIAL_ORBITAL_PAIRS = 0, 1
+GFK_MAX_TERMS = 4
+GFK_MAX_INSTANCES = 64
+
+# every entry point the header declares
+EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gfk_steps",
+           "gfk_energy", "gfk_sums", "gfk_get_walkers", "gfk_counters", "gfk_checkpoint_size",
+           "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
+           "gfk_destroy", "gfk_status_string", "gfk_last_error")
+
+
+class gfk_instance_desc(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("n_walkers", ctypes.c_int64), ("dt", ctypes.c_double),
+                ("e_trial", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("rng_stream", ctypes.c_uint32), ("ee_on", ctypes.c_int32),
+                ("init_sigma", ctypes.c_double)]
+
+
+class GfkError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        msg = f"{where}: {status_string(status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libgfk.so (building it in-tree first if sources changed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgfk.so missing at {path}; build it with "
+                               "python -m paper_1703_08977_gb300.build")
+        lib = ctypes.CDLL(path)
+        c = ctypes
+        P = c.c_void_p
+        dp = c.POINTER(c.c_double)
+        sig = {
+            "gfk_create": ([c.POINTER(gfk_instance_desc), c.c_int32, P, c.POINTER(P)], c.c_int),
+            "gfk_set_trial": ([P, c.c_int32, c.c_int32, dp, c.c_int32], c.c_int),
+            "gfk_set_launch": ([P, c.c_int32, c.c_int32], c.c_int),
+            "gfk_propagate": ([P, c.c_int64], c.c_int),
+            "gfk_steps": ([P, c.POINTER(c.c_int64)], c.c_int),
+            "gfk_energy": ([P, c.c_int32, dp, dp, dp, c.c_int64, dp], c.c_int),
+            "gfk_sums": ([P, c.c_int32, dp, c.c_int64], c.c_int),
+            "gfk_get_walkers": ([P, c.c_int32, dp, dp, c.POINTER(c.c_uint8)], c.c_int),
+            "gfk_counters": ([P, c.c_int32, c.POINTER(c.c_int64)], c.c_int),
+            "gfk_checkpoint_size": ([P, c.POINTER(c.c_int64)], c.c_int),
+            "gfk_checkpoint": ([P, P, c.c_int64], c.c_int),
+            "gfk_restore": ([P, P, c.c_int64], c.c_int),
+            "gfk_profile": ([P, c.c_int32], c.c_int),
+            "gfk_profile_read": ([P, dp, c.POINTER(c.c_int64), dp, c.c_int32], c.c_int),
+            "gfk_reset": ([P], c.c_int),
+            "gfk_destroy": ([P], None),
+            "gfk_status_string": ([c.c_int], c.c_char_p),
+            "gfk_last_error": ([P], c.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def status_string(status: int) -> str:
+    return load().gfk_status_string(int(status)).decode()
+
+
+def gfk_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def gfk_last_error(ctx) -> str:
+    return load().gfk_last_error(ctx).decode()
+
+
+def _check(status, where, ctx=None, ok=(GFK_OK,)):
+    if status not in ok:
+        raise GfkError(status, where, gfk_last_error(ctx) if ctx else "")
+    return status
+
+
+def _current_stream_ptr():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the GFK library needs a CUDA GPU")
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ----------------------------------------------------------------------------
+# Entry points with the C names (host arrays are numpy).
+# ----------------------------------------------------------------------------
+def gfk_create(descs, stream=None):
+    """descs: sequence of gfk_instance_desc (or InstanceDesc); returns the ctx handle."""
+    lib = load()
+    arr = (gfk_instance_desc * len(descs))(*[d.c() if isinstance(d, InstanceDesc) else d
+                                             for d in descs])
+    if stream is None:
+        stream = _current_stream_ptr()
+    out = ctypes.c_void_p()
+    _check(lib.gfk_create(arr, len(descs), stream, ctypes.byref(out)), "gfk_create")
+    return out
+
+
+def gfk_set_trial(ctx, inst, kind, params):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    _check(load().gfk_set_trial(ctx, int(inst), int(kind), _dp(p), len(p)), "gfk_set_trial", ctx)
+
+
+def gfk_set_launch(ctx, threads_per_block, walkers_per_thread):
+    _check(load().gfk_set_launch(ctx, int(threads_per_block), int(walkers_per_thread)),
+           "gfk_set_launch", ctx)
+
+
+def gfk_propagate(ctx, n_steps):
+    _check(load().gfk_propagate(ctx, int(n_steps)), "gfk_propagate", ctx)
+
+
+def gfk_steps(ctx) -> int:
+    v = ctypes.c_int64()
+    _check(load().gfk_steps(ctx, ctypes.byref(v)), "gfk_steps", ctx)
+    return v.value
+
+
+def gfk_energy(ctx, inst, cap=None, out=None):
+    """Returns (e_mixed, ln_z, ess, e_final, status); status may be GFK_ENONFINITE."""
+    n = gfk_steps(ctx) + 1
+    cap = n if cap is None else int(cap)
+    if out is None:
+        e, lz, es = np.empty(cap), np.empty(cap), np.empty(cap)
+    else:
+        e, lz, es = out
+    ef = ctypes.c_double()
+    st = load().gfk_energy(ctx, int(inst), _dp(e), _dp(lz), _dp(es), cap, ctypes.byref(ef))
+    _check(st, "gfk_energy", ctx, ok=(GFK_OK, GFK_ENONFINITE))
+    return e[:n], lz[:n], es[:n], ef.value, st
+
+
+def gfk_sums(ctx, inst):
+    n = gfk_steps(ctx) + 1
+    rows = np.empty((n, 6))
+    _check(load().gfk_sums(ctx, int(inst), _dp(rows), n), "gfk_sums", ctx)
+    return rows
+
+
+def gfk_get_walkers(ctx, inst, n_walkers):
+    x = np.empty((int(n_walkers), 6))
+    lw = np.empty(int(n_walkers))
+    al = np.empty(int(n_walkers), dtype=np.uint8)
+    _check(load().gfk_get_walkers(ctx, int(inst), _dp(x), _dp(lw),
+                                  al.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+           "gfk_get_walkers", ctx)
+    return x, lw, al
+
+
+def gfk_counters(ctx, inst):
+    c = np.zeros(3, dtype=np.int64)
+    _check(load().gfk_counters(ctx, int(inst), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+           "gfk_counters", ctx)
+    return c
+
+
+def gfk_checkpoint_size(ctx) -> int:
+    v = ctypes.c_int64()
+    _check(load().gfk_checkpoint_size(ctx, ctypes.byref(v)), "gfk_checkpoint_size", ctx)
+    return v.value
+
+
+def gfk_checkpoint(ctx) -> bytes:
+    n = gfk_checkpoint_size(ctx)
+    buf = ctypes.create_string_buffer(n)
+    _check(load().gfk_checkpoint(ctx, ctypes.cast(buf, ctypes.c_void_p), n), "gfk_checkpoint", ctx)
+    return buf.raw
+
+
+def gfk_restore(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(load().gfk_restore(ctx, ctypes.cast(buf, ctypes.c_void_p), len(blob)), "gfk_restore", ctx)
+
+
+def gfk_profile(ctx, enable=True):
+    _check(load().gfk_profile(ctx, int(bool(enable))), "gfk_profile", ctx)
+
+
+def gfk_profile_read(ctx, reset=True):
+    """(summed walk-kernel ms, launches, walker-steps) since the last reset."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    ws = ctypes.c_double()
+    _check(load().gfk_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(ws),
+                                   int(bool(reset))), "gfk_profile_read", ctx)
+    return ms.value, n.value, ws.value
+
+
+def gfk_reset(ctx):
+    _check(load().gfk_reset(ctx), "gfk_reset", ctx)
+
+
+def gfk_destroy(ctx):
+    load().gfk_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------
+# Convenience wrapper
+# ----------------------------------------------------------------------------
+@dataclass
+class InstanceDesc:
+    n_walkers: int
+    dt: float
+    e_trial: float
+    seed: int = 0
+    state: int = GFK_1S
+    prec: int = GFK_PREC_FP64
+    rng_stream: int = 0
+    ee_on: int = 1
+    init_sigma: float = 0.5
+
+    def c(self) -> gfk_instance_desc:
+        return gfk_instance_desc(int(self.state), int(self.prec), int(self.n_walkers),
+                                 float(self.dt), float(self.e_trial), int(self.seed),
+                                 int(self.rng_stream), int(self.ee_on), float(self.init_sigma))
+
+
+class Context:
+    """Owns one gfk_ctx; instances are described by InstanceDesc."""
+
+    def __init__(self, descs, trials=None, stream=None, launch=None):
+        self.descs = list(descs)
+        self.handle = gfk_create(self.descs, stream)
+        if trials is not None:
+            for i, (kind, params) in enumerate(trials):
+                gfk_set_trial(self.handle, i, kind, params)
+        if launch is not None:
+            gfk_set_launch(self.handle, *launch)
+
+    def set_trial(self, inst, kind, params):
+        gfk_set_trial(self.handle, inst, kind, params)
+
+    def set_launch(self, threads, wpt):
+        gfk_set_launch(self.handle, threads, wpt)
+
+    def propagate(self, n_steps):
+        gfk_propagate(self.handle, n_steps)
+        return self
+
+    @property
+    def steps(self):
+        return gfk_steps(self.handle)
+
+    def energy(self, inst=0):
+        e, lz, es, ef, st = gfk_energy(self.handle, inst)
+        return {"E": e, "ln_z": lz, "ess": es, "e_final": ef, "status": st}
+
+    def sums(self, inst=0):
+        return gfk_sums(self.handle, inst)
+
+    def walkers(self, inst=0):
+        return gfk_get_walkers(self.handle, inst, self.descs[inst].n_walkers)
+
+    def counters(self, inst=0):
+        return gfk_counters(self.handle, inst)
+
+    def checkpoint(self):
+        return gfk_checkpoint(self.handle)
+
+    def restore(self, blob):
+        gfk_restore(self.handle, blob)
+
+    def reset(self):
+        gfk_reset(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            gfk_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,213 @@
+"""Parity of the CUDA walk with the FP64 oracle, through the C ABI (GPU).
+
+FP64 path: per walker |dX|_inf <= 1e-12 max(1, |X|_inf) and
+|dlogw| <= 1e-12 max(1, |logw|); per step |dE| <= 1e-13 |E|.  Walkers of the
+excited states that pass within 1e-6 bohr of the node are ill-conditioned
+(the drift there is ~1/distance, so one-ulp differences in exp() between the
+two libms are amplified); they are compared with a looser bound and counted.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1703_08977_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+REL_WALKER = 1e-12
+REL_E = 1e-13
+
+
+def _gpu_run(gfk, kind, params, n, steps, dt, et, seed, prec, stream_id=0, ee_on=1,
+             sigma=0.5, launch=None, state=0, chunks=None):
+    d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=et, seed=seed, prec=prec,
+                         rng_stream=stream_id, ee_on=ee_on, init_sigma=sigma, state=state)
+    ctx = gfk.Context([d], trials=[(kind, params)], launch=launch)
+    for c in (chunks or [steps]):
+        ctx.propagate(c)
+    x, lw, al = ctx.walkers(0)
+    out = dict(x=x, logw=lw, alive=al, sums=ctx.sums(0), energy=ctx.energy(0),
+               counters=ctx.counters(0))
+    ctx.close()
+    return out
+
+
+def _oracle_run(kind, params, n, steps, dt, et, seed, stream_id=0, ee_on=True, sigma=0.5, ids=None):
+    w = oracle.Walk(kind, params, n_walkers=None if ids is not None else n, ids=ids, dt=dt,
+                    e_trial=et, seed=seed, inst=stream_id, sigma=sigma, ee_on=ee_on)
+    w.advance(steps)
+    return w
+
+
+def _walker_errors(g, w):
+    a = w.alive.astype(bool)
+    np.testing.assert_array_equal(g["alive"].astype(bool), a)
+    dx = np.abs(g["x"] - w.x).max(axis=1) / np.maximum(1.0, np.abs(w.x).max(axis=1))
+    dl = np.zeros_like(dx)
+    dl[a] = np.abs(g["logw"][a] - w.logw[a]) / np.maximum(1.0, np.abs(w.logw[a]))
+    assert np.all(np.isneginf(g["logw"][~a]))
+    return dx, dl
+
+
+def test_fp64_ground_state_config_full(gfk_lib):
+    """He 1^1S, 4096 walkers, 2000 steps at dt = 0.01, E_T = -2.9, seed 0 (the FP64
+    correctness workload): every walker and every step of E(t) against the oracle."""
+    gfk = gfk_lib
+    p = wl.ground()
+    n, steps, dt, et = 4096, 2000, 0.01, -2.9
+    g = _gpu_run(gfk, 0, p, n, steps, dt, et, 0, gfk.GFK_PREC_FP64)
+    w = _oracle_run(0, p, n, steps, dt, et, 0)
+    dx, dl = _walker_errors(g, w)
+    assert dx.max() <= REL_WALKER, dx.max()
+    assert dl.max() <= REL_WALKER, dl.max()
+    s = w.series()
+    E = g["energy"]["E"]
+    assert len(E) == steps + 1
+    np.testing.assert_allclose(E, s["E"], rtol=REL_E, atol=0)
+    np.testing.assert_allclose(g["energy"]["ln_z"], s["ln_z"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(g["energy"]["ess"], s["ess"], rtol=1e-12)
+    assert abs(g["energy"]["e_final"] - s["E"][-1]) <= REL_E * abs(s["E"][-1])
+    np.testing.assert_array_equal(g["sums"][:, 5], s["n_alive"])
+    np.testing.assert_array_equal(g["counters"], w.counters)
+
+
+@pytest.mark.parametrize("name", ["triplet_2s3", "pz_plus", "fn3", "fn7", "ground_poly"])
+def test_fp64_trial_families_ragged(gfk_lib, name):
+    """Every trial family on a ragged population (several blocks plus a partial one),
+    300 steps, compared walker by walker; node kills must agree exactly."""
+    gfk = gfk_lib
+    kind, p, et = {
+        "triplet_2s3": (1, wl.triplet_2s3(), -2.175),
+        "pz_plus": (1, wl.pz_state(+1.0), -2.12),
+        "fn3": (1, wl.fn3(), -2.124),
+        "fn7": (1, wl.fn7(1.1, 1.9, a=0.5, beta=0.6), -2.06),
+        "ground_poly": (0, wl.ground(Z=1.85, a=0.5, beta=0.37, c=(0.11, -0.07, 0.05, 0.02)), -2.9),
+    }[name]
+    n, steps, dt, seed = 1000 + 37, 300, 0.01, 7
+    g = _gpu_run(gfk, kind, p, n, steps, dt, et, seed, gfk.GFK_PREC_FP64, stream_id=3)
+    w = _oracle_run(kind, p, n, steps, dt, et, seed, stream_id=3)
+    dx, dl = _walker_errors(g, w)
+    bad = (dx > REL_WALKER) | (dl > REL_WALKER)
+    # ill-conditioned walkers (near a node) may drift apart at the 1e-12 level; they
+    # must be rare and still agree to 1e-8
+    assert bad.sum() <= max(2, n // 200), (bad.sum(), dx.max(), dl.max())
+    assert dx.max() <= 1e-8 and dl.max() <= 1e-8, (dx.max(), dl.max())
+    s = w.series()
+    np.testing.assert_allclose(g["energy"]["E"], s["E"], rtol=1e-11, atol=0)
+    np.testing.assert_array_equal(g["sums"][:, 5], s["n_alive"])
+    np.testing.assert_array_equal(g["counters"][:2], w.counters[:2])
+
+
+def test_fp64_exact_eigenfunction(gfk_lib):
+    """No e-e repulsion and psi = exp(-2 r1 - 2 r2): E_L = -4 exactly, so with E_T = -3.5
+    every log-weight is 0.5 t and E(t) = -4 at every step."""
+    gfk = gfk_lib
+    g = _gpu_run(gfk, 0, wl.ground(a=0.0), 333, 200, 0.01, -3.5, 1, gfk.GFK_PREC_FP64, ee_on=0)
+    t = np.arange(201) * 0.01
+    np.testing.assert_allclose(g["energy"]["E"], -4.0, atol=1e-11, rtol=0)
+    np.testing.assert_allclose(g["energy"]["ln_z"], -0.5 * t, atol=1e-11, rtol=0)
+    np.testing.assert_allclose(g["logw"], -0.5 * 2.0, atol=1e-11)
+
+
+@pytest.mark.parametrize("threads", [64, 256, 512])
+def test_fp64_launch_shape_does_not_change_walkers(gfk_lib, threads):
+    gfk = gfk_lib
+    kw = dict(kind=0, params=wl.ground(), n=777, steps=64, dt=0.01, et=-2.9, seed=2,
+              prec=gfk.GFK_PREC_FP64)
+    a = _gpu_run(gfk, **kw, launch=(128, 1))
+    b = _gpu_run(gfk, **kw, launch=(threads, 1))
+    np.testing.assert_array_equal(a["x"], b["x"])
+    np.testing.assert_array_equal(a["logw"], b["logw"])
+    np.testing.assert_allclose(a["energy"]["E"], b["energy"]["E"], rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_resume_is_bitwise(gfk_lib, prec):
+    """Counter-based randomness: chunked propagation (multiples of 16 steps), and a
+    checkpoint restored into a fresh context, reproduce the uninterrupted run bit for bit."""
+    gfk = gfk_lib
+    p = wl.triplet_2s3()
+    d = gfk.InstanceDesc(n_walkers=3000, dt=0.01, e_trial=-2.17, seed=5, prec=prec)
+    one = gfk.Context([d], trials=[(1, p)]).propagate(96)
+    two = gfk.Context([d], trials=[(1, p)]).propagate(32).propagate(16)
+    blob = two.checkpoint()
+    three = gfk.Context([d], trials=[(1, p)])
+    three.restore(blob)
+    three.propagate(48)
+    two.propagate(48)
+    for c in (two, three):
+        for u, v in zip(one.walkers(), c.walkers()):
+            np.testing.assert_array_equal(u, v)
+        np.testing.assert_array_equal(one.sums(), c.sums())
+        np.testing.assert_array_equal(one.counters(), c.counters())
+    for c in (one, two, three):
+        c.close()
+
+
+def test_batched_instances_match_single_runs(gfk_lib):
+    """Instances batched in one context (different trial families, dt, sizes) give the
+    same walkers as each instance alone: randomness is keyed by (seed, rng_stream, id)."""
+    gfk = gfk_lib
+    specs = [(0, wl.ground(), 500, 0.01, -2.9, 0), (1, wl.triplet_2s3(), 333, 0.005, -2.17, 1),
+             (1, wl.pz_state(1.0), 129, 0.0025, -2.12, 2)]
+    descs = [gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=et, seed=11, rng_stream=s)
+             for (_, _, n, dt, et, s) in specs]
+    ctx = gfk.Context(descs, trials=[(k, p) for (k, p, *_) in specs]).propagate(80)
+    for i, (k, p, n, dt, et, s) in enumerate(specs):
+        g = _gpu_run(gfk, k, p, n, 80, dt, et, 11, 0, stream_id=s)
+        x, lw, al = ctx.walkers(i)
+        np.testing.assert_array_equal(x, g["x"])
+        np.testing.assert_array_equal(lw, g["logw"])
+        np.testing.assert_allclose(ctx.energy(i)["E"], g["energy"]["E"], rtol=1e-15, atol=0)
+    ctx.close()
+
+
+def test_mixed_path_tracks_fp64_oracle(gfk_lib):
+    """FP32 physics, FP64 weights: after 100 steps the walkers stay within FP32-level
+    distance of the oracle's FP64 trajectories (same random words), and E(t) within 1e-5."""
+    gfk = gfk_lib
+    p = wl.ground()
+    n, steps = 2048 + 11, 100
+    g = _gpu_run(gfk, 0, p, n, steps, 0.01, -2.9, 3, gfk.GFK_PREC_MIXED, launch=(256, 2))
+    w = _oracle_run(0, p, n, steps, 0.01, -2.9, 3)
+    np.testing.assert_array_equal(g["alive"], w.alive)
+    dx = np.abs(g["x"] - w.x).max(axis=1)
+    assert np.median(dx) < 1e-5 and np.quantile(dx, 0.99) < 1e-3, (np.median(dx), dx.max())
+    dl = np.abs(g["logw"] - w.logw)
+    assert np.median(dl) < 1e-5, np.median(dl)
+    s = w.series()
+    assert np.max(np.abs(g["energy"]["E"] - s["E"])) < 1e-4
+
+
+def test_edge_cases(gfk_lib):
+    gfk = gfk_lib
+    # a single walker; zero-step propagate initialises only
+    g = _gpu_run(gfk, 0, wl.ground(), 1, 0, 0.01, -2.9, 0, 0)
+    w = _oracle_run(0, wl.ground(), 1, 0, 0.01, -2.9, 0)
+    assert len(g["energy"]["E"]) == 1
+    np.testing.assert_allclose(g["x"], w.x, rtol=1e-15)
+    # state errors
+    d = gfk.InstanceDesc(n_walkers=10, dt=0.01, e_trial=-2.9)
+    ctx = gfk.Context([d])
+    with pytest.raises(gfk.GfkError) as e:
+        ctx.propagate(1)          # no trial function yet
+    assert e.value.status == gfk.GFK_ESTATE
+    ctx.set_trial(0, 0, wl.ground())
+    ctx.propagate(5)
+    with pytest.raises(gfk.GfkError) as e:
+        ctx.set_trial(0, 0, wl.ground())
+    assert e.value.status == gfk.GFK_ESTATE
+    with pytest.raises(gfk.GfkError) as e:
+        gfk.gfk_energy(ctx.handle, 0, cap=3)
+    assert e.value.status == gfk.GFK_EOVERFLOW
+    with pytest.raises(gfk.GfkError):
+        ctx.set_launch(100, 1)
+    with pytest.raises(gfk.GfkError):
+        ctx.set_trial(0, 1, wl.triplet_2s3()[:-1])
+    ctx.reset()
+    ctx.set_trial(0, 1, wl.triplet_2s3())
+    ctx.propagate(3)
+    assert ctx.steps == 3
+    ctx.close()
