@@ -318,6 +318,24 @@ def run_ours(args):
     return out
 
 
+def profile_case(args):
+    """A small case for ncu captures: 2^22 walkers (state 128 MB, > L2) advanced 64
+    moves per launch on the mixed path (or the FP64 path with --prec 0)."""
+    import torch
+    from paper_1703_08977_gb300 import gfk
+    kind, params = TRIAL
+    n = 1 << 22 if args.prec == 1 else 1 << 20
+    d = gfk.InstanceDesc(n_walkers=n, dt=DT, e_trial=E_T, seed=SEED, prec=args.prec)
+    launch = (args.threads, args.wpt) if args.prec == 1 else (128, 1)
+    with gfk.Context([d], trials=[(kind, params)], launch=launch) as ctx:
+        ctx.propagate(64)
+        ctx.propagate(64)
+        torch.cuda.synchronize()
+        e = ctx.energy(0)["E"]
+    print(json.dumps({"profile_case": True, "walkers": n, "moves": 128, "prec": args.prec,
+                      "E_final": float(e[-1])}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -328,7 +346,13 @@ def main():
     ap.add_argument("--wpt", type=int, default=2)
     ap.add_argument("--fp64-moves", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the small ncu capture case instead of the benchmark")
+    ap.add_argument("--prec", type=int, default=1, help="profile case: 1 mixed, 0 FP64")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

@@ -93,8 +93,17 @@ __device__ __forceinline__ void normals6_f32(uint32_t walker, uint32_t step, uin
 // ---------------------------------------------------------------------------
 // Precision helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+// Distance and inverse distance from a squared distance.  FP32: one hardware
+// reciprocal square root.  FP64: the correctly rounded square root first (the
+// plain definition r = sqrt(x^2 + y^2 + z^2)), then its reciprocal.
+__device__ __forceinline__ void radius(float s, float& r, float& i) {
+    i = rsqrtf(s);
+    r = s * i;
+}
+__device__ __forceinline__ void radius(double s, double& r, double& i) {
+    r = sqrt(s);
+    i = 1.0 / r;
+}
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float expn(float x) { return __expf(x); }
@@ -195,8 +204,10 @@ __device__ __forceinline__ void eval_kind0(const TrialDev<R>& t, const R x[6], E
     R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
     R dx = x[0] - x[3], dy = x[1] - x[4], dz = x[2] - x[5];
     R s12 = dx * dx + dy * dy + dz * dz;
-    R i1 = rsq(s1), i2 = rsq(s2), i12 = rsq(s12);
-    R r12 = s12 * i12;
+    R r1, r2, r12, i1, i2, i12;
+    radius(s1, r1, i1);
+    radius(s2, r2, i2);
+    radius(s12, r12, i12);
     R ex = dx * i12, ey = dy * i12, ez = dz * i12;
     JastrowOut<R> j = jastrow(t, r12, i12);
     R h1x = x[0] * i1, h1y = x[1] * i1, h1z = x[2] * i1;
@@ -210,7 +221,6 @@ __device__ __forceinline__ void eval_kind0(const TrialDev<R>& t, const R x[6], E
     R proj = (h1x - h2x) * ex + (h1y - h2y) * ey + (h1z - h2z) * ez;
     o.el = t.Zm2 * (i1 + i2) - t.Z2 + j.jee - j.upp - j.up * j.up + t.Z * j.up * proj;
     o.sign = finite_(s1 + s2) ? 1 : 0;   // psi > 0 wherever X is finite
-    R r1 = s1 * i1, r2 = s2 * i2;
     o.rmin = fmin(fmin(r1, r2), r12);
 }
 
@@ -233,8 +243,10 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
     R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
     R dx = x[0] - x[3], dy = x[1] - x[4], dz = x[2] - x[5];
     R s12 = dx * dx + dy * dy + dz * dz;
-    R i1 = rsq(s1), i2 = rsq(s2), i12 = rsq(s12);
-    R r1 = s1 * i1, r2 = s2 * i2, r12 = s12 * i12;
+    R r1, r2, r12, i1, i2, i12;
+    radius(s1, r1, i1);
+    radius(s2, r2, i2);
+    radius(s12, r12, i12);
     R ex = dx * i12, ey = dy * i12, ez = dz * i12;
     R h1[3] = {x[0] * i1, x[1] * i1, x[2] * i1};
     R h2[3] = {x[3] * i2, x[4] * i2, x[5] * i2};
@@ -242,14 +254,29 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
     const R ir[2] = {i1, i2};
     const R zz[2] = {x[2], x[5]};
 
-    // largest exponent -(alphaA r1 + alphaB r2) over the terms
-    R emax = -(t.al[0][0] * r1 + t.al[0][1] * r2);
-    for (int k = 1; k < t.nterms; ++k) emax = fmax(emax, -(t.al[k][0] * r1 + t.al[k][1] * r2));
+    // FP32: the largest exponent -(alphaA r1 + alphaB r2) over the terms is
+    // factored out so no term underflows.  FP64 has the range to evaluate each
+    // orbital's exponential as it stands, which keeps the sign of Phi (the node
+    // test) computed exactly as the plain sum of products s f_A f_B.
+    constexpr bool kF64 = sizeof(R) == 8;
+    R emax = R(0);
+    if (!kF64) {
+        emax = -(t.al[0][0] * r1 + t.al[0][1] * r2);
+        for (int k = 1; k < t.nterms; ++k)
+            emax = fmax(emax, -(t.al[k][0] * r1 + t.al[k][1] * r2));
+    }
 
     R Phi = R(0), T = R(0);
     R G1[3] = {R(0), R(0), R(0)}, G2[3] = {R(0), R(0), R(0)};
     for (int k = 0; k < t.nterms; ++k) {
-        R g = expn(-(t.al[k][0] * r1 + t.al[k][1] * r2) - emax);
+        R gA = R(1), gB = R(1), g;
+        if (kF64) {
+            gA = expn(-t.al[k][0] * r1);
+            gB = expn(-t.al[k][1] * r2);
+            g = gA * gB;
+        } else {
+            g = expn(-(t.al[k][0] * r1 + t.al[k][1] * r2) - emax);
+        }
         R p[2], K[2], gr[2][3];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
@@ -265,7 +292,8 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
             p[e] = pe;
         }
         R sg = t.s[k] * g;
-        Phi += sg * p[0] * p[1];
+        if (kF64) Phi += t.s[k] * (p[0] * gA) * (p[1] * gB);
+        else Phi += sg * p[0] * p[1];
         T += sg * (K[0] * p[1] + p[0] * K[1]);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {

@@ -107,8 +107,9 @@ def test_fp64_exact_eigenfunction(gfk_lib):
     g = _gpu_run(gfk, 0, wl.ground(a=0.0), 333, 200, 0.01, -3.5, 1, gfk.GFK_PREC_FP64, ee_on=0)
     t = np.arange(201) * 0.01
     np.testing.assert_allclose(g["energy"]["E"], -4.0, atol=1e-11, rtol=0)
-    np.testing.assert_allclose(g["energy"]["ln_z"], -0.5 * t, atol=1e-11, rtol=0)
-    np.testing.assert_allclose(g["logw"], -0.5 * 2.0, atol=1e-11)
+    # logw = -(E_L - E_T) t = -(-4 + 3.5) t = +0.5 t
+    np.testing.assert_allclose(g["energy"]["ln_z"], 0.5 * t, atol=1e-11, rtol=0)
+    np.testing.assert_allclose(g["logw"], 0.5 * 2.0, atol=1e-11)
 
 
 @pytest.mark.parametrize("threads", [64, 256, 512])
