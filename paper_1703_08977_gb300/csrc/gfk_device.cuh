@@ -65,22 +65,24 @@ __device__ __forceinline__ void normals6_f64(uint32_t walker, uint32_t step, uin
     }
 }
 
-// FP32: the same words, u = ((w >> 8) + 1/2) 2^-24 (exact in FP32), the hardware
-// log2 / reciprocal square root / sine / cosine.  The angle is taken as
-// 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine are most
-// accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
+// FP32: the same words, u = ((w >> 9) + 1/2) 2^-23.  k + 1/2 with k < 2^23 needs
+// 24 significant bits, so u is exact in FP32 and lies strictly inside (0, 1)
+// (with 24 bits, (2^24 - 1 + 1/2) 2^-24 would round to 1 and log u to 0).
+// Then the hardware log2 / reciprocal square root / sine / cosine.  The angle
+// is taken as 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine
+// are most accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
 __device__ __forceinline__ void normals6_f32(uint32_t walker, uint32_t step, uint32_t stream,
                                              uint32_t k0, uint32_t k1, float xi[6]) {
     Words4 a = philox10(walker, step, stream, 0u, k0, k1);
     Words4 b = philox10(walker, step, stream, 1u, k0, k1);
     const uint32_t w[6] = {a.w[0], a.w[1], a.w[2], a.w[3], b.w[0], b.w[1]};
-    constexpr float kInv24 = 1.0f / 16777216.0f;
+    constexpr float kInv23 = 1.0f / 8388608.0f;
     constexpr float kMinus2Ln2 = -1.3862943611198906f;   // -2 ln 2
     constexpr float kTwoPi = 6.2831853071795865f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        float ua = ((float)(w[2 * j] >> 8) + 0.5f) * kInv24;
-        float ubc = ((float)(w[2 * j + 1] >> 8) + 0.5f) * kInv24 - 0.5f;   // exact
+        float ua = ((float)(w[2 * j] >> 9) + 0.5f) * kInv23;
+        float ubc = ((float)(w[2 * j + 1] >> 9) + 0.5f) * kInv23 - 0.5f;   // exact
         float r2 = kMinus2Ln2 * __log2f(ua);                               // -2 ln u > 0
         float rho = r2 * rsqrtf(r2);
         float s, c;

@@ -182,6 +182,22 @@ def test_mixed_path_tracks_fp64_oracle(gfk_lib):
     assert np.max(np.abs(g["energy"]["E"] - s["E"])) < 1e-4
 
 
+def test_mixed_normals_never_degenerate(gfk_lib):
+    """The FP32 uniforms stay strictly inside (0, 1): over 2^20 walkers x 48 moves
+    (3 x 1.5e8 Box-Muller radii) no ground-state walker is killed for a non-finite
+    drift or local energy, and every position stays finite."""
+    gfk = gfk_lib
+    d = gfk.InstanceDesc(n_walkers=1 << 20, dt=0.005, e_trial=-2.9, seed=1, prec=1)
+    with gfk.Context([d], trials=[(0, wl.ground())]) as ctx:
+        ctx.propagate(48)
+        c = ctx.counters(0)
+        x, lw, al = ctx.walkers(0)
+        st = ctx.energy(0)["status"]
+    assert c[0] == 0 and c[1] == 0, c
+    assert al.all() and np.isfinite(x).all() and np.isfinite(lw).all()
+    assert st == gfk.GFK_OK
+
+
 def test_edge_cases(gfk_lib):
     gfk = gfk_lib
     # a single walker; zero-step propagate initialises only
