@@ -185,6 +185,45 @@ gfk_status gfk_profile(gfk_ctx* ctx, int32_t enable);
 gfk_status gfk_profile_read(gfk_ctx* ctx, double* walk_ms, int64_t* launches,
                             double* walker_steps, int32_t reset);
 
+/* Allocation-free variant of the mixed-precision walk (the paper has no
+ * counterpart: this is a service to callers that cannot let a library call
+ * cudaMalloc -- frameworks that own all device memory through their own
+ * caching allocator or an arena reserved at start-up, and processes with a
+ * fixed memory budget, for whom a cudaMalloc would synchronise the device,
+ * could fail mid-run and fragments memory).
+ *
+ * Runs the same init / walk / merge kernels as gfk_propagate on one instance
+ * (desc->prec must be GFK_PREC_MIXED), with a fixed launch shape of 256
+ * threads x 2 walkers per thread, on memory the caller provides:
+ *   dev_p0, dev_p1  device float4[n_walkers] each (16-byte aligned): the
+ *                   walker planes p0 = (x1,y1,z1,x2), p1 = (y2,z2, log-weight as
+ *                   two 32-bit halves); written when init != 0, read and
+ *                   written otherwise
+ *   dev_sgn         device int8[n_walkers]: sign of psi at the start, 0 = dead
+ *   dev_rows        device double[(n_steps + (init ? 1 : 0)) * 6]: per-step sums
+ *                   {c, W, P, Q, R, n_alive} as in gfk_sums; row 0 is the initial
+ *                   population when init != 0
+ *   dev_counters    device uint64[3]: the counters of gfk_counters; zeroed by
+ *                   the call when init != 0, accumulated otherwise
+ * step0 is the global step of the first move (0 when init != 0).  The call is
+ * asynchronous on cuda_stream (NULL = legacy default stream).
+ * It allocates nothing.  Its only other device memory is a file-scope array of
+ * GFK_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits; the first call on each device looks up that array's
+ * address (make this first call before any stream capture).  All calls share
+ * the array, so calls that overlap on the GPU race; each call rewrites what it
+ * reads.  Returns GFK_EINVAL for n_walkers above GFK_NOALLOC_MAX_WALKERS (the
+ * most whose per-move records fit the array, 16 moves at a time) or any other
+ * bad argument, GFK_ECUDA if a launch or copy fails. */
+#define GFK_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define GFK_NOALLOC_MAX_WALKERS (1ll << 23)
+gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32_t trial_kind,
+                                 const double* params, int32_t n_params,
+                                 void* dev_p0, void* dev_p1, int8_t* dev_sgn,
+                                 int32_t init, int64_t step0, int64_t n_steps,
+                                 double* dev_rows, unsigned long long* dev_counters,
+                                 void* cuda_stream);
+
 /* Forget the population: the next gfk_propagate re-initialises it (step 0). */
 gfk_status gfk_reset(gfk_ctx* ctx);
 

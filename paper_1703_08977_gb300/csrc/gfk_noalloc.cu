@@ -1,0 +1,202 @@
+// gfk_propagate_noalloc: the mixed-precision walk without any allocation.
+//
+// Some callers cannot let a library call cudaMalloc: frameworks that own all
+// device memory through their own caching allocator or a fixed arena carved
+// out at start-up, and services whose memory budget is fixed for the life of
+// the process (cudaMalloc synchronises the device, can fail mid-run and
+// fragments memory).  This entry point serves them.  The caller passes every
+// input and output buffer; the only other device memory used is the
+// file-scope array below, which the CUDA runtime creates when the library is
+// loaded and every GPU that loads the library holds until the process exits.
+//
+// The array holds the instance record and the per-(move, block) population
+// records of one chunk of moves (the scratch the walk kernel writes and the
+// merge kernel reads).  Every call shares it, and it keeps the last call's
+// contents: each call rewrites the instance record and every record it later
+// reads, so nothing in it has to start at zero.  Calls whose work overlaps on
+// the GPU (two streams, or two host threads) race on it.
+//
+// The kernels launched are the library's own mixed init / walk / merge
+// kernels; only the memory they are given differs from gfk_propagate.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "gfk_types.h"
+
+namespace gfk {
+cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
+                              const BlockMap& bm, const StateMixed& st, PartialRec* part,
+                              unsigned long long* counters, cudaStream_t stream);
+cudaError_t launch_walk_mixed(int kind, int wpt, int threads, int nblk, const InstDev* insts,
+                              const BlockMap& bm, const StateMixed& st, uint32_t step0,
+                              int nsteps, PartialRec* part, unsigned long long* counters,
+                              cudaStream_t stream);
+cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
+                               SeriesRow* series, int64_t series_cap, int64_t row_base,
+                               cudaStream_t stream);
+}  // namespace gfk
+
+using namespace gfk;
+
+namespace {
+
+// The scratch.  Layout: [0, 4096) the InstDev record; [4096, end) PartialRec
+// records of one chunk, [move][block].
+constexpr size_t kHeaderBytes = 4096;
+static_assert(sizeof(InstDev) <= kHeaderBytes, "instance record must fit the header");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GFK_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kThreads = 256;   // launch shape of this entry point
+constexpr int kWpt = 2;
+
+// Device address of the scratch, looked up once per device with that device
+// current (in host code the symbol itself is only a host-side stand-in).
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {nullptr};
+
+gfk_status scratch_address(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= kMaxDevices) return GFK_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return GFK_ECUDA;
+        }
+        g_addr[dev] = p;
+    }
+    *out = (unsigned char*)g_addr[dev];
+    return GFK_OK;
+}
+
+bool parse_trial_noalloc(int kind, const double* p, int np, TrialHost* t) {
+    std::memset(t, 0, sizeof(*t));
+    if (!p) return false;
+    for (int i = 0; i < np; ++i)
+        if (!std::isfinite(p[i])) return false;
+    t->kind = kind;
+    if (kind == GFK_TRIAL_JASTROW_PRODUCT) {
+        if (np < 3 || np > 7) return false;
+        t->Z = p[0];
+        t->a = p[1];
+        t->beta = p[2];
+        for (int k = 0; k < 4; ++k) t->ck[k] = (3 + k < np) ? p[3 + k] : 0.0;
+        t->nterms = 1;
+        return t->Z > 0.0 && t->beta >= 0.0;
+    }
+    if (kind == GFK_TRIAL_ORBITAL_PAIRS) {
+        if (np < 7) return false;
+        t->a = p[0];
+        t->beta = p[1];
+        for (int k = 0; k < 4; ++k) t->ck[k] = p[2 + k];
+        const int nt = (int)p[6];
+        if ((double)nt != p[6] || nt < 1 || nt > GFK_MAX_TERMS || np != 7 + 9 * nt) return false;
+        if (t->beta < 0.0) return false;
+        t->nterms = nt;
+        for (int i = 0; i < nt; ++i) {
+            const double* q = p + 7 + 9 * i;
+            t->s[i] = q[0];
+            t->alpha[i][0] = q[1]; t->c0[i][0] = q[2]; t->c1[i][0] = q[3]; t->cz[i][0] = q[4];
+            t->alpha[i][1] = q[5]; t->c0[i][1] = q[6]; t->c1[i][1] = q[7]; t->cz[i][1] = q[8];
+            if (t->alpha[i][0] < 0.0 || t->alpha[i][1] < 0.0) return false;
+        }
+        return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32_t trial_kind,
+                                            const double* params, int32_t n_params,
+                                            void* dev_p0, void* dev_p1, int8_t* dev_sgn,
+                                            int32_t init, int64_t step0, int64_t n_steps,
+                                            double* dev_rows, unsigned long long* dev_counters,
+                                            void* cuda_stream) {
+    if (!desc || !dev_p0 || !dev_p1 || !dev_sgn || !dev_rows || !dev_counters) return GFK_EINVAL;
+    const gfk_instance_desc& d = *desc;
+    if (d.prec != GFK_PREC_MIXED) return GFK_EINVAL;
+    if (d.state < GFK_1S || d.state > GFK_PZ) return GFK_EINVAL;
+    if (d.n_walkers < 1 || d.n_walkers > GFK_NOALLOC_MAX_WALKERS) return GFK_EINVAL;
+    if (!(d.dt > 0.0) || !std::isfinite(d.dt) || !std::isfinite(d.e_trial)) return GFK_EINVAL;
+    if (!(d.init_sigma > 0.0) || !std::isfinite(d.init_sigma)) return GFK_EINVAL;
+    if (d.ee_on != 0 && d.ee_on != 1) return GFK_EINVAL;
+    if (n_steps < 0 || step0 < 0 || (init && step0 != 0)) return GFK_EINVAL;
+    if (step0 + n_steps > 0xffffffffll) return GFK_EINVAL;
+    if (((uintptr_t)dev_p0 | (uintptr_t)dev_p1) & 15u) return GFK_EINVAL;
+    TrialHost trial;
+    if (!parse_trial_noalloc(trial_kind, params, n_params, &trial)) return GFK_EINVAL;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GFK_ECUDA;
+    unsigned char* scratch = nullptr;
+    gfk_status st = scratch_address(dev, &scratch);
+    if (st != GFK_OK) return st;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    // instance record (host copy staged by the runtime before the call returns)
+    InstDev inst;
+    std::memset(&inst, 0, sizeof(inst));
+    inst.n = d.n_walkers;
+    inst.off = 0;
+    inst.dt = d.dt;
+    inst.sqrt_dt = std::sqrt(d.dt);
+    inst.e_trial = d.e_trial;
+    inst.sigma = d.init_sigma;
+    inst.k0 = (uint32_t)(d.seed & 0xffffffffull);
+    inst.k1 = (uint32_t)(d.seed >> 32);
+    inst.stream = d.rng_stream;
+    inst.ee_on = d.ee_on ? 1 : 0;
+    inst.trial = trial;
+    InstDev* d_inst = (InstDev*)scratch;
+    PartialRec* part = (PartialRec*)(scratch + kHeaderBytes);
+
+    BlockMap bm;
+    std::memset(&bm, 0, sizeof(bm));
+    bm.n_inst = 1;
+    bm.wpt = kWpt;
+    const int64_t per_block = (int64_t)kThreads * kWpt;
+    const int nblk = (int)((d.n_walkers + per_block - 1) / per_block);
+    bm.begin[0] = 0;
+    bm.begin[1] = nblk;
+    const int64_t rec_cap = (int64_t)((GFK_NOALLOC_SCRATCH_BYTES - kHeaderBytes) / sizeof(PartialRec));
+    int64_t rows_fit = rec_cap / nblk;
+    rows_fit = rows_fit > 1024 ? 1024 : (rows_fit / kRing) * kRing;
+    if (rows_fit < kRing) return GFK_EINVAL;   // cannot happen below GFK_NOALLOC_MAX_WALKERS
+
+    StateMixed sm;
+    sm.p0 = (float4*)dev_p0;
+    sm.p1 = (float4*)dev_p1;
+    sm.sgn = dev_sgn;
+    SeriesRow* rows = (SeriesRow*)dev_rows;
+    const int64_t n_rows = n_steps + (init ? 1 : 0);
+    const int kind = trial.kind;
+
+#define NA_CK(call)                                  \
+    do {                                             \
+        if ((call) != cudaSuccess) {                 \
+            (void)cudaGetLastError();                \
+            return GFK_ECUDA;                        \
+        }                                            \
+    } while (0)
+    NA_CK(cudaMemcpyAsync(d_inst, &inst, sizeof(inst), cudaMemcpyHostToDevice, stream));
+    if (init) {
+        NA_CK(cudaMemsetAsync(dev_counters, 0, sizeof(unsigned long long) * kNumCounters, stream));
+        NA_CK(launch_init_mixed(kind, kThreads, nblk, d_inst, bm, sm, part, dev_counters, stream));
+        NA_CK(launch_reduce_rows(part, nblk, bm, 1, rows, n_rows, 0, stream));
+    }
+    int64_t done = 0;
+    while (done < n_steps) {
+        const int chunk = (int)((n_steps - done) < rows_fit ? (n_steps - done) : rows_fit);
+        NA_CK(launch_walk_mixed(kind, kWpt, kThreads, nblk, d_inst, bm, sm,
+                                (uint32_t)(step0 + done), chunk, part, dev_counters, stream));
+        NA_CK(launch_reduce_rows(part, nblk, bm, chunk, rows, n_rows, (init ? 1 : 0) + done, stream));
+        done += chunk;
+    }
+#undef NA_CK
+    return GFK_OK;
+}

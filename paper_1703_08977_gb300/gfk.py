@@ -30,7 +30,9 @@ GFK_MAX_INSTANCES = 64
 EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gfk_steps",
            "gfk_energy", "gfk_sums", "gfk_get_walkers", "gfk_counters", "gfk_checkpoint_size",
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
-           "gfk_destroy", "gfk_status_string", "gfk_last_error")
+           "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc")
+GFK_NOALLOC_SCRATCH_BYTES = 16 << 20
+GFK_NOALLOC_MAX_WALKERS = 1 << 23
 
 
 class gfk_instance_desc(ctypes.Structure):
@@ -91,6 +93,9 @@ def load(build_if_needed: bool = True):
             "gfk_destroy": ([P], None),
             "gfk_status_string": ([c.c_int], c.c_char_p),
             "gfk_last_error": ([P], c.c_char_p),
+            "gfk_propagate_noalloc": ([c.POINTER(gfk_instance_desc), c.c_int32, dp, c.c_int32,
+                                       P, P, P, c.c_int32, c.c_int64, c.c_int64, P, P, P],
+                                      c.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -240,6 +245,21 @@ def gfk_reset(ctx):
 
 def gfk_destroy(ctx):
     load().gfk_destroy(ctx)
+
+
+def gfk_propagate_noalloc(desc, kind, params, p0, p1, sgn, init, step0, n_steps, rows, counters,
+                          stream=None):
+    """Allocation-free mixed walk on caller-provided device buffers (torch CUDA tensors:
+    p0, p1 float32 (n, 4); sgn int8 (n,); rows float64 (n_steps + init, 6); counters
+    int64 (3,)).  Passes their device addresses through unchanged; returns the status."""
+    d = desc.c() if isinstance(desc, InstanceDesc) else desc
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    if stream is None:
+        stream = _current_stream_ptr()
+    addr = lambda t: ctypes.c_void_p(t.data_ptr())
+    return load().gfk_propagate_noalloc(ctypes.byref(d), int(kind), _dp(p), len(p), addr(p0),
+                                        addr(p1), addr(sgn), int(init), int(step0),
+                                        int(n_steps), addr(rows), addr(counters), stream)
 
 
 # ----------------------------------------------------------------------------
