@@ -342,7 +342,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--wpt", type=int, default=2)
     ap.add_argument("--fp64-moves", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -53,7 +53,7 @@ typedef enum { GFK_1S = 0, GFK_2S3 = 1, GFK_PZ = 2 } gfk_state;
  * GFK_PREC_MIXED: positions, drift, local energy and random normals in FP32;
  *                 each walker's log-weight is an FP64 base plus an FP32
  *                 Kahan-compensated sum of increments folded into the base
- *                 every 16 steps; population sums go FP32 within a warp,
+ *                 every 32 steps; population sums go FP32 within a warp,
  *                 FP64 above it, compensated (TwoSum) across blocks. */
 typedef enum { GFK_PREC_FP64 = 0, GFK_PREC_MIXED = 1 } gfk_prec;
 
@@ -81,9 +81,10 @@ typedef enum { GFK_TRIAL_JASTROW_PRODUCT = 0, GFK_TRIAL_ORBITAL_PAIRS = 1 } gfk_
 /* One independent walk (an "instance"): the paper's statement of the problem
  * -- a symmetry, the trial energy E_T (the paper's lambda_0 of the trial
  * function), the time step dt, the number of replications N_rep and a seed.
- * Random numbers are Philox4x32-10 with counter (walker id, step, rng_stream,
- * tag) and key (seed low, seed high); the same (seed, rng_stream, walker id)
- * gives the same trajectory in any context and any launch configuration. */
+ * Random numbers are Philox4x32-10 with counter (walker id, m, rng_stream,
+ * tag) and key (seed low, seed high): moves 2m and 2m+1 take words 0-5 and
+ * 6-11 of the blocks with tags 0, 1, 2.  The same (seed, rng_stream, walker
+ * id) gives the same trajectory in any context and any launch configuration. */
 typedef struct {
     int32_t  state;          /* gfk_state                                         */
     int32_t  prec;           /* gfk_prec; all instances of a context share it     */
@@ -120,14 +121,14 @@ gfk_status gfk_set_launch(gfk_ctx* ctx, int32_t threads_per_block, int32_t walke
 
 /* Advance every instance by n_steps moves (asynchronous on the context's
  * stream).  The first call after gfk_create / gfk_reset initialises the
- * population (X0 = init_sigma * xi from Philox tags 2 and 3 at step 0,
+ * population (X0 = init_sigma * xi from the Philox blocks (id, 0, stream, 3/4),
  * log-weight 0) and records the step-0 population sums.  Each move is
  *   X <- X + b(X) dt + sqrt(dt) xi,   b = grad ln|psi|       (the SDE under Eq. 4)
  *   logw <- logw - (E_L(X) - E_T) dt, E_L = -Delta(psi)/(2 psi) + V
  * (the right-point Riemann sum of the Feynman-Kac exponent, Eq. 4), then the
  * fixed-node test, then the population sums of that step.
  * GFK_ESTATE if an instance has no trial function.  Step counts are
- * cumulative; a run interrupted and resumed at a multiple of 16 steps is
+ * cumulative; a run interrupted and resumed at a multiple of 32 steps is
  * bitwise identical to an uninterrupted one. */
 gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps);
 
@@ -170,7 +171,7 @@ gfk_status gfk_counters(gfk_ctx* ctx, int32_t inst, int64_t* host_counts3);
  * sums, counters) as an opaque host blob of gfk_checkpoint_size bytes.
  * gfk_restore loads a blob written by a context created with the same
  * descriptors and trial functions; resuming from it is bitwise identical to
- * never having stopped (when the step count is a multiple of 16).
+ * never having stopped (when the step count is a multiple of 32).
  * GFK_EINVAL if the blob does not match the context. */
 gfk_status gfk_checkpoint_size(gfk_ctx* ctx, int64_t* bytes);
 gfk_status gfk_checkpoint(gfk_ctx* ctx, void* host_blob, int64_t bytes);
@@ -213,16 +214,31 @@ gfk_status gfk_profile_read(gfk_ctx* ctx, double* walk_ms, int64_t* launches,
  * address (make this first call before any stream capture).  All calls share
  * the array, so calls that overlap on the GPU race; each call rewrites what it
  * reads.  Returns GFK_EINVAL for n_walkers above GFK_NOALLOC_MAX_WALKERS (the
- * most whose per-move records fit the array, 16 moves at a time) or any other
+ * most whose per-move records fit the array, 32 moves at a time) or any other
  * bad argument, GFK_ECUDA if a launch or copy fails. */
 #define GFK_NOALLOC_SCRATCH_BYTES (16u << 20)
-#define GFK_NOALLOC_MAX_WALKERS (1ll << 23)
+#define GFK_NOALLOC_MAX_WALKERS (1ll << 22)
 gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32_t trial_kind,
                                  const double* params, int32_t n_params,
                                  void* dev_p0, void* dev_p1, int8_t* dev_sgn,
                                  int32_t init, int64_t step0, int64_t n_steps,
                                  double* dev_rows, unsigned long long* dev_counters,
                                  void* cuda_stream);
+
+/* Instruction-throughput microbenchmarks (a measurement utility; the paper has
+ * no counterpart): the denominators of the walk kernels' ALU roofline,
+ * measured on the current device.  Each op runs independent chains of one
+ * PTX instruction on every SM; *lane_ops_per_s receives thread-level
+ * operations per second (one fma = one op; GFK_PEAK_IMAD_WIDE counts one
+ * mad.wide plus one xor per op; GFK_PEAK_F2F counts each of the two
+ * conversions of a float -> double -> float round trip).  Takes about 10 ms;
+ * synchronises cuda_stream; allocates 4 bytes from the stream-ordered pool. */
+typedef enum {
+    GFK_PEAK_FFMA = 0, GFK_PEAK_DFMA, GFK_PEAK_IMAD, GFK_PEAK_IMAD_HI, GFK_PEAK_IMAD_WIDE,
+    GFK_PEAK_LOP3, GFK_PEAK_EX2, GFK_PEAK_RSQ, GFK_PEAK_LG2, GFK_PEAK_SIN, GFK_PEAK_I2F,
+    GFK_PEAK_F2F, GFK_PEAK_COUNT
+} gfk_peak_op;
+gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* lane_ops_per_s);
 
 /* Forget the population: the next gfk_propagate re-initialises it (step 0). */
 gfk_status gfk_reset(gfk_ctx* ctx);

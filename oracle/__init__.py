@@ -10,7 +10,10 @@ module only compiles it (gcc, ``-ffp-contract=off``) and marshals arrays.
 Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
   philox4x32_10     pinned: an independent implementation (triton's Philox,
                     run by its CPU interpreter) agrees bitwise.
-  normals6          pinned: Kolmogorov-Smirnov and moment tests against N(0,1).
+  move_normals,
+  init_normals      pinned: Kolmogorov-Smirnov and moment tests against N(0,1), no
+                    correlation between components or between the two moves of
+                    one Philox pair index.
   trial_eval        pinned: closed-form eigenfunctions (E_L constant), 50-digit
                     finite differences of ln|psi|, exchange (anti)symmetry.
   run               pinned: exact weights for an exact eigenfunction, a
@@ -66,9 +69,10 @@ def _load():
         lib.orc_philox4x32_10.restype = None
         lib.orc_uniform.argtypes = [c.c_uint32]
         lib.orc_uniform.restype = c.c_double
-        lib.orc_normals6.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32,
-                                     c.c_uint32, dp]
-        lib.orc_normals6.restype = None
+        lib.orc_move_normals.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, dp]
+        lib.orc_move_normals.restype = None
+        lib.orc_init_normals.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, dp]
+        lib.orc_init_normals.restype = None
         lib.orc_trial_eval.argtypes = [c.c_int, dp, c.c_int, c.c_int, dp,
                                        c.POINTER(c.c_int), dp, dp, dp]
         lib.orc_trial_eval.restype = c.c_int
@@ -104,11 +108,18 @@ def uniform(word: int) -> float:
     return _load().orc_uniform(int(word))
 
 
-def normals6(seed: int, walker: int, step: int, inst: int, tag0: int = 0) -> np.ndarray:
-    """The six normals of (walker, step, inst) from Philox tags tag0, tag0+1."""
+def move_normals(seed: int, walker: int, step: int, inst: int) -> np.ndarray:
+    """The six normals of move `step` of walker `walker` (instance stream `inst`)."""
     out = np.zeros(6)
-    _load().orc_normals6(int(seed), int(walker), int(step), int(inst), int(tag0),
-                         _ptr(out, ctypes.c_double))
+    _load().orc_move_normals(int(seed), int(walker), int(step), int(inst),
+                             _ptr(out, ctypes.c_double))
+    return out
+
+
+def init_normals(seed: int, walker: int, inst: int) -> np.ndarray:
+    """The six normals that place walker `walker` initially (X0 = sigma * xi)."""
+    out = np.zeros(6)
+    _load().orc_init_normals(int(seed), int(walker), int(inst), _ptr(out, ctypes.c_double))
     return out
 
 

@@ -32,11 +32,13 @@
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3", SC'11) replaces the paper's Bernoulli
  * steps drawn from the "Superduper" congruential generator.  The counter is
- * (walker id, step, instance id, tag), the key the two halves of the 64-bit
- * seed.  Tags 0 and 1 give the 8 words of one move (6 used), tags 2 and 3 at
- * step 0 the initial positions.  Words map to uniforms u = (w + 1/2) 2^-32
- * and pairs of uniforms to normals by the Box-Muller transform
- * (Box and Muller 1958): xi = sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b).
+ * (walker id, pair index, instance id, tag), the key the two halves of the
+ * 64-bit seed.  Moves 2m and 2m+1 share the three blocks of pair index m,
+ * tags 0, 1, 2 (12 words): move 2m takes words 0-5, move 2m+1 words 6-11.
+ * The initial positions take the blocks of pair index 0 with tags 3 and 4
+ * (words 0-5).  Words map to uniforms u = (w + 1/2) 2^-32 and consecutive
+ * pairs of uniforms to normals by the Box-Muller transform (Box and Muller
+ * 1958): xi = sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b).
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused.
  */
@@ -96,21 +98,40 @@ static void orc_box_muller(uint32_t wa, uint32_t wb, double* xa, double* xb)
     *xb = rho * sin(ang);
 }
 
-/* Six standard normals for (walker, step, inst) from the Philox calls with
- * tags tag0 and tag0 + 1: words w0..w3 of the first call and w0..w3 of the
- * second form the pairs (w0,w1), (w2,w3), (w4,w5); w6, w7 are unused. */
-void orc_normals6(uint64_t seed, uint32_t walker, uint32_t step, uint32_t inst,
-                  uint32_t tag0, double xi[6])
+/* Six standard normals from six words: Box-Muller on (w0,w1), (w2,w3), (w4,w5). */
+static void orc_normals_from_words(const uint32_t w[6], double xi[6])
+{
+    orc_box_muller(w[0], w[1], &xi[0], &xi[1]);
+    orc_box_muller(w[2], w[3], &xi[2], &xi[3]);
+    orc_box_muller(w[4], w[5], &xi[4], &xi[5]);
+}
+
+/* The 12 words of pair index m: Philox blocks with tags 0, 1, 2. */
+static void orc_pair_words(uint64_t seed, uint32_t walker, uint32_t m, uint32_t inst,
+                           uint32_t tag0, uint32_t words[12])
 {
     uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
-    uint32_t ctr[4] = { walker, step, inst, tag0 };
-    uint32_t a[4], b[4];
-    orc_philox4x32_10(ctr, key, a);
-    ctr[3] = tag0 + 1u;
-    orc_philox4x32_10(ctr, key, b);
-    orc_box_muller(a[0], a[1], &xi[0], &xi[1]);
-    orc_box_muller(a[2], a[3], &xi[2], &xi[3]);
-    orc_box_muller(b[0], b[1], &xi[4], &xi[5]);
+    for (uint32_t t = 0; t < 3; ++t) {
+        uint32_t ctr[4] = { walker, m, inst, tag0 + t };
+        orc_philox4x32_10(ctr, key, words + 4 * t);
+    }
+}
+
+/* The six normals of move `step` (from global step `step` to step + 1). */
+void orc_move_normals(uint64_t seed, uint32_t walker, uint32_t step, uint32_t inst,
+                      double xi[6])
+{
+    uint32_t words[12];
+    orc_pair_words(seed, walker, step >> 1, inst, 0u, words);
+    orc_normals_from_words(words + 6 * (step & 1u), xi);
+}
+
+/* The six normals of the initial position: pair index 0, tags 3 and 4. */
+void orc_init_normals(uint64_t seed, uint32_t walker, uint32_t inst, double xi[6])
+{
+    uint32_t words[12];
+    orc_pair_words(seed, walker, 0u, inst, 3u, words);
+    orc_normals_from_words(words, xi);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -369,8 +390,8 @@ static void orc_population_sums(int64_t n, const double* logw, const double* el,
 /*
  * Run the walk for n walkers with ids ids[0..n) (NULL: ids 0..n-1).
  * State arrays (x: 6n, logw, el, alive, sgn) are read and written.
- *  - do_init != 0: first initialise every walker (X0 = sigma * xi from tags
- *    2/3 at step 0, logw = 0, alive = sign(psi(X0)) != 0 and finite) and write
+ *  - do_init != 0: first initialise every walker (X0 = sigma * xi from the
+ *    initial-position normals, logw = 0, alive = sign(psi(X0)) != 0 and finite) and write
  *    one stats row for the initial population (all weights 1).
  *  - then n_steps moves with global step counters step0 .. step0+n_steps-1,
  *    each followed by one stats row.
@@ -397,7 +418,7 @@ int orc_run(int kind, const double* params, int n_params, int ee_on,
         for (int64_t i = 0; i < n; ++i) {
             uint32_t id = ids ? ids[i] : (uint32_t)i;
             double xi[6];
-            orc_normals6(seed, id, 0u, inst, 2u, xi);
+            orc_init_normals(seed, id, inst, xi);
             double* xw = x + 6 * i;
             for (int d = 0; d < 6; ++d) xw[d] = sigma * xi[d];
             int s;
@@ -429,7 +450,7 @@ int orc_run(int kind, const double* params, int n_params, int ee_on,
             orc_eval(&t, ee_on, xw, &s0, b, &e0, &lp);
             /* Euler-Maruyama move X <- X + b dt + sqrt(dt) xi */
             double xi[6];
-            orc_normals6(seed, id, step, inst, 0u, xi);
+            orc_move_normals(seed, id, step, inst, xi);
             for (int d = 0; d < 6; ++d) xw[d] = xw[d] + b[d] * dt + sqrt_dt * xi[d];
             /* trial function at the new position */
             int s1;

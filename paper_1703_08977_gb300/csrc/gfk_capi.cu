@@ -465,7 +465,7 @@ gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_
     ctx->trial.assign(n_inst, TrialHost());
     ctx->has_trial.assign(n_inst, 0);
     ctx->stream = (cudaStream_t)cuda_stream;
-    ctx->threads = ctx->prec == GFK_PREC_FP64 ? 128 : 256;
+    ctx->threads = 128;
     ctx->wpt = ctx->prec == GFK_PREC_FP64 ? 1 : 2;
     int64_t o = 0;
     for (int i = 0; i < n_inst; ++i) {

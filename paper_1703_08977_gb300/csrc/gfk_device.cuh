@@ -40,18 +40,36 @@ __device__ __forceinline__ Words4 philox10(uint32_t c0, uint32_t c1, uint32_t c2
     return o;
 }
 
-// Six N(0,1) variates for one (walker, step): words 0..3 of the call with tag
-// `tag0` and words 0..1 of the call with tag0+1 form the Box-Muller pairs
-// (w0,w1), (w2,w3), (w4,w5); xi_a = sqrt(-2 ln u_a) cos(2 pi u_b),
-// xi_b = sqrt(-2 ln u_a) sin(2 pi u_b).
-//
+// Counter layout: moves 2m and 2m+1 of a walker share the three Philox blocks
+// (walker, m, stream, tag 0 / 1 / 2); move 2m takes words 0-5 of the twelve
+// (tag 0 words 0-3, tag 1 words 0-1), move 2m+1 words 6-11 (tag 1 words 2-3,
+// tag 2 words 0-3).  The initial position takes words 0-5 of the blocks
+// (walker, 0, stream, tag 3 / 4).
+__device__ __forceinline__ void move_words(uint32_t walker, uint32_t step, uint32_t stream,
+                                           uint32_t k0, uint32_t k1, uint32_t w[6]) {
+    const uint32_t m = step >> 1;
+    if ((step & 1u) == 0u) {
+        Words4 a = philox10(walker, m, stream, 0u, k0, k1);
+        Words4 b = philox10(walker, m, stream, 1u, k0, k1);
+        w[0] = a.w[0]; w[1] = a.w[1]; w[2] = a.w[2]; w[3] = a.w[3]; w[4] = b.w[0]; w[5] = b.w[1];
+    } else {
+        Words4 b = philox10(walker, m, stream, 1u, k0, k1);
+        Words4 c = philox10(walker, m, stream, 2u, k0, k1);
+        w[0] = b.w[2]; w[1] = b.w[3]; w[2] = c.w[0]; w[3] = c.w[1]; w[4] = c.w[2]; w[5] = c.w[3];
+    }
+}
+
+__device__ __forceinline__ void init_words(uint32_t walker, uint32_t stream, uint32_t k0,
+                                           uint32_t k1, uint32_t w[6]) {
+    Words4 a = philox10(walker, 0u, stream, 3u, k0, k1);
+    Words4 b = philox10(walker, 0u, stream, 4u, k0, k1);
+    w[0] = a.w[0]; w[1] = a.w[1]; w[2] = a.w[2]; w[3] = a.w[3]; w[4] = b.w[0]; w[5] = b.w[1];
+}
+
+// Six N(0,1) variates from six words: Box-Muller on (w0,w1), (w2,w3), (w4,w5),
+// xi_a = sqrt(-2 ln u_a) cos(2 pi u_b), xi_b = sqrt(-2 ln u_a) sin(2 pi u_b).
 // FP64: u = (w + 1/2) 2^-32 and library log/sqrt/sin/cos.
-__device__ __forceinline__ void normals6_f64(uint32_t walker, uint32_t step, uint32_t stream,
-                                             uint32_t tag0, uint32_t k0, uint32_t k1,
-                                             double xi[6]) {
-    Words4 a = philox10(walker, step, stream, tag0, k0, k1);
-    Words4 b = philox10(walker, step, stream, tag0 + 1u, k0, k1);
-    const uint32_t w[6] = {a.w[0], a.w[1], a.w[2], a.w[3], b.w[0], b.w[1]};
+__device__ __forceinline__ void normals6_f64(const uint32_t w[6], double xi[6]) {
     constexpr double kTwoPi = 6.283185307179586476925286766559;
     constexpr double kInv32 = 1.0 / 4294967296.0;
 #pragma unroll
@@ -65,24 +83,110 @@ __device__ __forceinline__ void normals6_f64(uint32_t walker, uint32_t step, uin
     }
 }
 
+// The Philox blocks of one walker share walker id and stream, so their first
+// round differs only in the pair index and the tag, and the blocks of tags 0
+// and 1 also share one product of their second round.  PhiloxPre holds the
+// first-round products that depend only on the walker id and the stream (with
+// the key words folded in).  philox10_pair gives the blocks of tags 0 and 1,
+// philox10_tag one block; both equal philox10 word for word.
+struct PhiloxPre {
+    uint32_t hiB_k0;    // umulhi(M_B, stream) ^ k0
+    uint32_t loB;       // M_B * stream
+    uint32_t hiA_k1;    // umulhi(M_A, walker) ^ k1
+    uint32_t loA;       // M_A * walker
+};
+
+__device__ __forceinline__ PhiloxPre philox_pre(uint32_t walker, uint32_t stream, uint32_t k0,
+                                                uint32_t k1) {
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    PhiloxPre p;
+    p.hiB_k0 = __umulhi(kMulB, stream) ^ k0;
+    p.loB = kMulB * stream;
+    p.hiA_k1 = __umulhi(kMulA, walker) ^ k1;
+    p.loA = kMulA * walker;
+    return p;
+}
+
+__device__ __forceinline__ Words4 philox10_tag(const PhiloxPre& p, uint32_t m, uint32_t tag,
+                                               uint32_t k0, uint32_t k1) {
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    constexpr uint32_t kBumpA = 0x9E3779B9u, kBumpB = 0xBB67AE85u;
+    // round 1 from the precomputed products: counters (walker, m, stream, tag)
+    uint32_t c0 = p.hiB_k0 ^ m, c1 = p.loB, c2 = p.hiA_k1 ^ tag, c3 = p.loA;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        k0 += kBumpA; k1 += kBumpB;
+        const uint32_t hA = __umulhi(kMulA, c0), lA = kMulA * c0;
+        const uint32_t hB = __umulhi(kMulB, c2), lB = kMulB * c2;
+        const uint32_t n0 = hB ^ c1 ^ k0, n2 = hA ^ c3 ^ k1;
+        c0 = n0; c1 = lB; c2 = n2; c3 = lA;
+    }
+    Words4 o;
+    o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+    return o;
+}
+
+__device__ __forceinline__ void philox10_pair(const PhiloxPre& p, uint32_t m, uint32_t k0,
+                                              uint32_t k1, Words4& a, Words4& b) {
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    constexpr uint32_t kBumpA = 0x9E3779B9u, kBumpB = 0xBB67AE85u;
+    // round 1 (key k0, k1): counters (walker, m, stream, tag)
+    const uint32_t r1c0 = p.hiB_k0 ^ m;          // shared
+    const uint32_t r1c1 = p.loB;                 // shared
+    uint32_t a2 = p.hiA_k1;                      // tag 0
+    uint32_t b2 = p.hiA_k1 ^ 1u;                 // tag 1
+    const uint32_t r1c3 = p.loA;                 // shared
+    // round 2 (key + 1 bump)
+    k0 += kBumpA; k1 += kBumpB;
+    const uint32_t hiA = __umulhi(kMulA, r1c0), loA = kMulA * r1c0;     // shared
+    const uint32_t n2 = hiA ^ r1c3 ^ k1;                                  // shared
+    uint32_t ac0, ac1, ac2 = n2, ac3 = loA;
+    uint32_t bc0, bc1, bc2 = n2, bc3 = loA;
+    {
+        uint32_t hiB = __umulhi(kMulB, a2), loB = kMulB * a2;
+        ac0 = hiB ^ r1c1 ^ k0;
+        ac1 = loB;
+        hiB = __umulhi(kMulB, b2);
+        loB = kMulB * b2;
+        bc0 = hiB ^ r1c1 ^ k0;
+        bc1 = loB;
+    }
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        k0 += kBumpA; k1 += kBumpB;
+        uint32_t hA = __umulhi(kMulA, ac0), lA = kMulA * ac0;
+        uint32_t hB = __umulhi(kMulB, ac2), lB = kMulB * ac2;
+        uint32_t n0a = hB ^ ac1 ^ k0, n2a = hA ^ ac3 ^ k1;
+        ac0 = n0a; ac1 = lB; ac2 = n2a; ac3 = lA;
+        hA = __umulhi(kMulA, bc0); lA = kMulA * bc0;
+        hB = __umulhi(kMulB, bc2); lB = kMulB * bc2;
+        uint32_t n0b = hB ^ bc1 ^ k0, n2b = hA ^ bc3 ^ k1;
+        bc0 = n0b; bc1 = lB; bc2 = n2b; bc3 = lA;
+    }
+    a.w[0] = ac0; a.w[1] = ac1; a.w[2] = ac2; a.w[3] = ac3;
+    b.w[0] = bc0; b.w[1] = bc1; b.w[2] = bc2; b.w[3] = bc3;
+}
+
 // FP32: the same words, u = ((w >> 9) + 1/2) 2^-23.  k + 1/2 with k < 2^23 needs
 // 24 significant bits, so u is exact in FP32 and lies strictly inside (0, 1)
 // (with 24 bits, (2^24 - 1 + 1/2) 2^-24 would round to 1 and log u to 0).
+// It is built without an integer-to-float conversion: the bit pattern
+// 0x3F800000 | k is the float 1 + k 2^-23, and subtracting 1 - 2^-24 leaves
+// (k + 1/2) 2^-23 exactly (the difference is representable, so the
+// subtraction does not round).
 // Then the hardware log2 / reciprocal square root / sine / cosine.  The angle
 // is taken as 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine
 // are most accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
-__device__ __forceinline__ void normals6_f32(uint32_t walker, uint32_t step, uint32_t stream,
-                                             uint32_t k0, uint32_t k1, float xi[6]) {
-    Words4 a = philox10(walker, step, stream, 0u, k0, k1);
-    Words4 b = philox10(walker, step, stream, 1u, k0, k1);
-    const uint32_t w[6] = {a.w[0], a.w[1], a.w[2], a.w[3], b.w[0], b.w[1]};
-    constexpr float kInv23 = 1.0f / 8388608.0f;
+__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6]) {
+    constexpr float kOneMinusHalfUlp = 1.0f - 1.0f / 16777216.0f;          // 1 - 2^-24
+    constexpr float kHalfUlp = 1.0f / 16777216.0f;                          // 2^-24
     constexpr float kMinus2Ln2 = -1.3862943611198906f;   // -2 ln 2
     constexpr float kTwoPi = 6.2831853071795865f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        float ua = ((float)(w[2 * j] >> 9) + 0.5f) * kInv23;
-        float ubc = ((float)(w[2 * j + 1] >> 9) + 0.5f) * kInv23 - 0.5f;   // exact
+        float ua = __int_as_float(0x3F800000 | (w[2 * j] >> 9)) - kOneMinusHalfUlp;
+        // u_b - 1/2 = ((1 + k 2^-23) - 3/2) + 2^-24: both steps exact
+        float ubc = (__int_as_float(0x3F800000 | (w[2 * j + 1] >> 9)) - 1.5f) + kHalfUlp;
         float r2 = kMinus2Ln2 * __log2f(ua);                               // -2 ln u > 0
         float rho = r2 * rsqrtf(r2);
         float s, c;
@@ -106,7 +210,11 @@ __device__ __forceinline__ void radius(double s, double& r, double& i) {
     r = sqrt(s);
     i = 1.0 / r;
 }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp(float x) {   // hardware reciprocal (<= 1 ulp)
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float expn(float x) { return __expf(x); }
 __device__ __forceinline__ double expn(double x) { return exp(x); }
@@ -327,12 +435,11 @@ __device__ __forceinline__ void eval_trial(const TrialDev<R>& t, const R x[6], E
     else eval_kind1<R>(t, x, o);
 }
 
+// A sum is finite only if every term is (an infinity or NaN in any term makes
+// it infinite or NaN), so one test covers the drift and the local energy.
 template <typename R>
 __device__ __forceinline__ bool eval_finite(const EvalOut<R>& o) {
-    bool f = finite_(o.el);
-#pragma unroll
-    for (int d = 0; d < 6; ++d) f = f && finite_(o.b[d]);
-    return f;
+    return finite_(((o.b[0] + o.b[1]) + (o.b[2] + o.b[3])) + ((o.b[4] + o.b[5]) + o.el));
 }
 
 // ---------------------------------------------------------------------------

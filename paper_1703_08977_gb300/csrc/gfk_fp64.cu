@@ -6,7 +6,7 @@
 // One thread advances one walker for a whole chunk of steps with its state in
 // registers.  Per step (the discretised Eq. 4 with the drifted diffusion under
 // it):
-//   xi       <- six N(0,1) from Philox4x32-10, counter (walker, step, stream, 0/1)
+//   xi       <- six N(0,1) from Philox4x32-10 words (three blocks per two moves)
 //   X        <- X + b(X) dt + sqrt(dt) xi                       (Euler-Maruyama)
 //   b, E_L   <- trial function at the new X
 //   node     :  sign psi changed (or psi = 0) -> walker killed
@@ -43,7 +43,9 @@ init_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
     if (valid) {
         const int64_t slot = I.off + id;
         double xi[6], x[6];
-        normals6_f64((uint32_t)id, 0u, I.stream, 2u, I.k0, I.k1, xi);
+        uint32_t words[6];
+        init_words((uint32_t)id, I.stream, I.k0, I.k1, words);
+        normals6_f64(words, xi);
 #pragma unroll
         for (int d = 0; d < 6; ++d) x[d] = I.sigma * xi[d];
         EvalOut<double> ev;
@@ -133,7 +135,9 @@ walk_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
         double q[5] = {0, 0, 0, 0, 0};
         if (sg != 0) {
             double xi[6];
-            normals6_f64((uint32_t)id, step, stream, 0u, k0, k1, xi);
+            uint32_t words[6];
+            move_words((uint32_t)id, step, stream, k0, k1, words);
+            normals6_f64(words, xi);
 #pragma unroll
             for (int d = 0; d < 6; ++d) x[d] = x[d] + ev.b[d] * dt + sdt * xi[d];
             eval_trial<KIND, double>(t, x, ev);

@@ -5,19 +5,20 @@
 // range, so every load and store is coalesced) for a whole chunk of steps with
 // the state in registers.  Per step and walker (the discretised Eq. 4 and the
 // drifted diffusion under it):
-//   xi     <- six N(0,1): Philox4x32-10 words, FP32 Box-Muller on the hardware
-//             log2 / rsqrt / sin / cos
+//   xi     <- six N(0,1): Philox4x32-10 words (three blocks serve two moves),
+//             FP32 Box-Muller on the hardware log2 / rsqrt / sin / cos
 //   X      <- X + b dt + sqrt(dt) xi                    (FP32, fused multiply-add)
 //   b, E_L <- trial function at X in the cusp-cancelled form (FP32)
 //   node   :  sign psi changed or psi = 0 -> killed
 //   S      <- S + (E_L - E_T)            (FP32 Kahan sum since the last fold)
-//   w      =  2^{(d - S dt) log2 e}      (d = FP64 base minus the block shift)
+//   w      =  2^{(d - S dt) log2 e}      (d = FP64 base minus the warp's shift)
 // Every kRing steps the FP32 sums are folded into the FP64 base,
 //   L <- L - (S + kRing (E_T,fp32 - E_T)) dt            (FP64),
-// the block shift c is reset to the block's largest L and d = (float)(L - c).
-// Per step each warp adds its (w, w E_L, w^2, w E_L^2, alive) in FP32; the
-// block adds its warps in FP64 every kRing steps and writes one PartialRec per
-// step; a deferred kernel merges blocks with compensated FP64 sums.
+// the warp's shift c is reset to its largest L and d = (float)(L - c).
+// Per step each warp adds its (w, w E_L, w^2, w E_L^2) in FP32 and counts its
+// live walkers; every kRing steps, after one block barrier, the block rescales
+// each warp's sums to the block's largest shift and adds them in FP64, writing
+// one PartialRec per step; a deferred kernel merges the blocks (double-double).
 #include <cuda_runtime.h>
 
 #include "gfk_block.cuh"
@@ -73,7 +74,9 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         // the initial positions are drawn in FP64, exactly as on the FP64 path,
         // then rounded: both paths start from the same population
         double xi[6];
-        normals6_f64((uint32_t)id, 0u, I.stream, 2u, I.k0, I.k1, xi);
+        uint32_t words[6];
+        init_words((uint32_t)id, I.stream, I.k0, I.k1, words);
+        normals6_f64(words, xi);
         float x[6];
 #pragma unroll
         for (int d = 0; d < 6; ++d) x[d] = (float)(I.sigma * xi[d]);
@@ -122,8 +125,11 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                   uint32_t step0, int nsteps, PartialRec* __restrict__ part, int nblk,
                   unsigned long long* __restrict__ counters) {
     __shared__ TrialDev<float> s_trial;
-    __shared__ float s_ring[kRing][5][kMaxWarps];
-    __shared__ double s_red[kMaxWarps];
+    // double-buffered ring of per-warp sums (W, P, Q, R) and alive counts, and
+    // the per-warp log-weight shift each buffer's window used
+    __shared__ float s_ring[2][kRing][4][kMaxWarps];
+    __shared__ unsigned s_cnt[2][kRing][kMaxWarps];
+    __shared__ double s_shift[2][kMaxWarps];
     const int blk = blockIdx.x;
     const int inst = block_instance(bm, blk);
     const InstDev& I = insts[inst];
@@ -136,16 +142,17 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     const float dt = (float)I.dt, sdt = (float)I.sqrt_dt;
     const float et = (float)I.e_trial;
     const double dt64 = I.dt;
-    // per-step E_T rounding, restored in FP64 at each fold
+    // per-move E_T rounding, restored in FP64 at each fold
     const double et_fix = ((double)et - I.e_trial);
     constexpr float kLog2e = 1.4426950408889634f;
     const float dt_log2e = dt * kLog2e;
-    const uint32_t k0 = I.k0, k1 = I.k1, stream = I.stream;
+    const uint32_t k0 = I.k0, k1 = I.k1;
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = T >> 5;
 
-    uint32_t wid[WPT];
+    PhiloxPre pre[WPT];
+    uint32_t carry[WPT][2];      // tag-1 words 2-3 of the even move, used by the odd one
     int64_t slot[WPT];
     bool valid[WPT];
     float x[WPT][6], b[WPT][6];
@@ -156,7 +163,8 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     for (int k = 0; k < WPT; ++k) {
         const int64_t id = (int64_t)(blk - bm.begin[inst]) * T * WPT + (int64_t)k * T + threadIdx.x;
         valid[k] = id < I.n;
-        wid[k] = (uint32_t)id;
+        pre[k] = philox_pre((uint32_t)id, I.stream, k0, k1);
+        carry[k][0] = carry[k][1] = 0u;
         slot[k] = I.off + id;
         sg[k] = 0;
         L[k] = -INFINITY;
@@ -173,98 +181,151 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         comp[k] = 0.f;
     }
     unsigned n_nonfinite = 0, n_node = 0, n_coal = 0;
+    // per-warp shift: the warp's largest log-weight (0 if the warp has none alive)
     double lmax = -INFINITY;
 #pragma unroll
     for (int k = 0; k < WPT; ++k)
         if (sg[k] != 0) lmax = fmax(lmax, L[k]);
-    double c = block_max_shift(lmax, s_red);
+    double c = warp_max(lmax);
+    if (!isfinite(c)) c = 0.0;
 #pragma unroll
     for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) : 0.f;
     int fold_len = 0;
+    int buf = 0;
 
     for (int s = 0; s < nsteps; ++s) {
         const uint32_t step = step0 + (uint32_t)s;
-        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f;
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+        unsigned na = 0;
+        // every walker slot runs the same instructions (dead or past the end
+        // included) so the compiler can interleave the WPT walkers; only the
+        // commit of the new state is predicated
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
-            if (sg[k] == 0) continue;
-            float xi[6];
-            normals6_f32(wid[k], step, stream, k0, k1, xi);
+            const bool alive = sg[k] != 0;
+            // words of this move: the even move of a pair runs the blocks of
+            // tags 0 and 1 and keeps tag 1's last two words for the odd move,
+            // which runs tag 2 (and tag 1 again if the launch starts on it)
+            uint32_t words[6];
+            const uint32_t m = step >> 1;
+            if ((step & 1u) == 0u) {
+                Words4 wa, wb;
+                philox10_pair(pre[k], m, k0, k1, wa, wb);
+                words[0] = wa.w[0]; words[1] = wa.w[1]; words[2] = wa.w[2]; words[3] = wa.w[3];
+                words[4] = wb.w[0]; words[5] = wb.w[1];
+                carry[k][0] = wb.w[2];
+                carry[k][1] = wb.w[3];
+            } else {
+                if (s == 0) {
+                    const Words4 wb = philox10_tag(pre[k], m, 1u, k0, k1);
+                    carry[k][0] = wb.w[2];
+                    carry[k][1] = wb.w[3];
+                }
+                const Words4 wc = philox10_tag(pre[k], m, 2u, k0, k1);
+                words[0] = carry[k][0]; words[1] = carry[k][1];
+                words[2] = wc.w[0]; words[3] = wc.w[1]; words[4] = wc.w[2]; words[5] = wc.w[3];
+            }
+            float xi[6], xn[6];
+            normals6_f32(words, xi);
 #pragma unroll
-            for (int d = 0; d < 6; ++d) x[k][d] = fmaf(sdt, xi[d], fmaf(b[k][d], dt, x[k][d]));
+            for (int d = 0; d < 6; ++d) xn[d] = fmaf(sdt, xi[d], fmaf(b[k][d], dt, x[k][d]));
             EvalOut<float> ev;
-            eval_trial<KIND, float>(t, x[k], ev);
-            if (ev.rmin < 1e-5f) ++n_coal;
-            if (ev.sign != sg[k]) {
-                sg[k] = 0;
-                L[k] = -INFINITY;
-                ++n_node;
-                continue;
-            }
-            if (!eval_finite(ev)) {
-                sg[k] = 0;
-                L[k] = -INFINITY;
-                ++n_nonfinite;
-                continue;
-            }
+            eval_trial<KIND, float>(t, xn, ev);
+            const bool node = ev.sign != sg[k];
+            const bool fin = eval_finite(ev);
+            const bool stay = alive && !node && fin;
+            n_coal += (alive && ev.rmin < 1e-5f) ? 1u : 0u;
+            n_node += (alive && node) ? 1u : 0u;
+            n_nonfinite += (alive && !node && !fin) ? 1u : 0u;
 #pragma unroll
-            for (int d = 0; d < 6; ++d) b[k][d] = ev.b[d];
+            for (int d = 0; d < 6; ++d) {
+                x[k][d] = alive ? xn[d] : x[k][d];      // a walker killed now stays here
+                b[k][d] = stay ? ev.b[d] : b[k][d];
+            }
+            sg[k] = stay ? sg[k] : 0;
             // Kahan: S accumulates E_L - E_T since the last fold
-            const float y = (ev.el - et) - comp[k];
+            const float el = stay ? ev.el : et;
+            const float y = (el - et) - comp[k];
             const float tsum = S[k] + y;
             comp[k] = (tsum - S[k]) - y;
             S[k] = tsum;
-            const float w = ex2_approx(fmaf(-S[k], dt_log2e, dsh[k] * kLog2e));
-            const float we = w * ev.el;
+            const float w = stay ? ex2_approx(fmaf(-S[k], dt_log2e, dsh[k] * kLog2e)) : 0.f;
+            const float we = w * el;
             q0 += w;
             q1 += we;
             q2 += w * w;
-            q3 += we * ev.el;
-            q4 += 1.f;
+            q3 += we * el;
+            na += stay ? 1u : 0u;
         }
         q0 = warp_sum(q0);
         q1 = warp_sum(q1);
         q2 = warp_sum(q2);
         q3 = warp_sum(q3);
-        q4 = warp_sum(q4);
+        na = __reduce_add_sync(0xffffffffu, na);
         const int r = s % kRing;
         if (lane == 0) {
-            s_ring[r][0][warp] = q0;
-            s_ring[r][1][warp] = q1;
-            s_ring[r][2][warp] = q2;
-            s_ring[r][3][warp] = q3;
-            s_ring[r][4][warp] = q4;
+            s_ring[buf][r][0][warp] = q0;
+            s_ring[buf][r][1][warp] = q1;
+            s_ring[buf][r][2][warp] = q2;
+            s_ring[buf][r][3][warp] = q3;
+            s_cnt[buf][r][warp] = na;
         }
         ++fold_len;
         if (r == kRing - 1 || s == nsteps - 1) {
-            __syncthreads();
-            const int rows = r + 1;
-            if ((int)threadIdx.x < rows) {
-                const int rr = threadIdx.x;
-                double acc[5] = {0, 0, 0, 0, 0};
-                for (int w = 0; w < nwarps; ++w)
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) acc[k] += (double)s_ring[rr][k][w];
-                PartialRec rec;
-                rec.c = c;
-                rec.W = acc[0]; rec.P = acc[1]; rec.Q = acc[2]; rec.R = acc[3]; rec.n = acc[4];
-                part[(int64_t)(s - r + rr) * nblk + blk] = rec;
-            }
-            // fold the FP32 increments into the FP64 base
+            if (lane == 0) s_shift[buf][warp] = c;
+            // fold the FP32 increments into the FP64 base; new per-warp shift
             lmax = -INFINITY;
 #pragma unroll
             for (int k = 0; k < WPT; ++k) {
                 if (sg[k] != 0) {
                     L[k] = L[k] - (((double)S[k] - (double)comp[k]) + (double)fold_len * et_fix) * dt64;
                     lmax = fmax(lmax, L[k]);
+                } else {
+                    L[k] = -INFINITY;
                 }
                 S[k] = 0.f;
                 comp[k] = 0.f;
             }
             fold_len = 0;
-            c = block_max_shift(lmax, s_red);
+            c = warp_max(lmax);
+            if (!isfinite(c)) c = 0.0;
 #pragma unroll
             for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) : 0.f;
+            // one barrier per window: the other buffer takes the next window,
+            // and nobody writes this one again before the next barrier
+            __syncthreads();
+            const int rows = r + 1;
+            if ((int)threadIdx.x < rows) {
+                const int rr = threadIdx.x;
+                double cb = -INFINITY;
+                for (int w = 0; w < nwarps; ++w)
+                    if (s_cnt[buf][rr][w] != 0u) cb = fmax(cb, s_shift[buf][w]);
+                double acc[4] = {0, 0, 0, 0};
+                unsigned n_alive = 0;
+                if (isfinite(cb)) {
+                    for (int w = 0; w < nwarps; ++w) {
+                        const unsigned nw = s_cnt[buf][rr][w];
+                        if (nw == 0u) continue;
+                        n_alive += nw;
+                        // warp shift relative to the block's: exact in FP64, then
+                        // the factor in FP32 (it multiplies FP32 warp sums)
+                        const float f = ex2_approx((float)(s_shift[buf][w] - cb) * kLog2e);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float fk = k == 2 ? f * f : f;
+                            acc[k] += (double)(s_ring[buf][rr][k][w] * fk);
+                        }
+                    }
+                } else {
+                    cb = 0.0;
+                }
+                PartialRec rec;
+                rec.c = cb;
+                rec.W = acc[0]; rec.P = acc[1]; rec.Q = acc[2]; rec.R = acc[3];
+                rec.n = (double)n_alive;
+                part[(int64_t)(s - r + rr) * nblk + blk] = rec;
+            }
+            buf ^= 1;
         }
     }
 #pragma unroll

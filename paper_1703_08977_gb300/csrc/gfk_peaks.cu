@@ -1,0 +1,130 @@
+// Instruction-throughput microbenchmarks: the ALU denominators of the walk's
+// roofline, measured on the device at hand (a measurement utility; the paper
+// has no counterpart).
+//
+// Each kernel runs kChains independent dependency chains per thread of one
+// instruction (inline PTX, so the compiler keeps exactly that instruction),
+// on enough blocks to fill every SM several times over.  The rate reported is
+// lane operations per second: threads x chains x iterations / elapsed time.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gfk_types.h"
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kIters = 2048;
+constexpr int kThreads = 256;
+
+template <int OP>
+__global__ void __launch_bounds__(kThreads) peak_kernel(unsigned* __restrict__ sink, unsigned seed) {
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned u[kChains];
+    float f[kChains];
+    double d[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) {
+        u[j] = t * 2654435761u + seed + j;
+        f[j] = 1.0f + (float)(u[j] & 1023) * 1e-4f;
+        d[j] = (double)f[j];
+    }
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) {
+            if (OP == GFK_PEAK_FFMA) {
+                asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(f[j]) : "f"(0.9999f), "f"(1e-4f));
+            } else if (OP == GFK_PEAK_DFMA) {
+                asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(d[j]) : "d"(0.9999), "d"(1e-4));
+            } else if (OP == GFK_PEAK_IMAD) {
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(u[j]) : "r"(0xD2511F53u), "r"(7u));
+            } else if (OP == GFK_PEAK_IMAD_HI) {
+                asm volatile("mad.hi.u32 %0, %0, %1, %0;" : "+r"(u[j]) : "r"(0xCD9E8D57u));
+            } else if (OP == GFK_PEAK_IMAD_WIDE) {
+                unsigned hi;
+                asm volatile("{ .reg .u64 w; mad.wide.u32 w, %0, %2, 12345; mov.b64 {%0, %1}, w; }"
+                             : "+r"(u[j]), "=r"(hi) : "r"(0xD2511F53u));
+                u[j] ^= hi;
+            } else if (OP == GFK_PEAK_LOP3) {
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(u[j]) : "r"(0x9E3779B9u), "r"(i));
+            } else if (OP == GFK_PEAK_EX2) {
+                asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(f[j]));
+            } else if (OP == GFK_PEAK_RSQ) {
+                asm volatile("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(f[j]));
+            } else if (OP == GFK_PEAK_LG2) {
+                asm volatile("lg2.approx.ftz.f32 %0, %0;" : "+f"(f[j]));
+            } else if (OP == GFK_PEAK_SIN) {
+                asm volatile("sin.approx.ftz.f32 %0, %0;" : "+f"(f[j]));
+            } else if (OP == GFK_PEAK_I2F) {
+                asm volatile("{ .reg .f32 v; cvt.rn.f32.u32 v, %0; mov.b32 %0, v; }" : "+r"(u[j]));
+            } else if (OP == GFK_PEAK_F2F) {
+                asm volatile("{ .reg .f64 v; cvt.f64.f32 v, %0; cvt.rn.f32.f64 %0, v; }" : "+f"(f[j]));
+            }
+        }
+    }
+    unsigned acc = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) acc ^= u[j] ^ __float_as_uint(f[j]) ^ (unsigned)__double_as_longlong(d[j]);
+    if (acc == 0x9E3779B9u) sink[0] = acc;   // practically never; keeps the chains live
+}
+
+template <int OP>
+cudaError_t time_op(int blocks, unsigned* sink, cudaStream_t s, float* best_ms) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) { cudaEventDestroy(a); return e; }
+    *best_ms = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(a, s);
+        if (e == cudaSuccess) { peak_kernel<OP><<<blocks, kThreads, 0, s>>>(sink, rep); e = cudaGetLastError(); }
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && rep > 0 && ms < *best_ms) *best_ms = ms;   // rep 0 warms up
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
+}
+
+}  // namespace
+
+extern "C" gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* lane_ops_per_s) {
+    if (!lane_ops_per_s || op < 0 || op >= GFK_PEAK_COUNT) return GFK_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GFK_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GFK_ECUDA;
+    const int blocks = sms * 32;   // 8 resident blocks of 256 threads per SM, 4 waves
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned* sink = nullptr;
+    // 4 bytes the kernels may write; taken from the stream-ordered pool and
+    // returned at the end of the call
+    if (cudaMallocAsync((void**)&sink, sizeof(unsigned), s) != cudaSuccess) return GFK_ENOMEM;
+    float ms = 0.f;
+    cudaError_t e = cudaSuccess;
+    switch (op) {
+        case GFK_PEAK_FFMA: e = time_op<GFK_PEAK_FFMA>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_DFMA: e = time_op<GFK_PEAK_DFMA>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_IMAD: e = time_op<GFK_PEAK_IMAD>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_IMAD_HI: e = time_op<GFK_PEAK_IMAD_HI>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_IMAD_WIDE: e = time_op<GFK_PEAK_IMAD_WIDE>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_LOP3: e = time_op<GFK_PEAK_LOP3>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_EX2: e = time_op<GFK_PEAK_EX2>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_RSQ: e = time_op<GFK_PEAK_RSQ>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_LG2: e = time_op<GFK_PEAK_LG2>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_SIN: e = time_op<GFK_PEAK_SIN>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_I2F: e = time_op<GFK_PEAK_I2F>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_F2F: e = time_op<GFK_PEAK_F2F>(blocks, sink, s, &ms); break;
+        default: e = cudaErrorInvalidValue; break;
+    }
+    cudaFreeAsync(sink, s);
+    if (e != cudaSuccess) return GFK_ECUDA;
+    const double ops = (double)blocks * kThreads * kChains * kIters * (op == GFK_PEAK_F2F ? 2 : 1);
+    *lane_ops_per_s = ops / (ms * 1e-3);
+    return GFK_OK;
+}

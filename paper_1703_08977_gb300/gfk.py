@@ -30,9 +30,12 @@ GFK_MAX_INSTANCES = 64
 EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gfk_steps",
            "gfk_energy", "gfk_sums", "gfk_get_walkers", "gfk_counters", "gfk_checkpoint_size",
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
-           "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc")
+           "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc",
+           "gfk_measure_peak")
+PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
+            "i2f", "f2f")
 GFK_NOALLOC_SCRATCH_BYTES = 16 << 20
-GFK_NOALLOC_MAX_WALKERS = 1 << 23
+GFK_NOALLOC_MAX_WALKERS = 1 << 22
 
 
 class gfk_instance_desc(ctypes.Structure):
@@ -93,6 +96,7 @@ def load(build_if_needed: bool = True):
             "gfk_destroy": ([P], None),
             "gfk_status_string": ([c.c_int], c.c_char_p),
             "gfk_last_error": ([P], c.c_char_p),
+            "gfk_measure_peak": ([c.c_int32, P, dp], c.c_int),
             "gfk_propagate_noalloc": ([c.POINTER(gfk_instance_desc), c.c_int32, dp, c.c_int32,
                                        P, P, P, c.c_int32, c.c_int64, c.c_int64, P, P, P],
                                       c.c_int),
@@ -260,6 +264,17 @@ def gfk_propagate_noalloc(desc, kind, params, p0, p1, sgn, init, step0, n_steps,
     return load().gfk_propagate_noalloc(ctypes.byref(d), int(kind), _dp(p), len(p), addr(p0),
                                         addr(p1), addr(sgn), int(init), int(step0),
                                         int(n_steps), addr(rows), addr(counters), stream)
+
+
+def gfk_measure_peak(op, stream=None) -> float:
+    """Measured lane-operations per second of one instruction class (see PEAK_OPS)."""
+    if isinstance(op, str):
+        op = PEAK_OPS.index(op)
+    if stream is None:
+        stream = _current_stream_ptr()
+    v = ctypes.c_double()
+    _check(load().gfk_measure_peak(int(op), stream, ctypes.byref(v)), "gfk_measure_peak")
+    return v.value
 
 
 # ----------------------------------------------------------------------------

@@ -89,23 +89,27 @@ def test_uniform_map_endpoints():
 
 def test_normals_are_standard_normal():
     """Box-Muller output: Kolmogorov-Smirnov against N(0,1) per component, unit
-    variance, no correlation between the six components of one step."""
+    variance, no correlation between the six components of a move, between the
+    two moves of one Philox pair index, or in the initial positions."""
     stats = pytest.importorskip("scipy.stats")
-    xs = np.array([oracle.normals6(seed=99, walker=i, step=3, inst=1) for i in range(20000)])
-    for d in range(6):
-        p = stats.kstest(xs[:, d], "norm").pvalue
-        assert p > 1e-4, (d, p)
-    assert abs(xs.mean()) < 0.01
-    assert abs(xs.var() - 1.0) < 0.01
-    cc = np.corrcoef(xs.T)
-    assert np.max(np.abs(cc - np.eye(6))) < 0.03
+    even = np.array([oracle.move_normals(99, i, 6, 1) for i in range(20000)])
+    odd = np.array([oracle.move_normals(99, i, 7, 1) for i in range(20000)])
+    init = np.array([oracle.init_normals(99, i, 1) for i in range(20000)])
+    for xs in (even, odd, init):
+        for d in range(6):
+            p = stats.kstest(xs[:, d], "norm").pvalue
+            assert p > 1e-4, (d, p)
+        assert abs(xs.mean()) < 0.01
+        assert abs(xs.var() - 1.0) < 0.01
+    cc = np.corrcoef(np.hstack([even, odd, init]).T)
+    assert np.max(np.abs(cc - np.eye(18))) < 0.03
     # distinct counters give distinct streams
-    a = oracle.normals6(0, 5, 0, 0, 0)
-    assert not np.allclose(a, oracle.normals6(0, 5, 1, 0, 0))
-    assert not np.allclose(a, oracle.normals6(0, 5, 0, 1, 0))
-    assert not np.allclose(a, oracle.normals6(0, 5, 0, 0, 2))
-    assert not np.allclose(a, oracle.normals6(1, 5, 0, 0, 0))
-    assert not np.allclose(a, oracle.normals6(1 << 32, 5, 0, 0, 0))
+    a = oracle.move_normals(0, 5, 0, 0)
+    for other in (oracle.move_normals(0, 5, 1, 0), oracle.move_normals(0, 5, 2, 0),
+                  oracle.move_normals(0, 5, 0, 1), oracle.move_normals(0, 6, 0, 0),
+                  oracle.move_normals(1, 5, 0, 0), oracle.move_normals(1 << 32, 5, 0, 0),
+                  oracle.init_normals(0, 5, 0)):
+        assert not np.allclose(a, other)
 
 
 # --------------------------------------------------------------------------
@@ -287,18 +291,18 @@ def test_exact_eigenfunction_gives_exact_weights():
 
 
 def test_single_step_by_hand():
-    """One walker, two steps, each recomputed from its definition: X0 = sigma xi(tags 2/3),
-    X1 = X0 + b(X0) dt + sqrt(dt) xi(step 0), logw1 = -(E_L(X1) - E_T) dt, with b and
+    """One walker, two steps, each recomputed from its definition: X0 = sigma xi(initial),
+    X1 = X0 + b(X0) dt + sqrt(dt) xi(move 0), logw1 = -(E_L(X1) - E_T) dt, with b and
     E_L from 50-digit finite differences of ln psi (right-point rule)."""
     kind, p = TRIALS["ground_jastrow_poly"]
     dt, et, seed, sigma, wid, inst = 0.01, -2.9, 77, 0.5, 5, 2
     w = oracle.Walk(kind, p, ids=[wid], dt=dt, e_trial=et, seed=seed, inst=inst, sigma=sigma)
-    X = sigma * oracle.normals6(seed, wid, 0, inst, 2)
+    X = sigma * oracle.init_normals(seed, wid, inst)
     np.testing.assert_array_equal(w.x[0], X)
     logw = 0.0
     for step in range(2):
         b, _, _ = _mp_drift_el(kind, p, X)
-        X = X + b * dt + math.sqrt(dt) * oracle.normals6(seed, wid, step, inst, 0)
+        X = X + b * dt + math.sqrt(dt) * oracle.move_normals(seed, wid, step, inst)
         _, el, _ = _mp_drift_el(kind, p, X)
         logw -= (el - et) * dt
         w.advance(1)
