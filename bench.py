@@ -1,6 +1,7 @@
 """Benchmark: walker-steps per second of the GFK helium walk on one GB300.
 
-One bench step = one full run of the headline workload through the C ABI:
+One bench step = one full run of a workload through the C ABI; the default
+(the headline) is:
 initialise 2^20 walkers of the He 1^1S trial function
 exp(-2 r1 - 2 r2) exp(r12 / (2 (1 + 0.5 r12))) and advance them 20000 moves at
 dt = 0.005 on the mixed-precision path (FP32 drift / local energy / normals,
@@ -29,26 +30,32 @@ sys.path.insert(0, ROOT)
 
 METRIC = "walker-steps/sec on 1 GB300 (FP32-mixed vs FP64) at stated energy error vs FP64 oracle"
 UNIT = "walker-steps/s"
-N_WALKERS = 1 << 20
-N_MOVES = 20000
-DT = 0.005
-E_T = -2.9037
+WORKLOADS = {
+    "ground": ("He 1^1S ground state: 2^20 walkers x 20000 moves, dt=0.005, trial "
+               "exp(-2r1-2r2)exp(r12/(2(1+0.5r12))), E_T=-2.9037, Philox seed 0, mixed FP32 "
+               "physics / FP64 weights"),
+    "triplet": ("He 2^3S: 2^20 walkers x 20000 moves, dt=0.0025, trial "
+                "(e^{-2r1-0.5r2}-e^{-0.5r1-2r2})exp(r12/(4(1+0.3r12))), node r1=r2 by kill, "
+                "E_T=-2.1752, mixed"),
+    "batched": ("12 instances {1^1S, 2^3S, P_z} x dt {0.01,0.005,0.0025,0.00125}, walker counts "
+                "round(2^U), U~U[16,21] (numpy default_rng(1)), sum 7.75e6 walkers x 10000 moves, "
+                "one launch per chunk, mixed"),
+}
 SEED = 0
-TRIAL = (0, [2.0, 0.5, 0.5])           # GFK_TRIAL_JASTROW_PRODUCT: Z, a, beta
-WORKLOAD = ("He 1^1S ground state: 2^20 walkers x 20000 moves, dt=0.005, "
-            "trial exp(-2r1-2r2)exp(r12/(2(1+0.5r12))), E_T=-2.9037, Philox seed 0, "
-            "mixed FP32 physics / FP64 weights")
 
-# Algorithmic ALU work of one walker-step of the mixed path for the kind-0 trial
-# (counted from the method, FMA = 1 op): Philox4x32-10
-# x2 (200 integer ops), Box-Muller x3 (51), move (12), trial evaluation (77),
-# log-weight and weighted sums (12).
-OPS_PER_WALKER_STEP = 352
+# Algorithmic ALU work of one walker-step of the mixed path for the kind-0 trial,
+# counted from the method's definition (one op per multiply, add, compare,
+# reciprocal, square root, log, exp, sine, cosine; a 32x32->64 multiply is one
+# op): Philox4x32-10 at 1.5 blocks per move (120),
+# Box-Muller x3 (42), move (12), trial evaluation, weight and sums (11).  The
+# trial evaluation is 105 ops for the ground-state product (kind 0) and 220 for
+# a two-term orbital-pair function (kind 1).
+OPS_PER_WALKER_STEP = {0: 290, 1: 405}
 # Lanes that can issue an ALU instruction per SM per clock (4 schedulers x 32).
 LANES_PER_SM_CLK = 128
 # DRAM traffic of the walk kernel per launch from an ncu capture, valid only for
 # the kernel sources it was taken on (sha256 prefix of csrc/*); None otherwise.
-WALK_TRAFFIC = {"src_sha": None, "bytes_per_walker_step": None}
+WALK_TRAFFIC = {"src_sha": None, "bytes_per_launch": None}
 
 
 def _src_sha() -> str:
@@ -128,10 +135,10 @@ def run_reference(args):
     import oracle
     oracle.build()
     n_sample, moves = 4096, 100
-    kind, params = TRIAL
+    kind, params, dt, et = 0, [2.0, 0.5, 0.5], 0.005, -2.9037
 
     def one():
-        w = oracle.Walk(kind, params, n_walkers=n_sample, dt=DT, e_trial=E_T, seed=SEED)
+        w = oracle.Walk(kind, params, n_walkers=n_sample, dt=dt, e_trial=et, seed=SEED)
         w.advance(moves)
         return w
 
@@ -147,7 +154,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "data": "synthetic", "config": {"workload": WORKLOADS["ground"], "name": "ground",
+                                        "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -158,14 +166,27 @@ def cpu_baseline():
     import oracle
     oracle.build()
     n_sample, moves = 1 << 14, 600
-    kind, params = TRIAL
+    kind, params, dt, et = 0, [2.0, 0.5, 0.5], 0.005, -2.9037
     t0 = time.perf_counter()
-    w = oracle.Walk(kind, params, n_walkers=n_sample, dt=DT, e_trial=E_T, seed=SEED)
+    w = oracle.Walk(kind, params, n_walkers=n_sample, dt=dt, e_trial=et, seed=SEED)
     w.advance(moves)
     el = time.perf_counter() - t0
     return {"value": n_sample * moves / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"2^14 walkers x {moves} moves of the same workload, one host thread "
                       f"({os.cpu_count()} cores on the host)"}
+
+
+def _workload(name, rank):
+    from paper_1703_08977_gb300 import workloads as wl
+    if name == "ground":
+        insts, moves = wl.ground_at_scale(0.005)
+    elif name == "triplet":
+        insts, moves = wl.triplet_at_scale()
+    else:
+        insts, moves = wl.batched()
+    for d in insts:
+        d["rng_stream"] += 1000 * rank     # each rank its own walkers (weak scaling)
+    return insts, moves
 
 
 def run_ours(args):
@@ -182,21 +203,27 @@ def run_ours(args):
 
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
-    kind, params = TRIAL
+    insts, n_moves = _workload(args.workload, rank)
+    n_walkers = sum(d["n_walkers"] for d in insts)
+    trials = [(d["kind"], d["params"]) for d in insts]
 
-    def make_ctx(prec, n_walkers=N_WALKERS, launch=None):
-        d = gfk.InstanceDesc(n_walkers=n_walkers, dt=DT, e_trial=E_T, seed=SEED,
-                             prec=prec, rng_stream=rank)
-        return gfk.Context([d], trials=[(kind, params)], launch=launch)
+    def descs(prec):
+        return [gfk.InstanceDesc(n_walkers=d["n_walkers"], dt=d["dt"], e_trial=d["e_trial"],
+                                 seed=d["seed"], state=d["state"], prec=prec,
+                                 rng_stream=d["rng_stream"]) for d in insts]
 
-    launch = (args.threads, args.wpt)
-    ctx = make_ctx(gfk.GFK_PREC_MIXED, launch=launch)
+    ctx = gfk.Context(descs(gfk.GFK_PREC_MIXED), trials=trials)
+    if args.threads and args.wpt:
+        ctx.set_launch(args.threads, args.wpt)
+        launch = (args.threads, args.wpt, None)
+    else:
+        launch = gfk.autotune_cached(ctx.handle, ctx.descs, trials, probe_steps=256)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
     stream = torch.cuda.current_stream()
 
     def device_step():
         ctx.reset()
-        ctx.propagate(N_MOVES)
+        ctx.propagate(n_moves)
 
     for _ in range(args.warmup):
         device_step()
@@ -231,84 +258,101 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_per_step = ms / args.steps
-    walker_steps_per_step = N_WALKERS * N_MOVES
+    walker_steps_per_step = n_walkers * n_moves
     value = walker_steps_per_step * ws * args.steps / (ms / 1e3)
 
-    # ---- end to end through the C ABI with host buffers ----
-    cap = N_MOVES + 1
-    e_host = np.empty(cap)
-    lz_host = np.empty(cap)
-    ess_host = np.empty(cap)
-    h2d = 8 * len(params) + 1024          # trial parameters + the instance table upload
-    d2h = 3 * 8 * cap + 8
+    # ---- end to end through the C ABI with host buffers (graph replay) ----
+    cap = n_moves + 1
+    e_host = [np.empty(cap) for _ in insts]
+    lz_host = [np.empty(cap) for _ in insts]
+    ess_host = [np.empty(cap) for _ in insts]
+    h2d = sum(8 * len(p) for _, p in trials) + 1024 * len(insts)   # trial vectors + instance table
+    d2h = len(insts) * (3 * 8 * cap + 8)
+    ctx.set_graph(True)
+    ctx.reset()
+    ctx.propagate(n_moves)              # capture once (outside the timing)
     torch.cuda.synchronize()
+    n_e2e = max(1, args.steps // 2)
     t0 = time.perf_counter()
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(n_e2e):
         gfk.gfk_reset(ctx.handle)
-        gfk.gfk_set_trial(ctx.handle, 0, kind, params)
-        gfk.gfk_propagate(ctx.handle, N_MOVES)
-        gfk.gfk_energy(ctx.handle, 0, cap=cap, out=(e_host, lz_host, ess_host))
-    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
-    e_mixed = e_host.copy()
+        for i, (k, p) in enumerate(trials):
+            gfk.gfk_set_trial(ctx.handle, i, k, p)
+        gfk.gfk_propagate(ctx.handle, n_moves)
+        for i in range(len(insts)):
+            gfk.gfk_energy(ctx.handle, i, cap=cap, out=(e_host[i], lz_host[i], ess_host[i]))
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e_mixed = e_host[0].copy()
     ctx.close()
 
     out = None
     if rank == 0:
-        # ---- the FP64 path on the same seeds, and the mixed path's energy error ----
-        n_cmp = args.fp64_moves
-        c64 = make_ctx(gfk.GFK_PREC_FP64)
-        c64.propagate(16)
-        torch.cuda.synchronize()
-        c64.reset()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        c64.propagate(n_cmp)
-        b.record(stream)
-        torch.cuda.synchronize()
-        fp64_ms = a.elapsed_time(b)
-        fp64_value = N_WALKERS * n_cmp / (fp64_ms / 1e3)
-        e64 = c64.energy(0)["E"]
-        c64.close()
-        diff = e_mixed[: n_cmp + 1] - e64
-        tail = diff[len(diff) // 2:]
         avg_launch_ms = walk_ms / max(1, walk_launches)
         ws_per_launch = walk_ws / max(1, walk_launches)
         sm_max = clk.get("sm_max_mhz") or 2070.0
         peak = n_sm * LANES_PER_SM_CLK * sm_max * 1e6 / 1e9      # Gop/s
-        achieved = OPS_PER_WALKER_STEP * ws_per_launch / (avg_launch_ms / 1e3) / 1e9
+        ops = sum(OPS_PER_WALKER_STEP[d["kind"]] * d["n_walkers"] for d in insts) / n_walkers
+        achieved = ops * ws_per_launch / (avg_launch_ms / 1e3) / 1e9
         traffic = None
-        if WALK_TRAFFIC["src_sha"] == _src_sha() and WALK_TRAFFIC["bytes_per_walker_step"]:
-            traffic = WALK_TRAFFIC["bytes_per_walker_step"] * ws_per_launch
+        if WALK_TRAFFIC["src_sha"] == _src_sha() and WALK_TRAFFIC["bytes_per_launch"]:
+            traffic = WALK_TRAFFIC["bytes_per_launch"]
         launches_per_step = 2 * walk_launches / args.steps + 2
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "walkers_per_gpu": N_WALKERS, "moves": N_MOVES,
-                       "dt": DT, "launch": {"threads": launch[0], "walkers_per_thread": launch[1]},
-                       "l2": "flushed (256 MB write) before every timed step; state 32 MB"},
+            "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                       "walkers_per_gpu": n_walkers, "moves": n_moves,
+                       "launch": {"threads": launch[0], "walkers_per_thread": launch[1],
+                                  "chosen_by": "autotune" if launch[2] else "flags"},
+                       "l2": "flushed (256 MB write) before every timed step; state "
+                             f"{n_walkers * 33 / 2**20:.0f} MB"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "e2e": {"value": walker_steps_per_step * ws / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "path": "gfk_set_trial + gfk_propagate (CUDA-graph replay) + gfk_energy "
+                            "into host arrays, wall clock"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "walk_mixed_kernel",
                          "peak_basis": f"{n_sm} SMs x {LANES_PER_SM_CLK} lanes x {sm_max:.0f} MHz "
-                                       "(issue limit; derived, no measured ALU peak)",
-                         "ops_per_walker_step": OPS_PER_WALKER_STEP,
-                         "avg_launch_ms": avg_launch_ms},
-            "fp64_path": {"value": fp64_value, "unit": UNIT, "moves": n_cmp,
-                          "mixed_over_fp64": value / ws / fp64_value},
-            "energy_error_vs_fp64": {
-                "moves": n_cmp, "max_abs_E_t": float(np.max(np.abs(diff))),
-                "mean_E_t_second_half": float(np.mean(tail)),
-                "final": float(diff[-1]),
-                "note": "mixed minus FP64 path, same seeds and walkers; the FP64 path "
-                        "matches the FP64 oracle to 1e-13 (tests)"},
+                                       "(instruction-issue limit, derived from unit counts and "
+                                       "clock)",
+                         "ops_per_walker_step": ops,
+                         "avg_launch_ms": avg_launch_ms, "walker_steps_per_launch": ws_per_launch},
         }
+        try:
+            out["roofline"]["measured_ffma_lane_ops_per_s"] = gfk.gfk_measure_peak("ffma")
+        except Exception:
+            pass
+        if args.workload == "ground":
+            # ---- the FP64 path on the same seeds, and the mixed path's energy error ----
+            n_cmp = args.fp64_moves
+            c64 = gfk.Context(descs(gfk.GFK_PREC_FP64), trials=trials)
+            c64.propagate(32)
+            torch.cuda.synchronize()
+            c64.reset()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c64.propagate(n_cmp)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fp64_ms = a.elapsed_time(b)
+            fp64_value = n_walkers * n_cmp / (fp64_ms / 1e3)
+            e64 = c64.energy(0)["E"]
+            c64.close()
+            diff = e_mixed[: n_cmp + 1] - e64
+            tail = diff[len(diff) // 2:]
+            out["fp64_path"] = {"value": fp64_value, "unit": UNIT, "moves": n_cmp,
+                                "mixed_over_fp64": value / ws / fp64_value}
+            out["energy_error_vs_fp64"] = {
+                "moves": n_cmp, "max_abs_E_t": float(np.max(np.abs(diff))),
+                "mean_E_t_second_half": float(np.mean(tail)), "final": float(diff[-1]),
+                "note": "mixed minus FP64 path, same seeds and walkers; the FP64 path "
+                        "matches the FP64 oracle to 1e-13 (tests)"}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)
@@ -323,10 +367,10 @@ def profile_case(args):
     moves per launch on the mixed path (or the FP64 path with --prec 0)."""
     import torch
     from paper_1703_08977_gb300 import gfk
-    kind, params = TRIAL
+    kind, params = 0, [2.0, 0.5, 0.5]
     n = 1 << 22 if args.prec == 1 else 1 << 20
-    d = gfk.InstanceDesc(n_walkers=n, dt=DT, e_trial=E_T, seed=SEED, prec=args.prec)
-    launch = (args.threads, args.wpt) if args.prec == 1 else (128, 1)
+    d = gfk.InstanceDesc(n_walkers=n, dt=0.005, e_trial=-2.9037, seed=SEED, prec=args.prec)
+    launch = (args.threads or 128, args.wpt or 2) if args.prec == 1 else (128, 1)
     with gfk.Context([d], trials=[(kind, params)], launch=launch) as ctx:
         ctx.propagate(64)
         ctx.propagate(64)
@@ -342,8 +386,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--threads", type=int, default=128)
-    ap.add_argument("--wpt", type=int, default=2)
+    ap.add_argument("--workload", default="ground", choices=sorted(WORKLOADS))
+    ap.add_argument("--threads", type=int, default=0, help="launch shape (0: autotune)")
+    ap.add_argument("--wpt", type=int, default=0, help="walkers per thread (0: autotune)")
     ap.add_argument("--fp64-moves", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",

@@ -119,6 +119,28 @@ gfk_status gfk_set_trial(gfk_ctx* ctx, int32_t inst, int32_t trial_kind,
  * Allowed at any time between calls. */
 gfk_status gfk_set_launch(gfk_ctx* ctx, int32_t threads_per_block, int32_t walkers_per_thread);
 
+/* Replay gfk_propagate as a CUDA graph.  When enabled (and gfk_profile is
+ * off), each gfk_propagate captures its launch sequence -- the initial
+ * population if due, then the walk and merge kernels of every chunk -- into a
+ * CUDA graph, keyed by start step, length and launch shape, and launches the
+ * graph; a later call with the same key (for example after gfk_reset) replays
+ * it without re-issuing the launches.  Up to 8 graphs are kept per context.
+ * Results are identical to the non-graph path.  The walk over all instances
+ * of a context is one launch per chunk: a batch of instances (several
+ * states, time steps and walker counts) runs as one launch sequence. */
+gfk_status gfk_set_graph(gfk_ctx* ctx, int32_t enable);
+
+/* Choose the launch shape by measurement: for every threads-per-block in
+ * {64, 128, 256, 512} and walkers-per-thread in {1, 2, 4} (FP64: 1), time the
+ * walk kernel and the merge of its block records on probe_steps moves
+ * (1..4096) of this context's own population,
+ * restoring the population and counters after each candidate, then keep the
+ * fastest shape (as gfk_set_launch would).  Outputs may be NULL.  Initialises
+ * the population first if needed.  Synchronises the stream; allocates a
+ * temporary copy of the population. */
+gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads,
+                        int32_t* best_walkers_per_thread, double* best_walker_steps_per_s);
+
 /* Advance every instance by n_steps moves (asynchronous on the context's
  * stream).  The first call after gfk_create / gfk_reset initialises the
  * population (X0 = init_sigma * xi from the Philox blocks (id, 0, stream, 3/4),

@@ -16,8 +16,10 @@ __device__ __forceinline__ int block_instance(const BlockMap& bm, int blk) {
     return inst;
 }
 
-// Maximum of v over the block; `red` holds kMaxWarps doubles of shared memory.
-// Returns 0 when every thread passed -inf (no live walker in the block).
+// Log-weight shift of the block: floor of the block's largest log-weight
+// (integer-valued, so the cross-block merge meets few distinct factors
+// e^{c_b - C}); `red` holds kMaxWarps doubles of shared memory.  Returns 0 when
+// every thread passed -inf (no live walker in the block).
 __device__ __forceinline__ double block_max_shift(double v, double* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -27,7 +29,7 @@ __device__ __forceinline__ double block_max_shift(double v, double* red) {
     double m = red[0];
     for (int w = 1; w < nwarps; ++w) m = fmax(m, red[w]);
     __syncthreads();
-    return isfinite(m) ? m : 0.0;
+    return isfinite(m) ? floor(m) : 0.0;
 }
 
 // Per-thread event counters folded into the instance's global counters.

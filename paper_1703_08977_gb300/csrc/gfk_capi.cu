@@ -69,6 +69,20 @@ struct gfk_ctx {
     int threads = 128;
     int wpt = 1;
     int64_t part_budget_bytes = 256ll << 20;
+    // CUDA-graph replay of gfk_propagate (gfk_set_graph)
+    bool use_graph = false;
+    struct GraphEntry {
+        int64_t step0, n_steps, nblk;
+        int init, threads, wpt;
+        const void* series;
+        const void* part;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    // graphs are captured and launched on a private stream, ordered against
+    // the caller's stream by events (the legacy default stream cannot capture)
+    cudaStream_t graph_stream = nullptr;
+    cudaEvent_t graph_fork = nullptr, graph_join = nullptr;
     // kernel timing (gfk_profile)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;     // pairs: [2k] start, [2k+1] stop
@@ -99,6 +113,7 @@ gfk_status cuda_fail(gfk_ctx* ctx, cudaError_t e, const char* what) {
     if (ctx) {
         ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
     }
+    (void)cudaGetLastError();   // clear it, so the next launch check does not see it again
     return GFK_ECUDA;
 }
 
@@ -295,20 +310,19 @@ gfk_status ensure_series(gfk_ctx* ctx, int64_t rows_needed) {
     return GFK_OK;
 }
 
-gfk_status initialise_population(gfk_ctx* ctx) {
+// Buffers and the instance table for a population that is about to start.
+gfk_status prepare_population(gfk_ctx* ctx) {
     for (int i = 0; i < ctx->n_inst; ++i)
         if (!ctx->has_trial[i]) return GFK_ESTATE;
     if (ctx->params_dirty) {
         gfk_status st = upload_instances(ctx);
         if (st != GFK_OK) return st;
     }
-    int64_t nblk = 0;
-    BlockMap bm = make_block_map(ctx, &nblk);
-    int64_t rows_fit = 0;
-    gfk_status st = ensure_partials(ctx, nblk, &rows_fit);
-    if (st != GFK_OK) return st;
-    st = ensure_series(ctx, 1);
-    if (st != GFK_OK) return st;
+    return ensure_series(ctx, 1);
+}
+
+// Queues the initial population (positions, signs, log-weights) and its sums.
+gfk_status enqueue_init(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk) {
     GFK_CK(ctx, cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * ctx->n_inst,
                                 ctx->stream));
     const int kind = launch_kind(ctx);
@@ -321,8 +335,44 @@ gfk_status initialise_population(gfk_ctx* ctx) {
     }
     GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, 1, ctx->series, ctx->series_cap, 0,
                                    ctx->stream));
-    ctx->initialized = true;
-    ctx->steps = 0;
+    return GFK_OK;
+}
+
+gfk_status profile_pair(gfk_ctx* ctx, cudaEvent_t* a, cudaEvent_t* b);
+
+// Queues n_steps moves from global step step_begin in chunks of rows_fit.
+gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t rows_fit,
+                         int64_t step_begin, int64_t n_steps, bool events) {
+    const int kind = launch_kind(ctx);
+    int64_t walkers = 0;
+    for (int i = 0; i < ctx->n_inst; ++i) walkers += ctx->desc[i].n_walkers;
+    int64_t done = 0;
+    while (done < n_steps) {
+        const int chunk = (int)std::min<int64_t>(n_steps - done, rows_fit);
+        const uint32_t step0 = (uint32_t)(step_begin + done);
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (events) {
+            gfk_status st = profile_pair(ctx, &ev0, &ev1);
+            if (st != GFK_OK) return st;
+        }
+        if (ev0) GFK_CK(ctx, cudaEventRecord(ev0, ctx->stream));
+        if (ctx->prec == GFK_PREC_FP64) {
+            GFK_CK(ctx, launch_walk_fp64(kind, ctx->threads, (int)nblk, ctx->d_inst, bm, ctx->s64,
+                                         step0, chunk, ctx->part, ctx->counters, ctx->stream));
+        } else {
+            GFK_CK(ctx, launch_walk_mixed(kind, ctx->wpt, ctx->threads, (int)nblk, ctx->d_inst, bm,
+                                          ctx->smx, step0, chunk, ctx->part, ctx->counters,
+                                          ctx->stream));
+        }
+        if (ev1) {
+            GFK_CK(ctx, cudaEventRecord(ev1, ctx->stream));
+            ctx->prof_launches += 1;
+            ctx->prof_walker_steps += (double)walkers * chunk;
+        }
+        GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
+                                       ctx->series_cap, step_begin + done + 1, ctx->stream));
+        done += chunk;
+    }
     return GFK_OK;
 }
 
@@ -346,6 +396,13 @@ void free_all(gfk_ctx* ctx) {
     dev_free(ctx->counters);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     ctx->ev_pool.clear();
+    for (auto& gph : ctx->graphs) cudaGraphExecDestroy(gph.exec);
+    ctx->graphs.clear();
+    if (ctx->graph_fork) cudaEventDestroy(ctx->graph_fork);
+    if (ctx->graph_join) cudaEventDestroy(ctx->graph_join);
+    if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
+    ctx->graph_fork = ctx->graph_join = nullptr;
+    ctx->graph_stream = nullptr;
 }
 
 // Harvests recorded event pairs into the running tallies.
@@ -542,13 +599,14 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
     if (!ctx || n_steps < 0) return GFK_EINVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
-    if (!ctx->initialized) {
-        gfk_status st = initialise_population(ctx);
+    const bool init = !ctx->initialized;
+    if (ctx->steps + n_steps > 0xffffffffll) return GFK_EINVAL;
+    gfk_status st = GFK_OK;
+    if (init) {
+        st = prepare_population(ctx);
         if (st != GFK_OK) return st;
     }
-    if (n_steps == 0) return GFK_OK;
-    if (ctx->steps + n_steps > 0xffffffffll) return GFK_EINVAL;
-    gfk_status st = ensure_series(ctx, ctx->steps + n_steps + 1);
+    st = ensure_series(ctx, ctx->steps + n_steps + 1);
     if (st != GFK_OK) return st;
     int64_t nblk = 0;
     BlockMap bm = make_block_map(ctx, &nblk);
@@ -556,35 +614,183 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
     int64_t rows_fit = 0;
     st = ensure_partials(ctx, nblk, &rows_fit);
     if (st != GFK_OK) return st;
-    const int kind = launch_kind(ctx);
-    int64_t left = n_steps;
+    const int64_t step_begin = init ? 0 : ctx->steps;
+
+    if (ctx->use_graph && !ctx->profiling && (init || n_steps > 0)) {
+        // replay a captured graph of this exact launch sequence, or capture one,
+        // on the private stream, after everything queued so far on the caller's
+        if (!ctx->graph_stream) {
+            GFK_CK(ctx, cudaStreamCreateWithFlags(&ctx->graph_stream, cudaStreamNonBlocking));
+            GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->graph_fork, cudaEventDisableTiming));
+            GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->graph_join, cudaEventDisableTiming));
+        }
+        cudaStream_t user = ctx->stream;
+        GFK_CK(ctx, cudaEventRecord(ctx->graph_fork, user));
+        GFK_CK(ctx, cudaStreamWaitEvent(ctx->graph_stream, ctx->graph_fork, 0));
+        gfk_ctx::GraphEntry* hit = nullptr;
+        for (auto& e : ctx->graphs)
+            if (e.step0 == step_begin && e.n_steps == n_steps && e.nblk == nblk &&
+                e.init == (init ? 1 : 0) && e.threads == ctx->threads && e.wpt == ctx->wpt &&
+                e.series == ctx->series && e.part == ctx->part) {
+                hit = &e;
+                break;
+            }
+        if (!hit) {
+            GFK_CK(ctx, cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeThreadLocal));
+            ctx->stream = ctx->graph_stream;          // the enqueue helpers use ctx->stream
+            gfk_status cs = GFK_OK;
+            if (init) cs = enqueue_init(ctx, bm, nblk);
+            if (cs == GFK_OK) cs = enqueue_moves(ctx, bm, nblk, rows_fit, step_begin, n_steps, false);
+            ctx->stream = user;
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(ctx->graph_stream, &graph);
+            if (cs != GFK_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return cs;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+            cudaGraphExec_t exec = nullptr;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
+            if (ctx->graphs.size() >= 8) {
+                cudaGraphExecDestroy(ctx->graphs.front().exec);
+                ctx->graphs.erase(ctx->graphs.begin());
+            }
+            ctx->graphs.push_back({step_begin, n_steps, nblk, init ? 1 : 0, ctx->threads, ctx->wpt,
+                                   ctx->series, ctx->part, exec});
+            hit = &ctx->graphs.back();
+        }
+        GFK_CK(ctx, cudaGraphLaunch(hit->exec, ctx->graph_stream));
+        GFK_CK(ctx, cudaEventRecord(ctx->graph_join, ctx->graph_stream));
+        GFK_CK(ctx, cudaStreamWaitEvent(user, ctx->graph_join, 0));
+    } else {
+        if (init) {
+            st = enqueue_init(ctx, bm, nblk);
+            if (st != GFK_OK) return st;
+        }
+        st = enqueue_moves(ctx, bm, nblk, rows_fit, step_begin, n_steps, ctx->profiling);
+        if (st != GFK_OK) return st;
+    }
+    ctx->initialized = true;
+    ctx->steps = step_begin + n_steps;
+    return GFK_OK;
+}
+
+gfk_status gfk_set_graph(gfk_ctx* ctx, int32_t enable) {
+    if (!ctx) return GFK_EINVAL;
+    ctx->use_graph = enable != 0;
+    return GFK_OK;
+}
+
+gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads,
+                        int32_t* best_wpt, double* best_rate) {
+    if (!ctx || probe_steps < 1 || probe_steps > 4096) return GFK_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!ctx->initialized) {
+        // start the population so the probe walks representative walkers
+        gfk_status st = gfk_propagate(ctx, 0);
+        if (st != GFK_OK) return st;
+    }
+    // keep a copy of everything the probe launches change
+    const size_t sb = state_bytes(ctx);
+    const size_t cb = sizeof(unsigned long long) * kNumCounters * ctx->n_inst;
+    void* saved = nullptr;
+    gfk_status st = dev_alloc(ctx, &saved, sb + cb);
+    if (st != GFK_OK) return st;
+    char* sp = (char*)saved;
+    const int64_t ns = ctx->n_slots;
+    auto copy_state = [&](bool save) -> cudaError_t {
+        cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+        size_t o = 0;
+        cudaError_t e;
+        auto cp = [&](void* dev, size_t n) {
+            e = save ? cudaMemcpyAsync(sp + o, dev, n, k, ctx->stream)
+                     : cudaMemcpyAsync(dev, sp + o, n, k, ctx->stream);
+            o += n;
+            return e;
+        };
+        if (ctx->prec == GFK_PREC_FP64) {
+            if ((e = cp(ctx->s64.x, sizeof(double) * 6 * ns)) != cudaSuccess) return e;
+            if ((e = cp(ctx->s64.logw, sizeof(double) * ns)) != cudaSuccess) return e;
+            if ((e = cp(ctx->s64.sgn, (size_t)ns)) != cudaSuccess) return e;
+        } else {
+            if ((e = cp(ctx->smx.p0, sizeof(float4) * ns)) != cudaSuccess) return e;
+            if ((e = cp(ctx->smx.p1, sizeof(float4) * ns)) != cudaSuccess) return e;
+            if ((e = cp(ctx->smx.sgn, (size_t)ns)) != cudaSuccess) return e;
+        }
+        return cp(ctx->counters, cb);
+    };
+    cudaError_t e = copy_state(true);
+    const int thr[4] = {64, 128, 256, 512};
+    const int wp[3] = {1, 2, 4};
+    const int n_wp = ctx->prec == GFK_PREC_FP64 ? 1 : 3;
+    int bt = ctx->threads, bw = ctx->wpt;
+    double best = -1.0;
     int64_t walkers = 0;
     for (int i = 0; i < ctx->n_inst; ++i) walkers += ctx->desc[i].n_walkers;
-    while (left > 0) {
-        const int chunk = (int)std::min<int64_t>(left, rows_fit);
-        const uint32_t step0 = (uint32_t)ctx->steps;
-        cudaEvent_t ev0, ev1;
-        st = profile_pair(ctx, &ev0, &ev1);
-        if (st != GFK_OK) return st;
-        if (ev0) GFK_CK(ctx, cudaEventRecord(ev0, ctx->stream));
-        if (ctx->prec == GFK_PREC_FP64) {
-            GFK_CK(ctx, launch_walk_fp64(kind, ctx->threads, (int)nblk, ctx->d_inst, bm, ctx->s64,
-                                         step0, chunk, ctx->part, ctx->counters, ctx->stream));
-        } else {
-            GFK_CK(ctx, launch_walk_mixed(kind, ctx->wpt, ctx->threads, (int)nblk, ctx->d_inst, bm,
-                                          ctx->smx, step0, chunk, ctx->part, ctx->counters,
-                                          ctx->stream));
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const int kind = launch_kind(ctx);
+    for (int ti = 0; ti < 4 && e == cudaSuccess && st == GFK_OK; ++ti) {
+        for (int wi = 0; wi < n_wp && e == cudaSuccess && st == GFK_OK; ++wi) {
+            const int save_t = ctx->threads, save_w = ctx->wpt;
+            ctx->threads = thr[ti];
+            ctx->wpt = wp[wi];
+            int64_t nblk = 0;
+            BlockMap bm = make_block_map(ctx, &nblk);
+            int64_t rows_fit = 0;
+            st = ensure_partials(ctx, nblk, &rows_fit);
+            const int chunk = (int)std::min<int64_t>(probe_steps, rows_fit);
+            // the merge of the chunk's block records is timed too (its cost grows
+            // with the number of blocks); it writes rows past the last real one,
+            // which the next gfk_propagate overwrites
+            if (st == GFK_OK) st = ensure_series(ctx, ctx->steps + 1 + chunk);
+            float best_ms = 1e30f;
+            for (int rep = 0; rep < 2 && st == GFK_OK && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(a, ctx->stream);
+                if (e != cudaSuccess) break;
+                if (ctx->prec == GFK_PREC_FP64)
+                    e = launch_walk_fp64(kind, ctx->threads, (int)nblk, ctx->d_inst, bm, ctx->s64,
+                                         (uint32_t)ctx->steps, chunk, ctx->part, ctx->counters,
+                                         ctx->stream);
+                else
+                    e = launch_walk_mixed(kind, ctx->wpt, ctx->threads, (int)nblk, ctx->d_inst, bm,
+                                          ctx->smx, (uint32_t)ctx->steps, chunk, ctx->part,
+                                          ctx->counters, ctx->stream);
+                if (e == cudaSuccess)
+                    e = launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
+                                           ctx->series_cap, ctx->steps + 1, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                if (e == cudaSuccess && rep > 0 && ms < best_ms) best_ms = ms;  // rep 0 warms up
+                if (e == cudaSuccess) e = copy_state(false);   // same start for every candidate
+            }
+            ctx->threads = save_t;
+            ctx->wpt = save_w;
+            const double rate = (double)walkers * chunk / (best_ms * 1e-3);
+            if (e == cudaSuccess && st == GFK_OK && rate > best) {
+                best = rate;
+                bt = thr[ti];
+                bw = wp[wi];
+            }
         }
-        if (ev1) {
-            GFK_CK(ctx, cudaEventRecord(ev1, ctx->stream));
-            ctx->prof_launches += 1;
-            ctx->prof_walker_steps += (double)walkers * chunk;
-        }
-        GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
-                                       ctx->series_cap, ctx->steps + 1, ctx->stream));
-        ctx->steps += chunk;
-        left -= chunk;
     }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+    dev_free(saved);
+    if (st != GFK_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gfk_autotune");
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "gfk_autotune");
+    ctx->threads = bt;
+    ctx->wpt = bw;
+    if (best_threads) *best_threads = bt;
+    if (best_wpt) *best_wpt = bw;
+    if (best_rate) *best_rate = best;
     return GFK_OK;
 }
 

@@ -14,7 +14,7 @@
 //   w      =  2^{(d - S dt) log2 e}      (d = FP64 base minus the warp's shift)
 // Every kRing steps the FP32 sums are folded into the FP64 base,
 //   L <- L - (S + kRing (E_T,fp32 - E_T)) dt            (FP64),
-// the warp's shift c is reset to its largest L and d = (float)(L - c).
+// the warp's shift c is reset to the floor of its largest L and d = (float)(L - c).
 // Per step each warp adds its (w, w E_L, w^2, w E_L^2) in FP32 and counts its
 // live walkers; every kRing steps, after one block barrier, the block rescales
 // each warp's sums to the block's largest shift and adds them in FP64, writing
@@ -187,7 +187,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     for (int k = 0; k < WPT; ++k)
         if (sg[k] != 0) lmax = fmax(lmax, L[k]);
     double c = warp_max(lmax);
-    if (!isfinite(c)) c = 0.0;
+    c = isfinite(c) ? floor(c) : 0.0;      // integer-valued shift
 #pragma unroll
     for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) : 0.f;
     int fold_len = 0;
@@ -288,7 +288,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             }
             fold_len = 0;
             c = warp_max(lmax);
-            if (!isfinite(c)) c = 0.0;
+            c = isfinite(c) ? floor(c) : 0.0;
 #pragma unroll
             for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) : 0.f;
             // one barrier per window: the other buffer takes the next window,

@@ -4,9 +4,13 @@
 // reduce_rows_kernel: for one instance and one step, merges the instance's
 // block records {c_b, W_b, P_b, Q_b, R_b, n_b} into
 //   C = max_b c_b,  W = sum_b W_b e^{c_b - C},  P = sum_b P_b e^{c_b - C},
-//   Q = sum_b Q_b e^{2 (c_b - C)},  R = sum_b R_b e^{c_b - C},  n = sum_b n_b,
-// with every sum carried as an unevaluated double-double (TwoSum), so the
-// merged value is the correctly rounded sum of the block values up to O(2^-100).
+//   Q = sum_b Q_b e^{2 (c_b - C)},  R = sum_b R_b e^{c_b - C},  n = sum_b n_b.
+// W and P (the energy's denominator and numerator) are carried as
+// unevaluated double-doubles (Neumaier compensation per thread, TwoSum across
+// threads), so E = P / W is the quotient of correctly rounded sums up to
+// O(2^-100); Q and R (effective sample size, variance) are plain FP64 sums;
+// n is an integer count, exact in FP64.  The shifts c_b are integer-valued, so
+// a thread recomputes the factor e^{c_b - C} only when the integer changes.
 // finalize_kernel turns merged rows into E(t) = P/W, ln z(t) = C + ln W - ln N
 // and ESS = W^2/Q (Eq. 4's z(t) and the space-averaged energy).
 #include <cuda_runtime.h>
@@ -58,21 +62,37 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) C = fmax(C, s_max[w]);
     if (!isfinite(C)) C = 0.0;
 
-    DD acc[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) acc[k] = DD{0.0, 0.0};
+    // per-thread Neumaier sums for W and P, plain sums for Q, R, n
+    double sW = 0.0, cW = 0.0, sP = 0.0, cP = 0.0, sQ = 0.0, sR = 0.0, sN = 0.0;
+    double last_k = -1.0, f = 0.0;
     for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
         const PartialRec r = rp[b];
         if (!(r.n > 0.0)) continue;
-        const double f = exp(r.c - C);
-        const double v[5] = {r.W * f, r.P * f, r.Q * f * f, r.R * f, r.n};
-#pragma unroll
-        for (int k = 0; k < 5; ++k) acc[k] = dd_add(acc[k], DD{v[k], 0.0});
+        const double k = C - r.c;
+        if (k != last_k) {
+            f = exp(-k);
+            last_k = k;
+        }
+        const double w = r.W * f, p = r.P * f;
+        double t = sW + w;
+        cW += fabs(sW) >= fabs(w) ? (sW - t) + w : (w - t) + sW;
+        sW = t;
+        t = sP + p;
+        cP += fabs(sP) >= fabs(p) ? (sP - t) + p : (p - t) + sP;
+        sP = t;
+        sQ += r.Q * f * f;
+        sR += r.R * f;
+        sN += r.n;
     }
+    DD acc[5] = {{sW, cW}, {sP, cP}, {sQ, 0.0}, {sR, 0.0}, {sN, 0.0}};
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
+        if (k < 2) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[k] = dd_add(acc[k], dd_shfl_xor(acc[k], o));
+            for (int o = 16; o > 0; o >>= 1) acc[k] = dd_add(acc[k], dd_shfl_xor(acc[k], o));
+        } else {
+            acc[k].hi = warp_sum(acc[k].hi);
+        }
         if (lane == 0) s_acc[k][warp] = acc[k];
     }
     __syncthreads();
@@ -80,15 +100,18 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
         DD tot[5];
         for (int k = 0; k < 5; ++k) {
             tot[k] = s_acc[k][0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot[k] = dd_add(tot[k], s_acc[k][w]);
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                if (k < 2) tot[k] = dd_add(tot[k], s_acc[k][w]);
+                else tot[k].hi += s_acc[k][w].hi;
+            }
         }
         SeriesRow out;
         out.c = C;
         out.W = tot[0].hi + tot[0].lo;
         out.P = tot[1].hi + tot[1].lo;
-        out.Q = tot[2].hi + tot[2].lo;
-        out.R = tot[3].hi + tot[3].lo;
-        out.n = tot[4].hi + tot[4].lo;
+        out.Q = tot[2].hi;
+        out.R = tot[3].hi;
+        out.n = tot[4].hi;
         series[(int64_t)inst * series_cap + row_base + row] = out;
     }
 }

@@ -31,7 +31,7 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_energy", "gfk_sums", "gfk_get_walkers", "gfk_counters", "gfk_checkpoint_size",
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
            "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc",
-           "gfk_measure_peak")
+           "gfk_measure_peak", "gfk_set_graph", "gfk_autotune")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
             "i2f", "f2f")
 GFK_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -97,6 +97,9 @@ def load(build_if_needed: bool = True):
             "gfk_status_string": ([c.c_int], c.c_char_p),
             "gfk_last_error": ([P], c.c_char_p),
             "gfk_measure_peak": ([c.c_int32, P, dp], c.c_int),
+            "gfk_set_graph": ([P, c.c_int32], c.c_int),
+            "gfk_autotune": ([P, c.c_int64, c.POINTER(c.c_int32), c.POINTER(c.c_int32), dp],
+                             c.c_int),
             "gfk_propagate_noalloc": ([c.POINTER(gfk_instance_desc), c.c_int32, dp, c.c_int32,
                                        P, P, P, c.c_int32, c.c_int64, c.c_int64, P, P, P],
                                       c.c_int),
@@ -266,6 +269,50 @@ def gfk_propagate_noalloc(desc, kind, params, p0, p1, sgn, init, step0, n_steps,
                                         int(n_steps), addr(rows), addr(counters), stream)
 
 
+def gfk_set_graph(ctx, enable=True):
+    _check(load().gfk_set_graph(ctx, int(bool(enable))), "gfk_set_graph", ctx)
+
+
+def gfk_autotune(ctx, probe_steps=256):
+    """(threads, walkers_per_thread, walker-steps/s) of the fastest launch shape; applied."""
+    t = ctypes.c_int32()
+    w = ctypes.c_int32()
+    r = ctypes.c_double()
+    _check(load().gfk_autotune(ctx, int(probe_steps), ctypes.byref(t), ctypes.byref(w),
+                               ctypes.byref(r)), "gfk_autotune", ctx)
+    return t.value, w.value, r.value
+
+
+def autotune_cached(ctx, descs, trials, probe_steps=256, path=None):
+    """gfk_autotune with a JSON cache keyed by device, precision, trial kinds and walker
+    counts (in the package's build folder); a cached shape is applied without timing."""
+    import json
+    import torch
+    path = path or os.path.join(os.path.dirname(_build.LIB), "autotune.json")
+    key = json.dumps({"device": torch.cuda.get_device_name(),
+                      "prec": int(descs[0].prec),
+                      "kinds": [int(k) for k, _ in trials],
+                      "walkers": [int(d.n_walkers) for d in descs]}, sort_keys=True)
+    cache = {}
+    if os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        t, w, r = cache[key]
+        gfk_set_launch(ctx, t, w)
+        return t, w, r
+    t, w, r = gfk_autotune(ctx, probe_steps)
+    cache[key] = [t, w, r]
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1)
+    os.replace(tmp, path)
+    return t, w, r
+
+
 def gfk_measure_peak(op, stream=None) -> float:
     """Measured lane-operations per second of one instruction class (see PEAK_OPS)."""
     if isinstance(op, str):
@@ -315,6 +362,15 @@ class Context:
 
     def set_launch(self, threads, wpt):
         gfk_set_launch(self.handle, threads, wpt)
+
+    def set_graph(self, enable=True):
+        gfk_set_graph(self.handle, enable)
+
+    def autotune(self, probe_steps=256, cache=True, trials=None):
+        if cache:
+            return autotune_cached(self.handle, self.descs, trials or [(0, None)] * len(self.descs),
+                                   probe_steps)
+        return gfk_autotune(self.handle, probe_steps)
 
     def propagate(self, n_steps):
         gfk_propagate(self.handle, n_steps)

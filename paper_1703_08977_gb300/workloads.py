@@ -72,3 +72,59 @@ def hydrogenic_1s2pz(sign=1.0):
     """1s(Z=2) 2p_z(Z=2) product, (anti)symmetrised: exact eigenfunction without e-e repulsion."""
     return pairs([term(1.0, orb(2.0), orb(1.0, c0=0.0, cz=1.0)),
                   term(sign, orb(1.0, c0=0.0, cz=1.0), orb(2.0))])
+
+
+# ---------------------------------------------------------------------------
+# Benchmark workloads (synthetic, seeded).  Each instance is a plain dict:
+# state (0 = 1^1S, 1 = 2^3S, 2 = P_z), n_walkers, dt, e_trial, seed,
+# rng_stream, kind and params of the trial function.
+# ---------------------------------------------------------------------------
+# Trial energies: the variational energies of the paper's summary table,
+# rounded (they shift every log-weight equally and leave E(t) unchanged).
+E_T = {0: -2.9037, 1: -2.1752, 2: -2.1238}
+
+
+def trial_for_state(state):
+    """The workloads' trial function per state: ground product with Jastrow a=1/2,
+    beta=0.5; the 2^3S antisymmetric 2s-like pair with a=1/4, beta=0.3; the P_z
+    pair with + exchange and the ground Jastrow factor."""
+    return {0: (KIND0, ground()), 1: (KIND1, triplet_2s3()), 2: (KIND1, pz_state(+1.0))}[state]
+
+
+def instance(state, n_walkers, dt, seed=0, rng_stream=0):
+    kind, params = trial_for_state(state)
+    return dict(state=state, n_walkers=int(n_walkers), dt=float(dt), e_trial=E_T[state],
+                seed=int(seed), rng_stream=int(rng_stream), kind=kind, params=params)
+
+
+def ground_fp64_correctness():
+    """He 1^1S in FP64: 4096 walkers, dt 0.01, E_T -2.9, 2000 moves, seed 0."""
+    d = instance(0, 4096, 0.01)
+    d["e_trial"] = -2.9
+    return [d], 2000
+
+
+def ground_at_scale(dt=0.005):
+    """He 1^1S: 2^20 walkers, 20000 moves at dt in {0.005, 0.0025, 0.00125}."""
+    return [instance(0, 1 << 20, dt)], 20000
+
+
+def triplet_at_scale():
+    """He 2^3S with the exact node: 2^20 walkers, dt 0.0025, 20000 moves."""
+    return [instance(1, 1 << 20, 0.0025)], 20000
+
+
+def batched(seed=1, n_moves=10000, scale=1.0):
+    """Twelve instances: {1^1S, 2^3S, P_z} x dt {0.01, 0.005, 0.0025, 0.00125}, walker
+    counts round(2^U) with U ~ U[16, 21] from numpy's default_rng(seed), one Philox
+    stream each.  `scale` shrinks the walker counts for tests."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    i = 0
+    for state in (0, 1, 2):
+        for dt in (0.01, 0.005, 0.0025, 0.00125):
+            n = int(round(2.0 ** rng.uniform(16.0, 21.0) * scale))
+            out.append(instance(state, max(n, 1), dt, seed=0, rng_stream=i))
+            i += 1
+    return out, n_moves

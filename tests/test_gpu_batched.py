@@ -1,0 +1,83 @@
+"""Batched instances, CUDA-graph replay and the autotuner (GPU)."""
+import numpy as np
+import pytest
+
+from paper_1703_08977_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _descs(gfk, insts, prec):
+    return [gfk.InstanceDesc(n_walkers=d["n_walkers"], dt=d["dt"], e_trial=d["e_trial"],
+                             seed=d["seed"], state=d["state"], prec=prec,
+                             rng_stream=d["rng_stream"]) for d in insts]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_matches_direct_launches(gfk_lib, prec):
+    """gfk_set_graph: the captured sequence (init + chunks), and its replay after a reset,
+    give bitwise the walkers and sums of the direct launches."""
+    gfk = gfk_lib
+    insts, _ = wl.batched(scale=1 / 64)
+    descs = _descs(gfk, insts[:5], prec)
+    trials = [(d["kind"], d["params"]) for d in insts[:5]]
+    a = gfk.Context(descs, trials=trials).propagate(100)
+    b = gfk.Context(descs, trials=trials)
+    b.set_graph(True)
+    b.propagate(100)
+    for i in range(5):
+        for u, v in zip(a.walkers(i), b.walkers(i)):
+            np.testing.assert_array_equal(u, v)
+        np.testing.assert_array_equal(a.sums(i), b.sums(i))
+    b.reset()
+    b.propagate(100)          # replays the cached graph
+    for i in range(5):
+        np.testing.assert_array_equal(a.sums(i), b.sums(i))
+    b.propagate(64)           # continues with a new graph
+    a.propagate(64)
+    for i in range(5):
+        np.testing.assert_array_equal(a.sums(i), b.sums(i))
+    a.close()
+    b.close()
+
+
+def test_batched_mixed_instances_match_single(gfk_lib):
+    """The twelve-instance mix in one context (mixed path, one launch per chunk with the
+    trial family dispatched per block) reproduces each instance run alone, walker by
+    walker (positions and log-weights do not depend on the batch or launch shape)."""
+    gfk = gfk_lib
+    insts, _ = wl.batched(scale=1 / 256)
+    descs = _descs(gfk, insts, 1)
+    ctx = gfk.Context(descs, trials=[(d["kind"], d["params"]) for d in insts])
+    ctx.set_graph(True)
+    ctx.propagate(96)
+    for i in (0, 5, 11):
+        d = insts[i]
+        with gfk.Context([descs[i]], trials=[(d["kind"], d["params"])]) as one:
+            one.propagate(96)
+            for u, v in zip(ctx.walkers(i), one.walkers(0)):
+                np.testing.assert_array_equal(u, v)
+            np.testing.assert_allclose(ctx.energy(i)["E"], one.energy(0)["E"], rtol=2e-6)
+    ctx.close()
+
+
+def test_autotune_restores_population(gfk_lib):
+    """gfk_autotune times every launch shape on the live population and restores it:
+    the walk continued after tuning equals an untuned walk."""
+    gfk = gfk_lib
+    insts, _ = wl.batched(scale=1 / 128)
+    descs = _descs(gfk, insts[:4], 1)
+    trials = [(d["kind"], d["params"]) for d in insts[:4]]
+    a = gfk.Context(descs, trials=trials).propagate(64)
+    b = gfk.Context(descs, trials=trials).propagate(64)
+    t, w, rate = gfk.gfk_autotune(b.handle, 64)
+    assert t in (64, 128, 256, 512) and w in (1, 2, 4) and rate > 0
+    a.propagate(64)
+    b.propagate(64)
+    for i in range(4):
+        for u, v in zip(a.walkers(i), b.walkers(i)):
+            np.testing.assert_array_equal(u, v)
+        np.testing.assert_array_equal(a.counters(i), b.counters(i))
+        np.testing.assert_allclose(a.energy(i)["E"], b.energy(i)["E"], rtol=2e-6)
+    a.close()
+    b.close()
