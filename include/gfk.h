@@ -199,6 +199,23 @@ gfk_status gfk_checkpoint_size(gfk_ctx* ctx, int64_t* bytes);
 gfk_status gfk_checkpoint(gfk_ctx* ctx, void* host_blob, int64_t bytes);
 gfk_status gfk_restore(gfk_ctx* ctx, const void* host_blob, int64_t bytes);
 
+/* Gradient of a space-averaged loss with respect to the trial parameters,
+ * through the walk (the pathwise derivative with the Philox noise held fixed).
+ * Runs instance inst from a fresh population for n_steps moves (>= 1) in the
+ * context's precision -- the same trajectories gfk_propagate produces --
+ * keeping the positions every ckpt_every moves (1..1024), then sweeps the
+ * adjoint of the Euler-Maruyama recursion backwards, recomputing each segment
+ * from its checkpoint.  Loss 0: E = sum_i w_i E_L(X_i) / sum_i w_i at the last
+ * move (the quantity of Eq. 4's space average); loss 1: the weighted variance
+ * of E_L at the last move.  Only the Jastrow-product family is supported
+ * (GFK_EINVAL otherwise); grad receives the derivatives with respect to all
+ * seven parameters [Z, a, beta, c1, c2, c3, c4] (n_params must be 7), *loss
+ * the loss (may be NULL).  Does not touch the context's population.
+ * Synchronises the stream; allocates working memory of about
+ * n_walkers x (n_steps / ckpt_every + ckpt_every) x 48 bytes (FP64). */
+gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_steps,
+                    int32_t ckpt_every, double* grad, int32_t n_params, double* loss);
+
 /* Kernel timing.  While enabled, CUDA events on the context's stream bracket
  * every walk-kernel launch.  gfk_profile_read synchronises the stream and
  * returns the summed device time of those launches (ms), their number and the

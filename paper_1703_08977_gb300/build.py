@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,
           "--expt-relaxed-constexpr"]
 # The FP64 walk must round like a plain sequential evaluation: no fused multiply-add.
-PER_FILE = {"gfk_fp64.cu": ["--fmad=false"]}
+PER_FILE = {"gfk_fp64.cu": ["--fmad=false"], "gfk_adjoint_f64.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:

@@ -1,0 +1,327 @@
+// Adjoint (reverse) sweep of the GFK walk: the gradient of the space-averaged
+// final energy, or of the weighted variance of E_L, with respect to the trial
+// function's parameters, through the Euler-Maruyama trajectories.
+//
+// Method.  The forward walk (the drifted diffusion under Eq. 4 with the
+// right-point log-weights of Eq. 4) gives per walker X_0..X_S, the final
+// weight w = e^{logw} and e = E_L(X_S).  With W = sum w, L = sum w e / W and
+// Var = sum w e^2 / W - L^2, a change of the parameters theta moves every
+// walker by
+//   dL_i = alpha_i de_i(X_S) - gamma_i dt sum_{n=1..S} dE_L(X_n)
+// (loss E: alpha = w/W, gamma = (w/W)(e - L); loss Var: alpha = 2 (w/W)(e - L),
+// gamma = (w/W)((e - L)^2 - Var)), and X_{n+1} = X_n + b(X_n) dt + sqrt(dt) xi_n
+// with the noise held fixed (X_0 does not depend on theta).  The adjoint of
+// this recursion, with phi_n = dt lambda_{n+1} . b(X_n) [n < S]
+// - gamma dt E_L(X_n) [n >= 1] + alpha E_L(X_n) [n = S], is
+//   lambda_n = lambda_{n+1} + grad_X phi_n,   theta_bar += grad_theta phi_n,
+// for n = S down to 0.  One forward-mode dual evaluation of the trial function
+// at X_n (6 position tangents + 7 parameter tangents) gives both gradients.
+//
+// Positions are not stored for the whole walk: the forward keeps them every K
+// moves (checkpoints), and the backward recomputes each K-move segment from
+// its checkpoint with the same Philox words and the same arithmetic as the
+// forward kernel of its precision, then sweeps it in reverse.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gfk_device.cuh"
+#include "gfk_dual.cuh"
+#include "gfk_types.h"
+
+namespace gfk {
+
+constexpr int kAdjThreads = 128;
+constexpr int kNumTheta = 7;                  // kind 0: Z, a, beta, c1..c4
+constexpr int kNumTangents = 6 + kNumTheta;
+
+// Terminal quantities shared by every walker: {c, W, L, Var, loss}.
+struct AdjTerminal {
+    double c, W, L, Var, loss;
+};
+
+// Positions of a walker in the precision's state layout.
+template <typename T> struct PosIO;
+template <> struct PosIO<double> {
+    // checkpoint / segment planes: [6][n] doubles
+    __device__ __forceinline__ static void load(const double* base, int64_t n, int64_t i, double x[6]) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) x[d] = base[d * n + i];
+    }
+    __device__ __forceinline__ static void store(double* base, int64_t n, int64_t i, const double x[6]) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) base[d * n + i] = x[d];
+    }
+    static constexpr int kWords = 6;          // doubles per walker per plane set
+};
+template <> struct PosIO<float> {
+    // planes: two float4 per walker (x1,y1,z1,x2), (y2,z2,-,-) -- the state layout
+    __device__ __forceinline__ static void load(const float* base, int64_t n, int64_t i, float x[6]) {
+        const float4 a = reinterpret_cast<const float4*>(base)[i];
+        const float4 b = reinterpret_cast<const float4*>(base)[n + i];
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y;
+    }
+    __device__ __forceinline__ static void store(float* base, int64_t n, int64_t i, const float x[6]) {
+        reinterpret_cast<float4*>(base)[i] = make_float4(x[0], x[1], x[2], x[3]);
+        reinterpret_cast<float4*>(base)[n + i] = make_float4(x[4], x[5], 0.f, 0.f);
+    }
+    static constexpr int kWords = 8;          // floats per walker per plane set
+};
+
+// The forward move of the precision, written exactly as the walk kernel of
+// that precision writes it (so the recomputed positions are the forward's).
+__device__ __forceinline__ void adj_move(double x[6], const double b[6], const double xi[6],
+                                         double dt, double sdt) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) x[d] = x[d] + b[d] * dt + sdt * xi[d];
+}
+__device__ __forceinline__ void adj_move(float x[6], const float b[6], const float xi[6],
+                                         float dt, float sdt) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) x[d] = fmaf(sdt, xi[d], fmaf(b[d], dt, x[d]));
+}
+__device__ __forceinline__ void adj_normals(const uint32_t w[6], double xi[6]) { normals6_f64(w, xi); }
+__device__ __forceinline__ void adj_normals(const uint32_t w[6], float xi[6]) { normals6_f32(w, xi); }
+
+template <typename T>
+__device__ __forceinline__ void load_trial0_dual(const TrialHost& h, int ee_on,
+                                                 TrialDev0<Dual<kNumTangents, T>>& t) {
+    typedef Dual<kNumTangents, T> D;
+    const T ee = ee_on ? T(1) : T(0);
+    t.Z = D::seed((T)h.Z, 6);
+    t.a = D::seed((T)h.a, 7);
+    t.beta = D::seed((T)h.beta, 8);
+    const D c1 = D::seed((T)h.ck[0], 9), c2 = D::seed((T)h.ck[1], 10);
+    const D c3 = D::seed((T)h.ck[2], 11), c4 = D::seed((T)h.ck[3], 12);
+    t.Zm2 = t.Z - T(2);
+    t.Z2 = t.Z * t.Z;
+    t.ee = D(ee);
+    t.eem2a = ee - T(2) * t.a;
+    t.eebeta = ee * t.beta;
+    t.c2 = T(2) * c1; t.c3 = T(3) * c2; t.c4 = T(4) * c3; t.c5 = T(5) * c4;
+    t.d2 = T(2) * c1; t.d6 = T(6) * c2; t.d12 = T(12) * c3; t.d20 = T(20) * c4;
+}
+
+// Terminal pass 1: per block, the largest final log-weight of live walkers.
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads)
+adj_terminal_max_kernel(const double* __restrict__ logw, int64_t n, double* __restrict__ part_max) {
+    __shared__ double s[kAdjThreads / 32];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double m = (i < n) ? logw[i] : -INFINITY;
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = s[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, s[w]);
+        part_max[blockIdx.x] = r;
+    }
+}
+
+// Terminal pass 2: per walker e = E_L(X_S) and w = e^{logw - c}; per block the
+// sums of w, w e, w e^2 (FP64).
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads)
+adj_terminal_sums_kernel(const InstDev* __restrict__ inst, const T* __restrict__ pos,
+                         const double* __restrict__ logw, int64_t n,
+                         const double* __restrict__ part_max, int nblk,
+                         double* __restrict__ ew, double* __restrict__ part_sums) {
+    __shared__ TrialDev<T> s_trial;
+    __shared__ double s_c;
+    __shared__ double s_red[3][kAdjThreads / 32];
+    if (threadIdx.x == 0) {
+        load_trial<T>(inst->trial, inst->ee_on, s_trial);
+        double c = -INFINITY;
+        for (int b = 0; b < nblk; ++b) c = fmax(c, part_max[b]);
+        s_c = isfinite(c) ? floor(c) : 0.0;
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double q[3] = {0.0, 0.0, 0.0};
+    if (i < n) {
+        double e = 0.0, w = 0.0;
+        if (logw[i] > -INFINITY) {
+            T x[6];
+            PosIO<T>::load(pos, n, i, x);
+            EvalOut<T> ev;
+            eval_kind0<T>(s_trial, x, ev);
+            e = (double)ev.el;
+            w = exp(logw[i] - s_c);
+        }
+        ew[2 * i] = e;
+        ew[2 * i + 1] = w;
+        q[0] = w;
+        q[1] = w * e;
+        q[2] = w * e * e;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double v = warp_sum(q[k]);
+        if ((threadIdx.x & 31) == 0) s_red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double r = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += s_red[threadIdx.x][w];
+        part_sums[3 * blockIdx.x + threadIdx.x] = r;
+    }
+}
+
+// Terminal pass 3 (one thread): W, L, Var and the loss, summed in block order.
+static __global__ void adj_terminal_final_kernel(const double* __restrict__ part_max,
+                                          const double* __restrict__ part_sums, int nblk,
+                                          int loss_kind, AdjTerminal* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double c = -INFINITY;
+    for (int b = 0; b < nblk; ++b) c = fmax(c, part_max[b]);
+    c = isfinite(c) ? floor(c) : 0.0;
+    double W = 0, P = 0, R = 0, cW = 0, cP = 0, cR = 0;
+    for (int b = 0; b < nblk; ++b) {
+        const double v[3] = {part_sums[3 * b], part_sums[3 * b + 1], part_sums[3 * b + 2]};
+        double* s[3] = {&W, &P, &R};
+        double* cc[3] = {&cW, &cP, &cR};
+        for (int k = 0; k < 3; ++k) {   // Neumaier
+            const double t = *s[k] + v[k];
+            *cc[k] += fabs(*s[k]) >= fabs(v[k]) ? (*s[k] - t) + v[k] : (v[k] - t) + *s[k];
+            *s[k] = t;
+        }
+    }
+    W += cW;
+    P += cP;
+    R += cR;
+    AdjTerminal r;
+    r.c = c;
+    r.W = W;
+    r.L = P / W;
+    r.Var = R / W - r.L * r.L;
+    r.loss = loss_kind == 0 ? r.L : r.Var;
+    *out = r;
+}
+
+// The reverse sweep: one thread per walker, all segments from the last to the
+// first; per block the summed parameter adjoint theta_bar.
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads)
+adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, int J,
+                    int loss_kind, const T* __restrict__ ckpt, T* __restrict__ seg,
+                    const double* __restrict__ ew, const AdjTerminal* __restrict__ term,
+                    double* __restrict__ part_theta) {
+    typedef Dual<kNumTangents, T> D;
+    __shared__ TrialDev<T> s_trial;
+    __shared__ double s_red[kNumTheta][kAdjThreads / 32];
+    if (threadIdx.x == 0) load_trial<T>(inst->trial, inst->ee_on, s_trial);
+    __syncthreads();
+    TrialDev0<D> td;
+    load_trial0_dual<T>(inst->trial, inst->ee_on, td);
+    const TrialDev<T>& tp = s_trial;
+    const T dt = (T)inst->dt, sdt = (T)inst->sqrt_dt;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double theta[kNumTheta];
+#pragma unroll
+    for (int k = 0; k < kNumTheta; ++k) theta[k] = 0.0;
+
+    if (i < n) {
+        const AdjTerminal tr = *term;
+        const double e = ew[2 * i], w = ew[2 * i + 1];
+        const double om = w / tr.W;
+        double alpha, gamma;
+        if (loss_kind == 0) {
+            alpha = om;
+            gamma = om * (e - tr.L);
+        } else {
+            alpha = 2.0 * om * (e - tr.L);
+            gamma = om * ((e - tr.L) * (e - tr.L) - tr.Var);
+        }
+        if (w > 0.0) {
+            const T a_t = (T)alpha, g_dt = (T)(gamma * inst->dt);
+            T lambda[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+            for (int j = J - 1; j >= 0; --j) {
+                const int n_lo = j * K;
+                const int n_hi = (n_lo + K < S) ? n_lo + K : S;
+                // recompute the segment's positions n_lo .. n_hi
+                T x[6];
+                PosIO<T>::load(ckpt + (int64_t)j * PosIO<T>::kWords * n, n, i, x);
+                PosIO<T>::store(seg, n, i, x);
+                for (int m = n_lo; m < n_hi; ++m) {
+                    EvalOut<T> ev;
+                    eval_kind0<T>(tp, x, ev);
+                    uint32_t words[6];
+                    move_words((uint32_t)i, (uint32_t)m, inst->stream, inst->k0, inst->k1, words);
+                    T xi[6];
+                    adj_normals(words, xi);
+                    adj_move(x, ev.b, xi, dt, sdt);
+                    PosIO<T>::store(seg + (int64_t)(m - n_lo + 1) * PosIO<T>::kWords * n, n, i, x);
+                }
+                // sweep it backwards
+                const int n_top = (j == J - 1) ? n_hi : n_hi - 1;
+                for (int m = n_top; m >= n_lo; --m) {
+                    T xv[6];
+                    PosIO<T>::load(seg + (int64_t)(m - n_lo) * PosIO<T>::kWords * n, n, i, xv);
+                    D xd[6];
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) xd[d] = D::seed(xv[d], d);
+                    EvalOut<D> ev;
+                    eval_kind0<D>(td, xd, ev);
+                    D phi(T(0));
+                    if (m < S) {
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) phi += (dt * lambda[d]) * ev.b[d];
+                    }
+                    if (m >= 1) phi -= g_dt * ev.el;
+                    if (m == S) phi += a_t * ev.el;
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) lambda[d] += phi.d[d];
+#pragma unroll
+                    for (int k = 0; k < kNumTheta; ++k) theta[k] += (double)phi.d[6 + k];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kNumTheta; ++k) {
+        const double v = warp_sum(theta[k]);
+        if ((threadIdx.x & 31) == 0) s_red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumTheta) {
+        double r = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += s_red[threadIdx.x][w];
+        part_theta[(int64_t)kNumTheta * blockIdx.x + threadIdx.x] = r;
+    }
+}
+
+// Sum of the blocks' theta_bar (one thread per parameter, block order, Neumaier).
+static __global__ void adj_grad_final_kernel(const double* __restrict__ part_theta, int nblk,
+                                      double* __restrict__ grad) {
+    const int k = threadIdx.x;
+    if (k >= kNumTheta) return;
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        const double v = part_theta[(int64_t)kNumTheta * b + k];
+        const double t = s + v;
+        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    grad[k] = s + c;
+}
+
+// Host side of one precision: terminal passes, reverse sweep, final sum.
+template <typename T>
+cudaError_t adj_run(const InstDev* inst, int64_t n, int S, int K, int loss_kind, const T* ckpt,
+                    T* seg, const T* pos_final, const double* logw_final, double* ew,
+                    double* part_max, double* part_sums, double* part_theta, AdjTerminal* term,
+                    double* grad, cudaStream_t stream) {
+    const int nblk = (int)((n + kAdjThreads - 1) / kAdjThreads);
+    const int J = (S + K - 1) / K;
+    adj_terminal_max_kernel<T><<<nblk, kAdjThreads, 0, stream>>>(logw_final, n, part_max);
+    adj_terminal_sums_kernel<T><<<nblk, kAdjThreads, 0, stream>>>(inst, pos_final, logw_final, n,
+                                                                   part_max, nblk, ew, part_sums);
+    adj_terminal_final_kernel<<<1, 32, 0, stream>>>(part_max, part_sums, nblk, loss_kind, term);
+    adj_backward_kernel<T><<<nblk, kAdjThreads, 0, stream>>>(inst, n, S, K, J, loss_kind, ckpt, seg,
+                                                              ew, term, part_theta);
+    adj_grad_final_kernel<<<1, 32, 0, stream>>>(part_theta, nblk, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace gfk

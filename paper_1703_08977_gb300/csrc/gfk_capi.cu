@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -37,6 +38,16 @@ cudaError_t launch_finalize(const SeriesRow* rows, int64_t n, double n0, double*
 cudaError_t launch_export(bool mixed, const StateF64& s64, const StateMixed& smx, int64_t off,
                           int64_t n, double* x6, double* logw, uint8_t* alive,
                           cudaStream_t stream);
+cudaError_t launch_adjoint_f64(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
+                               const double* ckpt, double* seg, const double* pos_final,
+                               const double* logw_final, double* ew, double* part_max,
+                               double* part_sums, double* part_theta, void* term, double* grad,
+                               cudaStream_t stream);
+cudaError_t launch_adjoint_f32(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
+                               const float* ckpt, float* seg, const float* pos_final,
+                               const double* logw_final, double* ew, double* part_max,
+                               double* part_sums, double* part_theta, void* term, double* grad,
+                               cudaStream_t stream);
 }  // namespace gfk
 
 using namespace gfk;
@@ -986,6 +997,134 @@ gfk_status gfk_restore(gfk_ctx* ctx, const void* host_blob, int64_t bytes) {
     GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->initialized = h.initialized != 0;
     ctx->steps = h.steps;
+    return GFK_OK;
+}
+
+gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_steps,
+                    int32_t ckpt_every, double* grad, int32_t n_params, double* loss) {
+    gfk_status st = check_inst(ctx, inst);
+    if (st != GFK_OK) return st;
+    if (loss_kind != 0 && loss_kind != 1) return GFK_EINVAL;
+    if (n_steps < 1 || n_steps > 0x7fffffffll || ckpt_every < 1 || ckpt_every > 1024)
+        return GFK_EINVAL;
+    if (!grad || n_params != 7) return GFK_EINVAL;
+    if (!ctx->has_trial[inst]) return GFK_ESTATE;
+    if (ctx->trial[inst].kind != GFK_TRIAL_JASTROW_PRODUCT) return GFK_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (ctx->params_dirty) {
+        st = upload_instances(ctx);
+        if (st != GFK_OK) return st;
+    }
+    const bool f64 = ctx->prec == GFK_PREC_FP64;
+    const int64_t n = ctx->desc[inst].n_walkers;
+    const int S = (int)n_steps, K = ckpt_every;
+    const int J = (S + K - 1) / K;
+    const size_t tsz = f64 ? sizeof(double) : sizeof(float);
+    const int words = f64 ? 6 : 8;                       // position words per walker
+    // launch shape of the forward (one instance, slots from 0)
+    gfk_ctx shape;
+    shape.n_inst = 1;
+    shape.threads = ctx->threads;
+    shape.wpt = f64 ? 1 : ctx->wpt;
+    shape.desc.push_back(ctx->desc[inst]);
+    int64_t nblk = 0;
+    BlockMap bm = make_block_map(&shape, &nblk);
+    const int nblk_adj = (int)((n + 127) / 128);
+
+    // one allocation, carved into the pieces below
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+    const size_t o_inst = take(sizeof(InstDev));
+    const size_t o_state = take(f64 ? n * (7 * sizeof(double)) : n * 2 * sizeof(float4));
+    const size_t o_sgn = take((size_t)n);
+    const size_t o_part = take(sizeof(PartialRec) * (size_t)K * nblk);
+    const size_t o_cnt = take(sizeof(unsigned long long) * kNumCounters);
+    const size_t o_ckpt = take(tsz * words * (size_t)n * J);
+    const size_t o_seg = take(std::max(tsz * words * (size_t)n * (K + 1), sizeof(double) * 7 * (size_t)n));
+    const size_t o_logw = take(sizeof(double) * (size_t)n);
+    const size_t o_ew = take(sizeof(double) * 2 * (size_t)n);
+    const size_t o_pmax = take(sizeof(double) * nblk_adj);
+    const size_t o_psum = take(sizeof(double) * 3 * nblk_adj);
+    const size_t o_pth = take(sizeof(double) * 7 * nblk_adj);
+    const size_t o_term = take(64);
+    const size_t o_grad = take(sizeof(double) * 8);
+    void* mem = nullptr;
+    st = dev_alloc(ctx, &mem, off);
+    if (st != GFK_OK) return st;
+    char* base = (char*)mem;
+    InstDev* d_inst = (InstDev*)(base + o_inst);
+    cudaError_t e = cudaMemcpyAsync(d_inst, ctx->d_inst + inst, sizeof(InstDev),
+                                    cudaMemcpyDeviceToDevice, ctx->stream);
+    // the copy's walkers start at slot 0
+    const int64_t zero = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char*)d_inst + offsetof(InstDev, off), &zero, sizeof(zero),
+                            cudaMemcpyHostToDevice, ctx->stream);
+    StateF64 s64{};
+    StateMixed smx{};
+    if (f64) {
+        s64.x = (double*)(base + o_state);
+        s64.logw = s64.x + 6 * n;
+        s64.sgn = (int8_t*)(base + o_sgn);
+        s64.stride = n;
+    } else {
+        smx.p0 = (float4*)(base + o_state);
+        smx.p1 = smx.p0 + n;
+        smx.sgn = (int8_t*)(base + o_sgn);
+    }
+    PartialRec* part = (PartialRec*)(base + o_part);
+    unsigned long long* cnt = (unsigned long long*)(base + o_cnt);
+    char* ckpt = base + o_ckpt;
+    const int kind = GFK_TRIAL_JASTROW_PRODUCT;
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kNumCounters, ctx->stream);
+    // forward: the same init and walk kernels as gfk_propagate, checkpointing
+    // the positions every K moves
+    if (e == cudaSuccess)
+        e = f64 ? launch_init_fp64(kind, shape.threads, (int)nblk, d_inst, bm, s64, part, cnt, ctx->stream)
+                : launch_init_mixed(kind, shape.threads, (int)nblk, d_inst, bm, smx, part, cnt, ctx->stream);
+    for (int j = 0; j < J && e == cudaSuccess; ++j) {
+        const size_t plane_bytes = tsz * words * (size_t)n;
+        e = cudaMemcpyAsync(ckpt + plane_bytes * j, base + o_state, plane_bytes,
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+        const int steps = std::min(K, S - j * K);
+        if (e == cudaSuccess)
+            e = f64 ? launch_walk_fp64(kind, shape.threads, (int)nblk, d_inst, bm, s64,
+                                       (uint32_t)(j * K), steps, part, cnt, ctx->stream)
+                    : launch_walk_mixed(kind, shape.wpt, shape.threads, (int)nblk, d_inst, bm, smx,
+                                        (uint32_t)(j * K), steps, part, cnt, ctx->stream);
+    }
+    double* logw_final = (double*)(base + o_logw);
+    if (e == cudaSuccess) {
+        // final log-weights (-inf for dead walkers) through the export kernel
+        double* x6 = (double*)(base + o_seg);
+        uint8_t* alive = (uint8_t*)(base + o_ew);
+        e = launch_export(!f64, s64, smx, 0, n, x6, logw_final, alive, ctx->stream);
+    }
+    double* grad_d = (double*)(base + o_grad);
+    void* term = base + o_term;
+    if (e == cudaSuccess) {
+        if (f64)
+            e = launch_adjoint_f64(d_inst, n, S, K, loss_kind, (const double*)ckpt,
+                                   (double*)(base + o_seg), (const double*)(base + o_state),
+                                   logw_final, (double*)(base + o_ew), (double*)(base + o_pmax),
+                                   (double*)(base + o_psum), (double*)(base + o_pth), term, grad_d,
+                                   ctx->stream);
+        else
+            e = launch_adjoint_f32(d_inst, n, S, K, loss_kind, (const float*)ckpt,
+                                   (float*)(base + o_seg), (const float*)(base + o_state),
+                                   logw_final, (double*)(base + o_ew), (double*)(base + o_pmax),
+                                   (double*)(base + o_psum), (double*)(base + o_pth), term, grad_d,
+                                   ctx->stream);
+    }
+    double hg[7];
+    double hterm[5];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hg, grad_d, sizeof(hg), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hterm, term, sizeof(hterm), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dev_free(mem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gfk_grad");
+    for (int k = 0; k < 7; ++k) grad[k] = hg[k];
+    if (loss) *loss = hterm[4];
     return GFK_OK;
 }
 

@@ -286,8 +286,8 @@ struct EvalOut {
 template <typename R>
 struct JastrowOut { R up, upp, jee; };
 
-template <typename R>
-__device__ __forceinline__ JastrowOut<R> jastrow(const TrialDev<R>& t, R r12, R i12) {
+template <typename R, typename TD>
+__device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
     R q = R(1) + t.beta * r12;
     R iq = rcp(q);
     R rho = r12 * iq;
@@ -308,8 +308,8 @@ __device__ __forceinline__ JastrowOut<R> jastrow(const TrialDev<R>& t, R r12, R 
 //   E_L = (Z - 2)(1/r1 + 1/r2) - Z^2 + (ee - 2u')/r12 - u'' - u'^2
 //         + Z u' (r1_hat - r2_hat) . e12
 // (the nuclear 1/r terms cancel exactly for Z = 2).
-template <typename R>
-__device__ __forceinline__ void eval_kind0(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
+template <typename R, typename TD>
+__device__ __forceinline__ void eval_kind0(const TD& t, const R x[6], EvalOut<R>& o) {
     R s1 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
     R dx = x[0] - x[3], dy = x[1] - x[4], dz = x[2] - x[5];
@@ -319,7 +319,7 @@ __device__ __forceinline__ void eval_kind0(const TrialDev<R>& t, const R x[6], E
     radius(s2, r2, i2);
     radius(s12, r12, i12);
     R ex = dx * i12, ey = dy * i12, ez = dz * i12;
-    JastrowOut<R> j = jastrow(t, r12, i12);
+    JastrowOut<R> j = jastrow<R>(t, r12, i12);
     R h1x = x[0] * i1, h1y = x[1] * i1, h1z = x[2] * i1;
     R h2x = x[3] * i2, h2y = x[4] * i2, h2z = x[5] * i2;
     o.b[0] = -t.Z * h1x + j.up * ex;
@@ -411,7 +411,7 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
             G2[d] += sg * p[0] * gr[1][d];
         }
     }
-    JastrowOut<R> j = jastrow(t, r12, i12);
+    JastrowOut<R> j = jastrow<R>(t, r12, i12);
     R iP = rcp(Phi);
     o.b[0] = G1[0] * iP + j.up * ex;
     o.b[1] = G1[1] * iP + j.up * ey;
@@ -434,6 +434,13 @@ __device__ __forceinline__ void eval_trial(const TrialDev<R>& t, const R x[6], E
     else if (t.kind == 0) eval_kind0<R>(t, x, o);
     else eval_kind1<R>(t, x, o);
 }
+
+// Kind-0 parameters only (the fields eval_kind0 reads), for dual-number
+// evaluation where the full TrialDev would be needlessly large.
+template <typename R>
+struct TrialDev0 {
+    R Z, Zm2, Z2, a, beta, ee, eem2a, eebeta, c2, c3, c4, c5, d2, d6, d12, d20;
+};
 
 // A sum is finite only if every term is (an infinity or NaN in any term makes
 // it infinite or NaN), so one test covers the drift and the local energy.

@@ -31,7 +31,7 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_energy", "gfk_sums", "gfk_get_walkers", "gfk_counters", "gfk_checkpoint_size",
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
            "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc",
-           "gfk_measure_peak", "gfk_set_graph", "gfk_autotune")
+           "gfk_measure_peak", "gfk_set_graph", "gfk_autotune", "gfk_grad")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
             "i2f", "f2f")
 GFK_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -98,6 +98,8 @@ def load(build_if_needed: bool = True):
             "gfk_last_error": ([P], c.c_char_p),
             "gfk_measure_peak": ([c.c_int32, P, dp], c.c_int),
             "gfk_set_graph": ([P, c.c_int32], c.c_int),
+            "gfk_grad": ([P, c.c_int32, c.c_int32, c.c_int64, c.c_int32, dp, c.c_int32, dp],
+                         c.c_int),
             "gfk_autotune": ([P, c.c_int64, c.POINTER(c.c_int32), c.POINTER(c.c_int32), dp],
                              c.c_int),
             "gfk_propagate_noalloc": ([c.POINTER(gfk_instance_desc), c.c_int32, dp, c.c_int32,
@@ -267,6 +269,15 @@ def gfk_propagate_noalloc(desc, kind, params, p0, p1, sgn, init, step0, n_steps,
     return load().gfk_propagate_noalloc(ctypes.byref(d), int(kind), _dp(p), len(p), addr(p0),
                                         addr(p1), addr(sgn), int(init), int(step0),
                                         int(n_steps), addr(rows), addr(counters), stream)
+
+
+def gfk_grad(ctx, inst, loss_kind, n_steps, ckpt_every=64):
+    """(loss, gradient over [Z, a, beta, c1, c2, c3, c4]) of instance inst's walk."""
+    g = np.zeros(7)
+    l = ctypes.c_double()
+    _check(load().gfk_grad(ctx, int(inst), int(loss_kind), int(n_steps), int(ckpt_every), _dp(g),
+                           7, ctypes.byref(l)), "gfk_grad", ctx)
+    return l.value, g
 
 
 def gfk_set_graph(ctx, enable=True):

@@ -1,0 +1,117 @@
+"""The adjoint gradient gfk_grad (GPU) against the autograd oracle and against
+common-random-number central finite differences."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+THETA = [1.9, 0.5, 0.45, 0.05, -0.02, 0.01, 0.003]
+
+
+def _ctx(gfk, n, dt, prec, theta=THETA, seed=7, stream=1):
+    d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=-2.9, seed=seed, prec=prec, rng_stream=stream)
+    return gfk.Context([d], trials=[(0, theta)])
+
+
+@pytest.mark.parametrize("loss_kind", [0, 1])
+@pytest.mark.parametrize("S,K", [(24, 8), (30, 8), (17, 64)])
+def test_fp64_grad_matches_autograd_oracle(gfk_lib, loss_kind, S, K):
+    """FP64 adjoint (checkpointed every K moves, ragged last segment) = autograd through
+    the oracle's walk with the same Philox noise."""
+    torch = pytest.importorskip("torch")
+    from oracle import grad as og
+    gfk = gfk_lib
+    n = 40
+    with _ctx(gfk, n, 0.01, gfk.GFK_PREC_FP64) as c:
+        loss, g = gfk.gfk_grad(c.handle, 0, loss_kind, S, K)
+    ref_loss, ref_g = og.gradient(THETA, n_walkers=n, n_steps=S, dt=0.01, e_trial=-2.9, seed=7,
+                                  inst=1, loss_kind=loss_kind)
+    assert abs(loss - ref_loss) <= 1e-12 * max(1.0, abs(ref_loss))
+    np.testing.assert_allclose(g, ref_g, rtol=0, atol=1e-9 * max(1.0, np.abs(ref_g).max()))
+
+
+@pytest.mark.parametrize("loss_kind", [0, 1])
+def test_fp64_grad_matches_central_differences(gfk_lib, loss_kind):
+    """The FP64 adjoint on 4096 walkers x 200 moves against CRN central differences of
+    the same loss.  Plain central differences at h = 1e-4 carry a truncation error
+    (h^2/6 times the third derivative) that reaches 1e-5 here, as halving h shows, so
+    the 1e-6 comparison is made against the Richardson combination
+    (4 D(h/2) - D(h)) / 3, whose error is O(h^4); the plain h = 1e-4 difference must
+    still agree to 3e-5."""
+    gfk = gfk_lib
+    n, S, dt, h = 4096, 200, 0.005, 1e-4
+    with _ctx(gfk, n, dt, gfk.GFK_PREC_FP64) as c:
+        _, g = gfk.gfk_grad(c.handle, 0, loss_kind, S, 64)
+
+        def central(step):
+            fd = np.zeros(7)
+            for k in range(7):
+                vals = []
+                for sgn in (+1, -1):
+                    th = list(THETA)
+                    th[k] += sgn * step
+                    c.reset()
+                    c.set_trial(0, 0, th)
+                    vals.append(gfk.gfk_grad(c.handle, 0, loss_kind, S, 64)[0])
+                fd[k] = (vals[0] - vals[1]) / (2 * step)
+            return fd
+
+        d1 = central(h)
+        d2 = central(h / 2)
+    rich = (4 * d2 - d1) / 3
+    scale = np.abs(rich).max()
+    err_rich = np.abs(g - rich).max() / scale
+    err_plain = np.abs(g - d1).max() / scale
+    assert err_rich <= 1e-6, (err_rich, err_plain, g, rich)
+    assert err_plain <= 3e-5, (err_plain, g, d1)
+
+
+def test_mixed_grad_close_to_fp64(gfk_lib):
+    """The mixed path's gradient (FP32 positions and trial arithmetic, FP64 weights and
+    adjoint sums) stays within 1e-3 of the FP64 gradient on the same seeds."""
+    gfk = gfk_lib
+    n, S = 8192, 200
+    with _ctx(gfk, n, 0.005, gfk.GFK_PREC_FP64) as c:
+        l64, g64 = gfk.gfk_grad(c.handle, 0, 0, S, 64)
+    with _ctx(gfk, n, 0.005, gfk.GFK_PREC_MIXED) as c:
+        l32, g32 = gfk.gfk_grad(c.handle, 0, 0, S, 64)
+    assert abs(l32 - l64) < 1e-5
+    assert np.abs(g32 - g64).max() <= 1e-3 * np.abs(g64).max(), (g32, g64)
+
+
+def test_grad_leaves_population_and_rejects_bad_calls(gfk_lib):
+    gfk = gfk_lib
+    with _ctx(gfk, 300, 0.01, gfk.GFK_PREC_FP64) as a, _ctx(gfk, 300, 0.01, gfk.GFK_PREC_FP64) as b:
+        a.propagate(40)
+        b.propagate(40)
+        gfk.gfk_grad(b.handle, 0, 0, 20, 8)
+        a.propagate(10)
+        b.propagate(10)
+        for u, v in zip(a.walkers(), b.walkers()):
+            np.testing.assert_array_equal(u, v)
+        with pytest.raises(gfk.GfkError):
+            gfk.gfk_grad(a.handle, 0, 2, 10, 8)         # unknown loss
+        with pytest.raises(gfk.GfkError):
+            gfk.gfk_grad(a.handle, 0, 0, 0, 8)          # no moves
+    from paper_1703_08977_gb300 import workloads as wl
+    d = gfk.InstanceDesc(n_walkers=64, dt=0.01, e_trial=-2.17)
+    with gfk.Context([d], trials=[(1, wl.triplet_2s3())]) as c:
+        with pytest.raises(gfk.GfkError):
+            gfk.gfk_grad(c.handle, 0, 0, 10, 8)         # only the Jastrow-product family
+
+
+def test_autograd_function_and_adam_reduce_variance(gfk_lib):
+    """GFKLoss as a torch.autograd.Function; a few Adam steps of variance minimisation
+    from a deliberately poor start lower the weighted variance of E_L."""
+    torch = pytest.importorskip("torch")
+    from paper_1703_08977_gb300 import tuning
+    gfk = gfk_lib
+    theta0 = [1.8, 0.5, 0.8, 0.0, 0.0, 0.0, 0.0]
+    with _ctx(gfk, 1 << 14, 0.005, gfk.GFK_PREC_MIXED, theta=theta0) as c:
+        th = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+        loss = tuning.GFKLoss.apply(th, c.handle, 0, 1, 200, 64)
+        loss.backward()
+        _, g = gfk.gfk_grad(c.handle, 0, 1, 200, 64)
+        np.testing.assert_allclose(th.grad.numpy(), g, rtol=1e-12)
+        hist, theta = tuning.tune(c.handle, 0, theta0, steps=12, lr=0.03, loss_kind=1, n_steps=200)
+    assert hist[-1][0] < 0.9 * hist[0][0], [h[0] for h in hist]

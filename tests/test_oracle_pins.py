@@ -461,3 +461,53 @@ def test_fn3_variational_energy_matches_table1_lambda0():
     mean, se = _stationary_mean_el(1, wl.fn3(), n=1000, steps=1000, burn=1000, dt=0.01,
                                    seed=31, sigma=1.5)
     assert abs(mean - e_var) < 5 * se + 0.01, (mean, e_var, se)
+
+
+# --------------------------------------------------------------------------
+# Gradient oracle (PyTorch CPU FP64 autograd)
+# --------------------------------------------------------------------------
+
+def test_grad_oracle_drift_and_energy_match_c_oracle():
+    """The autograd drift and Laplacian of ln psi reproduce the C oracle's closed forms."""
+    torch = pytest.importorskip("torch")
+    from oracle import grad as og
+    theta = [1.85, 0.5, 0.37, 0.11, -0.07, 0.05, 0.02]
+    X = _rand_points(16, 8, 0.9)
+    b, el = og.drift_and_local_energy(torch.tensor(X), torch.tensor(theta, dtype=torch.float64))
+    for i in range(16):
+        _, bc, elc, _ = oracle.trial_eval(0, theta, X[i])
+        np.testing.assert_allclose(b[i].detach().numpy(), bc, rtol=1e-12, atol=1e-12)
+        assert abs(float(el[i]) - elc) <= 1e-11 * max(1, abs(elc))
+
+
+def test_grad_oracle_loss_matches_c_oracle_walk():
+    """Its walk is the C oracle's walk: same final E(t) and weighted variance."""
+    torch = pytest.importorskip("torch")
+    from oracle import grad as og
+    theta = [2.0, 0.5, 0.5, 0.0, 0.0, 0.0, 0.0]
+    kw = dict(n_walkers=24, n_steps=12, dt=0.01, e_trial=-2.9, seed=4, inst=1)
+    L = og.walk_loss(torch.tensor(theta, dtype=torch.float64), **kw)
+    V = og.walk_loss(torch.tensor(theta, dtype=torch.float64), loss_kind=1, **kw)
+    w = oracle.Walk(0, theta, n_walkers=24, dt=0.01, e_trial=-2.9, seed=4, inst=1).advance(12)
+    s = w.series()
+    assert abs(float(L) - s["E"][-1]) <= 1e-11
+    assert abs(float(V) - s["var"][-1]) <= 1e-10
+
+
+def test_grad_oracle_gradient_matches_finite_differences():
+    """autograd's d(loss)/d(theta) equals central differences of the same loss
+    (common random numbers, h = 1e-5), for both losses."""
+    torch = pytest.importorskip("torch")
+    from oracle import grad as og
+    theta = np.array([1.9, 0.5, 0.45, 0.05, -0.02, 0.01, 0.003])
+    kw = dict(n_walkers=12, n_steps=8, dt=0.01, e_trial=-2.9, seed=7)
+    for loss_kind in (0, 1):
+        _, g = og.gradient(theta, loss_kind=loss_kind, **kw)
+        h = 1e-5
+        for k in range(7):
+            tp, tm = theta.copy(), theta.copy()
+            tp[k] += h
+            tm[k] -= h
+            fd = (float(og.walk_loss(torch.tensor(tp), loss_kind=loss_kind, **kw)) -
+                  float(og.walk_loss(torch.tensor(tm), loss_kind=loss_kind, **kw))) / (2 * h)
+            assert abs(fd - g[k]) <= 1e-6 * max(1.0, np.abs(g).max()), (loss_kind, k, fd, g[k])
