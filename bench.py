@@ -185,7 +185,9 @@ def _workload(name, rank):
     else:
         insts, moves = wl.batched()
     for d in insts:
-        d["rng_stream"] += 1000 * rank     # each rank its own walkers (weak scaling)
+        # each rank advances its own walker ids of one global population
+        # (weak scaling: the population grows with the number of ranks)
+        d["walker_id0"] = rank * d["n_walkers"]
     return insts, moves
 
 
@@ -210,7 +212,8 @@ def run_ours(args):
     def descs(prec):
         return [gfk.InstanceDesc(n_walkers=d["n_walkers"], dt=d["dt"], e_trial=d["e_trial"],
                                  seed=d["seed"], state=d["state"], prec=prec,
-                                 rng_stream=d["rng_stream"]) for d in insts]
+                                 rng_stream=d["rng_stream"], walker_id0=d["walker_id0"])
+                for d in insts]
 
     ctx = gfk.Context(descs(gfk.GFK_PREC_MIXED), trials=trials)
     if args.threads and args.wpt:
@@ -283,6 +286,12 @@ def run_ours(args):
             gfk.gfk_energy(ctx.handle, i, cap=cap, out=(e_host[i], lz_host[i], ess_host[i]))
     e2e_s = (time.perf_counter() - t0) / n_e2e
     e_mixed = e_host[0].copy()
+    merged_e_final = None
+    if ws > 1:
+        # the one exchange step: merge the ranks' per-step sums of instance 0
+        from paper_1703_08977_gb300 import distributed as gd
+        merged = gd.merge_sums(ctx.sums(0))
+        merged_e_final = float(gd.estimators(merged, insts[0]["n_walkers"] * ws)["E"][-1])
     ctx.close()
 
     out = None
@@ -353,6 +362,8 @@ def run_ours(args):
                 "mean_E_t_second_half": float(np.mean(tail)), "final": float(diff[-1]),
                 "note": "mixed minus FP64 path, same seeds and walkers; the FP64 path "
                         "matches the FP64 oracle to 1e-13 (tests)"}
+        if merged_e_final is not None:
+            out["merged_E_final_all_ranks"] = merged_e_final
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)

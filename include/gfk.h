@@ -83,8 +83,9 @@ typedef enum { GFK_TRIAL_JASTROW_PRODUCT = 0, GFK_TRIAL_ORBITAL_PAIRS = 1 } gfk_
  * function), the time step dt, the number of replications N_rep and a seed.
  * Random numbers are Philox4x32-10 with counter (walker id, m, rng_stream,
  * tag) and key (seed low, seed high): moves 2m and 2m+1 take words 0-5 and
- * 6-11 of the blocks with tags 0, 1, 2.  The same (seed, rng_stream, walker
- * id) gives the same trajectory in any context and any launch configuration. */
+ * 6-11 of the blocks with tags 0, 1, 2; the walker id is walker_id0 + the
+ * walker's index.  The same (seed, rng_stream, walker id) gives the same
+ * trajectory in any context and any launch configuration. */
 typedef struct {
     int32_t  state;          /* gfk_state                                         */
     int32_t  prec;           /* gfk_prec; all instances of a context share it     */
@@ -95,6 +96,11 @@ typedef struct {
     uint32_t rng_stream;     /* third Philox counter word                         */
     int32_t  ee_on;          /* 1: V includes 1/r12; 0: drops it (test hook)      */
     double   init_sigma;     /* initial positions: each coordinate ~ N(0, sigma^2) */
+    uint32_t walker_id0;     /* Philox id of walker 0 (walker k uses id0 + k): shards
+                                of one population on several GPUs take disjoint
+                                id ranges and together reproduce it exactly;
+                                id0 + n_walkers must not exceed 2^32             */
+    int32_t  reserved;       /* 0                                                  */
 } gfk_instance_desc;
 
 /* Create a context holding n_inst instances (1 .. GFK_MAX_INSTANCES).

@@ -247,7 +247,7 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                     EvalOut<T> ev;
                     eval_kind0<T>(tp, x, ev);
                     uint32_t words[6];
-                    move_words((uint32_t)i, (uint32_t)m, inst->stream, inst->k0, inst->k1, words);
+                    move_words(inst->id0 + (uint32_t)i, (uint32_t)m, inst->stream, inst->k0, inst->k1, words);
                     T xi[6];
                     adj_normals(words, xi);
                     adj_move(x, ev.b, xi, dt, sdt);

@@ -265,6 +265,7 @@ gfk_status upload_instances(gfk_ctx* ctx) {
         v.k0 = (uint32_t)(d.seed & 0xffffffffull);
         v.k1 = (uint32_t)(d.seed >> 32);
         v.stream = d.rng_stream;
+        v.id0 = d.walker_id0;
         v.ee_on = d.ee_on ? 1 : 0;
         v.trial = ctx->trial[i];
     }
@@ -475,6 +476,7 @@ uint64_t desc_hash(const gfk_ctx* ctx) {
         h = fnv1a(&d.rng_stream, sizeof(d.rng_stream), h);
         h = fnv1a(&d.ee_on, sizeof(d.ee_on), h);
         h = fnv1a(&d.init_sigma, sizeof(d.init_sigma), h);
+        h = fnv1a(&d.walker_id0, sizeof(d.walker_id0), h);
         h = fnv1a(&ctx->trial[i], sizeof(TrialHost), h);
     }
     return h;
@@ -521,6 +523,8 @@ gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_
         if (!finite_d(d.e_trial)) return GFK_EINVAL;
         if (!(d.init_sigma > 0.0) || !finite_d(d.init_sigma)) return GFK_EINVAL;
         if (d.ee_on != 0 && d.ee_on != 1) return GFK_EINVAL;
+        if ((uint64_t)d.walker_id0 + (uint64_t)d.n_walkers > (1ull << 32)) return GFK_EINVAL;
+        if (d.reserved != 0) return GFK_EINVAL;
         total += (d.n_walkers + 31) / 32 * 32;
     }
     if (total > (1ll << 34)) return GFK_EINVAL;

@@ -44,7 +44,7 @@ init_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
         const int64_t slot = I.off + id;
         double xi[6], x[6];
         uint32_t words[6];
-        init_words((uint32_t)id, I.stream, I.k0, I.k1, words);
+        init_words(I.id0 + (uint32_t)id, I.stream, I.k0, I.k1, words);
         normals6_f64(words, xi);
 #pragma unroll
         for (int d = 0; d < 6; ++d) x[d] = I.sigma * xi[d];
@@ -136,7 +136,7 @@ walk_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
         if (sg != 0) {
             double xi[6];
             uint32_t words[6];
-            move_words((uint32_t)id, step, stream, k0, k1, words);
+            move_words(I.id0 + (uint32_t)id, step, stream, k0, k1, words);
             normals6_f64(words, xi);
 #pragma unroll
             for (int d = 0; d < 6; ++d) x[d] = x[d] + ev.b[d] * dt + sdt * xi[d];

@@ -75,7 +75,7 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         // then rounded: both paths start from the same population
         double xi[6];
         uint32_t words[6];
-        init_words((uint32_t)id, I.stream, I.k0, I.k1, words);
+        init_words(I.id0 + (uint32_t)id, I.stream, I.k0, I.k1, words);
         normals6_f64(words, xi);
         float x[6];
 #pragma unroll
@@ -163,7 +163,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     for (int k = 0; k < WPT; ++k) {
         const int64_t id = (int64_t)(blk - bm.begin[inst]) * T * WPT + (int64_t)k * T + threadIdx.x;
         valid[k] = id < I.n;
-        pre[k] = philox_pre((uint32_t)id, I.stream, k0, k1);
+        pre[k] = philox_pre(I.id0 + (uint32_t)id, I.stream, k0, k1);
         carry[k][0] = carry[k][1] = 0u;
         slot[k] = I.off + id;
         sg[k] = 0;

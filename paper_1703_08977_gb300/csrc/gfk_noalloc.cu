@@ -125,6 +125,8 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     if (!(d.dt > 0.0) || !std::isfinite(d.dt) || !std::isfinite(d.e_trial)) return GFK_EINVAL;
     if (!(d.init_sigma > 0.0) || !std::isfinite(d.init_sigma)) return GFK_EINVAL;
     if (d.ee_on != 0 && d.ee_on != 1) return GFK_EINVAL;
+    if ((uint64_t)d.walker_id0 + (uint64_t)d.n_walkers > (1ull << 32) || d.reserved != 0)
+        return GFK_EINVAL;
     if (n_steps < 0 || step0 < 0 || (init && step0 != 0)) return GFK_EINVAL;
     if (step0 + n_steps > 0xffffffffll) return GFK_EINVAL;
     if (((uintptr_t)dev_p0 | (uintptr_t)dev_p1) & 15u) return GFK_EINVAL;
@@ -150,6 +152,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     inst.k0 = (uint32_t)(d.seed & 0xffffffffull);
     inst.k1 = (uint32_t)(d.seed >> 32);
     inst.stream = d.rng_stream;
+    inst.id0 = d.walker_id0;
     inst.ee_on = d.ee_on ? 1 : 0;
     inst.trial = trial;
     InstDev* d_inst = (InstDev*)scratch;

@@ -29,6 +29,7 @@ struct InstDev {
     double dt, sqrt_dt, e_trial, sigma;
     uint32_t k0, k1;    // Philox key = seed
     uint32_t stream;    // third Philox counter word
+    uint32_t id0;       // Philox id of the instance's first walker
     int32_t ee_on;
     TrialHost trial;
 };

@@ -43,7 +43,8 @@ class gfk_instance_desc(ctypes.Structure):
                 ("n_walkers", ctypes.c_int64), ("dt", ctypes.c_double),
                 ("e_trial", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("rng_stream", ctypes.c_uint32), ("ee_on", ctypes.c_int32),
-                ("init_sigma", ctypes.c_double)]
+                ("init_sigma", ctypes.c_double), ("walker_id0", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32)]
 
 
 class GfkError(RuntimeError):
@@ -349,11 +350,13 @@ class InstanceDesc:
     rng_stream: int = 0
     ee_on: int = 1
     init_sigma: float = 0.5
+    walker_id0: int = 0
 
     def c(self) -> gfk_instance_desc:
         return gfk_instance_desc(int(self.state), int(self.prec), int(self.n_walkers),
                                  float(self.dt), float(self.e_trial), int(self.seed),
-                                 int(self.rng_stream), int(self.ee_on), float(self.init_sigma))
+                                 int(self.rng_stream), int(self.ee_on), float(self.init_sigma),
+                                 int(self.walker_id0), 0)
 
 
 class Context:

@@ -228,3 +228,38 @@ def test_edge_cases(gfk_lib):
     ctx.propagate(3)
     assert ctx.steps == 3
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_walker_id_shards_reproduce_one_population(gfk_lib, prec):
+    """Two contexts holding walker ids [0, 700) and [700, 1500) (walker_id0) give the
+    walkers of one 1500-walker context bitwise, and their per-step sums merged by the
+    multi-GPU rule (common shift, then sums) give its sums."""
+    gfk = gfk_lib
+    from paper_1703_08977_gb300 import distributed as gd
+    p = wl.triplet_2s3()
+    kw = dict(dt=0.01, e_trial=-2.17, seed=9, prec=prec, rng_stream=4)
+    full = gfk.Context([gfk.InstanceDesc(n_walkers=1500, **kw)], trials=[(1, p)]).propagate(64)
+    parts = [gfk.Context([gfk.InstanceDesc(n_walkers=k, walker_id0=i0, **kw)],
+                         trials=[(1, p)]).propagate(64) for i0, k in ((0, 700), (700, 800))]
+    fx, fl, fa = full.walkers()
+    xs = [c.walkers() for c in parts]
+    np.testing.assert_array_equal(np.vstack([xs[0][0], xs[1][0]]), fx)
+    np.testing.assert_array_equal(np.concatenate([xs[0][1], xs[1][1]]), fl)
+    rows = [c.sums() for c in parts]
+    C = np.maximum(np.where(rows[0][:, 5] > 0, rows[0][:, 0], -np.inf),
+                   np.where(rows[1][:, 5] > 0, rows[1][:, 0], -np.inf))
+    merged = np.zeros_like(rows[0])
+    merged[:, 0] = C
+    for r in rows:
+        f = np.where(r[:, 5] > 0, np.exp(r[:, 0] - C), 0.0)
+        merged[:, 1] += r[:, 1] * f
+        merged[:, 2] += r[:, 2] * f
+        merged[:, 3] += r[:, 3] * f * f
+        merged[:, 4] += r[:, 4] * f
+        merged[:, 5] += r[:, 5]
+    e_m = gd.estimators(merged, 1500)
+    np.testing.assert_allclose(e_m["E"], full.energy()["E"], rtol=1e-13 if prec == 0 else 2e-6)
+    np.testing.assert_array_equal(merged[:, 5], full.sums()[:, 5])
+    for c in parts + [full]:
+        c.close()
