@@ -167,28 +167,36 @@ __device__ __forceinline__ void philox10_pair(const PhiloxPre& p, uint32_t m, ui
     b.w[0] = bc0; b.w[1] = bc1; b.w[2] = bc2; b.w[3] = bc3;
 }
 
-// FP32: the same words, u = ((w >> 9) + 1/2) 2^-23.  k + 1/2 with k < 2^23 needs
-// 24 significant bits, so u is exact in FP32 and lies strictly inside (0, 1)
-// (with 24 bits, (2^24 - 1 + 1/2) 2^-24 would round to 1 and log u to 0).
-// It is built without an integer-to-float conversion: the bit pattern
-// 0x3F800000 | k is the float 1 + k 2^-23, and subtracting 1 - 2^-24 leaves
-// (k + 1/2) 2^-23 exactly (the difference is representable, so the
-// subtraction does not round).
-// Then the hardware log2 / reciprocal square root / sine / cosine.  The angle
-// is taken as 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine
-// are most accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
+// FP32: the same words.  The radius uniform keeps the full 32-bit resolution,
+// u_a = fl(fl(w) 2^-32 + 2^-33) (exact for w < 2^23, where the Gaussian tail
+// lives; elsewhere within an FP32 ulp of (w + 1/2) 2^-32).  A coarser grid
+// would bias the walk: with N equal bins at their midpoints, the mean of
+// -ln u falls short of 1 by (1 - ln 2)/N (the first bin, next to the log
+// singularity), so the normals' variance -- the diffusion constant -- would be
+// low by that fraction and E(t) high by about that fraction of the kinetic
+// energy.  u_a is at least 2^-33 > 0; values that round to 1 give radius 0
+// (the square root of 0 is 0).  The angle uniform uses 23 bits,
+// u_b - 1/2 = ((1 + k 2^-23) - 3/2) + 2^-24 with k = w >> 9, built exactly
+// from the bit pattern 0x3F800000 | k (= 1 + k 2^-23); an equally spaced grid
+// of angles keeps cos^2 and sin^2 at mean 1/2 exactly.  The radius takes the
+// library logarithm (about 1 ulp): the hardware log2's error does not average
+// to zero over u, and a mean relative error of 2e-8 in -ln u is a 2e-8 error
+// in the diffusion constant, measured as a 6e-8 hartree shift of E.  Then the
+// hardware square root, sine and cosine; the angle is taken as
+// 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine are most
+// accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
 __device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6]) {
-    constexpr float kOneMinusHalfUlp = 1.0f - 1.0f / 16777216.0f;          // 1 - 2^-24
-    constexpr float kHalfUlp = 1.0f / 16777216.0f;                          // 2^-24
-    constexpr float kMinus2Ln2 = -1.3862943611198906f;   // -2 ln 2
+    constexpr float kInv32 = 1.0f / 4294967296.0f;                        // 2^-32
+    constexpr float kHalfInv32 = 0.5f / 4294967296.0f;                    // 2^-33
+    constexpr float kHalfUlp = 1.0f / 16777216.0f;                        // 2^-24
     constexpr float kTwoPi = 6.2831853071795865f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        float ua = __int_as_float(0x3F800000 | (w[2 * j] >> 9)) - kOneMinusHalfUlp;
-        // u_b - 1/2 = ((1 + k 2^-23) - 3/2) + 2^-24: both steps exact
-        float ubc = (__int_as_float(0x3F800000 | (w[2 * j + 1] >> 9)) - 1.5f) + kHalfUlp;
-        float r2 = kMinus2Ln2 * __log2f(ua);                               // -2 ln u > 0
-        float rho = r2 * rsqrtf(r2);
+        const float ua = fmaf((float)w[2 * j], kInv32, kHalfInv32);
+        const float ubc = (__int_as_float(0x3F800000 | (w[2 * j + 1] >> 9)) - 1.5f) + kHalfUlp;
+        const float r2 = fmaxf(-2.0f * logf(ua), 0.0f);                    // -2 ln u >= 0
+        float rho;
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(rho) : "f"(r2));
         float s, c;
         __sincosf(kTwoPi * ubc, &s, &c);
         xi[2 * j] = -rho * c;

@@ -4,7 +4,7 @@
 
 #include <cstdint>
 
-#include "../../include/gfk.h"
+#include "gfk.h"   // include/ is on the include path
 
 namespace gfk {
 
