@@ -37,6 +37,9 @@ WORKLOADS = {
     "triplet": ("He 2^3S: 2^20 walkers x 20000 moves, dt=0.0025, trial "
                 "(e^{-2r1-0.5r2}-e^{-0.5r1-2r2})exp(r12/(4(1+0.3r12))), node r1=r2 by kill, "
                 "E_T=-2.1752, mixed"),
+    "adjoint": ("gradient of the final space-averaged 1^1S energy w.r.t. [Z, a, beta, c1..c4]: "
+                "2^18 walkers x 2000 moves, dt=0.005, checkpoints every 64 moves, FP32 forward "
+                "with FP64 weights (gfk_grad: forward + recompute + reverse sweep)"),
     "batched": ("12 instances {1^1S, 2^3S, P_z} x dt {0.01,0.005,0.0025,0.00125}, walker counts "
                 "round(2^U), U~U[16,21] (numpy default_rng(1)), sum 7.75e6 walkers x 10000 moves, "
                 "one launch per chunk, mixed"),
@@ -189,6 +192,55 @@ def _workload(name, rank):
         # (weak scaling: the population grows with the number of ranks)
         d["walker_id0"] = rank * d["n_walkers"]
     return insts, moves
+
+
+def run_adjoint(args):
+    """Workload 5: walker-steps/s of gfk_grad (each walker-step counted once although it
+    is walked forward, recomputed and swept backwards), mixed and FP64, and optionally
+    the 50-step Adam variance minimisation."""
+    import numpy as np
+    import torch
+    ws, rank, local = _dist_env()
+    if rank != 0:
+        return
+    from paper_1703_08977_gb300 import gfk, tuning
+    n, S, K, dt = 1 << 18, 2000, 64, 0.005
+    theta = [2.0, 0.5, 0.5, 0.0, 0.0, 0.0, 0.0]
+    res = {}
+    for prec, name in ((gfk.GFK_PREC_MIXED, "mixed"), (gfk.GFK_PREC_FP64, "fp64")):
+        d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=-2.9037, seed=SEED, prec=prec)
+        with gfk.Context([d], trials=[(0, theta)]) as ctx:
+            reps = args.steps if prec == gfk.GFK_PREC_MIXED else 1
+            for _ in range(1 if prec == gfk.GFK_PREC_FP64 else args.warmup):
+                gfk.gfk_grad(ctx.handle, 0, 0, S, K)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                loss, g = gfk.gfk_grad(ctx.handle, 0, 0, S, K)
+            el = (time.perf_counter() - t0) / reps
+            res[name] = {"value": n * S / el, "seconds": el, "loss": loss, "grad": g.tolist()}
+    gerr = np.abs(np.array(res["mixed"]["grad"]) - np.array(res["fp64"]["grad"])).max() / \
+        np.abs(np.array(res["fp64"]["grad"])).max()
+    out = {"metric": "gradient walker-steps/sec on 1 GB300 (adjoint through the walk)",
+           "value": res["mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * res["mixed"]["seconds"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "data": "synthetic", "config": {"workload": WORKLOADS["adjoint"], "name": "adjoint"},
+           "fp64_path": {"value": res["fp64"]["value"], "unit": UNIT,
+                         "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"]},
+           "gradient_mixed_vs_fp64_rel": float(gerr),
+           "gpu_launches": 5 + 2 * ((S + K - 1) // K) + 1}
+    if args.adam:
+        d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=-2.9037, seed=SEED,
+                             prec=gfk.GFK_PREC_MIXED)
+        with gfk.Context([d], trials=[(0, theta)]) as ctx:
+            t0 = time.perf_counter()
+            hist, th = tuning.tune(ctx.handle, 0, theta, steps=50, lr=1e-2, loss_kind=1,
+                                   n_steps=S, ckpt_every=K)
+            out["adam"] = {"steps": 50, "lr": 1e-2, "loss": "weighted variance of E_L",
+                           "variance_first": hist[0][0], "variance_last": hist[-1][0],
+                           "theta_final": th.tolist(), "seconds": time.perf_counter() - t0}
+    print(json.dumps(out), flush=True)
 
 
 def run_ours(args):
@@ -405,6 +457,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small ncu capture case instead of the benchmark")
     ap.add_argument("--prec", type=int, default=1, help="profile case: 1 mixed, 0 FP64")
+    ap.add_argument("--adam", action="store_true", help="adjoint workload: run 50 Adam steps")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args)
@@ -413,6 +466,8 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -461,14 +461,19 @@ int orc_run(int kind, const double* params, int n_params, int ee_on,
             double dx = xw[0] - xw[3], dy = xw[1] - xw[4], dz = xw[2] - xw[5];
             double r12 = sqrt(dx * dx + dy * dy + dz * dz);
             if (r1 < 1e-10 || r2 < 1e-10 || r12 < 1e-10) ++cnt[2];
-            if (s1 != sgn[i]) {                        /* node crossed (or psi = 0) */
+            /* the order of the tests: a position that is not finite is a
+             * non-finite kill; then a sign change (or psi = 0) is a node kill;
+             * then a drift or local energy that is not finite */
+            int xfinite = 1;
+            for (int d = 0; d < 6; ++d) xfinite = xfinite && isfinite(xw[d]);
+            if (xfinite && s1 != sgn[i]) {             /* node crossed (or psi = 0) */
                 alive[i] = 0;
                 logw[i] = -INFINITY;
                 ++cnt[1];
                 continue;
             }
-            int finite = isfinite(e1);
-            for (int d = 0; d < 6; ++d) finite = finite && isfinite(b1[d]) && isfinite(xw[d]);
+            int finite = xfinite && isfinite(e1);
+            for (int d = 0; d < 6; ++d) finite = finite && isfinite(b1[d]);
             if (!finite) {
                 alive[i] = 0;
                 logw[i] = -INFINITY;

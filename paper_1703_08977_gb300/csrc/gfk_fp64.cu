@@ -142,7 +142,11 @@ walk_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
             for (int d = 0; d < 6; ++d) x[d] = x[d] + ev.b[d] * dt + sdt * xi[d];
             eval_trial<KIND, double>(t, x, ev);
             if (ev.rmin < 1e-10) ++n_coal;
-            if (ev.sign != sg) {
+            // a non-finite position is a non-finite kill, then a sign change a
+            // node kill, then a non-finite drift or local energy
+            bool node = ev.sign != sg;
+            if (node) node = finite_(((x[0] + x[1]) + (x[2] + x[3])) + (x[4] + x[5]));
+            if (node) {
                 sg = 0;
                 logw = -INFINITY;
                 ++n_node;

@@ -231,7 +231,12 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             for (int d = 0; d < 6; ++d) xn[d] = fmaf(sdt, xi[d], fmaf(b[k][d], dt, x[k][d]));
             EvalOut<float> ev;
             eval_trial<KIND, float>(t, xn, ev);
-            const bool node = ev.sign != sg[k];
+            // a non-finite position is a non-finite kill, then a sign change a
+            // node kill, then a non-finite drift or local energy (a position that
+            // is not finite makes E_L not finite, so the position itself is only
+            // examined in the rare case that the sign test fires)
+            bool node = ev.sign != sg[k];
+            if (node) node = finite_(((xn[0] + xn[1]) + (xn[2] + xn[3])) + (xn[4] + xn[5]));
             const bool fin = eval_finite(ev);
             const bool stay = alive && !node && fin;
             n_coal += (alive && ev.rmin < 1e-5f) ? 1u : 0u;
