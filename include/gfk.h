@@ -53,7 +53,7 @@ typedef enum { GFK_1S = 0, GFK_2S3 = 1, GFK_PZ = 2 } gfk_state;
  * GFK_PREC_MIXED: positions, drift, local energy and random normals in FP32;
  *                 each walker's log-weight is an FP64 base plus an FP32
  *                 Kahan-compensated sum of increments folded into the base
- *                 every 32 steps; population sums go FP32 within a warp,
+ *                 every 64 steps; population sums go FP32 within a warp,
  *                 FP64 above it, compensated (TwoSum) across blocks. */
 typedef enum { GFK_PREC_FP64 = 0, GFK_PREC_MIXED = 1 } gfk_prec;
 
@@ -156,7 +156,7 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
  * (the right-point Riemann sum of the Feynman-Kac exponent, Eq. 4), then the
  * fixed-node test, then the population sums of that step.
  * GFK_ESTATE if an instance has no trial function.  Step counts are
- * cumulative; a run interrupted and resumed at a multiple of 32 steps is
+ * cumulative; a run interrupted and resumed at a multiple of 64 steps is
  * bitwise identical to an uninterrupted one. */
 gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps);
 
@@ -199,7 +199,7 @@ gfk_status gfk_counters(gfk_ctx* ctx, int32_t inst, int64_t* host_counts3);
  * sums, counters) as an opaque host blob of gfk_checkpoint_size bytes.
  * gfk_restore loads a blob written by a context created with the same
  * descriptors and trial functions; resuming from it is bitwise identical to
- * never having stopped (when the step count is a multiple of 32).
+ * never having stopped (when the step count is a multiple of 64).
  * GFK_EINVAL if the blob does not match the context. */
 gfk_status gfk_checkpoint_size(gfk_ctx* ctx, int64_t* bytes);
 gfk_status gfk_checkpoint(gfk_ctx* ctx, void* host_blob, int64_t bytes);
@@ -259,7 +259,7 @@ gfk_status gfk_profile_read(gfk_ctx* ctx, double* walk_ms, int64_t* launches,
  * address (make this first call before any stream capture).  All calls share
  * the array, so calls that overlap on the GPU race; each call rewrites what it
  * reads.  Returns GFK_EINVAL for n_walkers above GFK_NOALLOC_MAX_WALKERS (the
- * most whose per-move records fit the array, 32 moves at a time) or any other
+ * most whose per-move records fit the array, 16 moves at a time) or any other
  * bad argument, GFK_ECUDA if a launch or copy fails. */
 #define GFK_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define GFK_NOALLOC_MAX_WALKERS (1ll << 22)

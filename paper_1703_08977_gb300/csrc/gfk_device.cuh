@@ -235,6 +235,7 @@ __device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
 template <typename R>
 struct TrialDev {
     int kind, nterms;
+    int poly;                      // any c_k != 0 (else the Jastrow polynomial is skipped)
     R Z, Zm2, Z2;                  // kind 0: Z, Z - 2, Z^2
     R a, beta, ee, eem2a, eebeta;  // Jastrow: a, beta, ee (0/1), ee - 2a, ee*beta
     R c2, c3, c4, c5;              // 2c1, 3c2, 4c3, 5c4 (du/drho coefficients)
@@ -249,6 +250,7 @@ template <typename R>
 __device__ __forceinline__ void load_trial(const TrialHost& h, int ee_on, TrialDev<R>& t) {
     t.kind = h.kind;
     t.nterms = h.nterms;
+    t.poly = (h.ck[0] != 0.0 || h.ck[1] != 0.0 || h.ck[2] != 0.0 || h.ck[3] != 0.0) ? 1 : 0;
     t.Z = (R)h.Z;
     t.Zm2 = (R)(h.Z - 2.0);
     t.Z2 = (R)(h.Z * h.Z);
@@ -294,6 +296,14 @@ struct EvalOut {
 template <typename R>
 struct JastrowOut { R up, upp, jee; };
 
+// Whether the Jastrow polynomial terms are present (a block-uniform branch);
+// the dual-number parameter set always carries them (their derivatives are
+// wanted even where the coefficients are zero).
+template <typename R>
+__device__ __forceinline__ bool has_poly(const TrialDev<R>& t) { return t.poly != 0; }
+template <typename TD>
+__device__ __forceinline__ bool has_poly(const TD&) { return true; }
+
 template <typename R, typename TD>
 __device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
     R q = R(1) + t.beta * r12;
@@ -301,13 +311,20 @@ __device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
     R rho = r12 * iq;
     R drho = iq * iq;                          // d rho / dr
     R d2rho = R(-2) * t.beta * drho * iq;      // d2 rho / dr2
-    R h = t.c2 + rho * (t.c3 + rho * (t.c4 + rho * t.c5));   // (du/drho - a) / rho
-    R du = t.a + rho * h;                                   // du / drho
-    R d2u = t.d2 + rho * (t.d6 + rho * (t.d12 + rho * t.d20));
     JastrowOut<R> o;
-    o.up = du * drho;
-    o.upp = d2u * drho * drho + du * d2rho;
-    o.jee = (t.eem2a * i12 + t.eebeta * (R(2) + t.beta * r12)) * drho - R(2) * h * drho * iq;
+    const R jee0 = (t.eem2a * i12 + t.eebeta * (R(2) + t.beta * r12)) * drho;
+    if (has_poly(t)) {
+        R h = t.c2 + rho * (t.c3 + rho * (t.c4 + rho * t.c5));   // (du/drho - a) / rho
+        R du = t.a + rho * h;                                   // du / drho
+        R d2u = t.d2 + rho * (t.d6 + rho * (t.d12 + rho * t.d20));
+        o.up = du * drho;
+        o.upp = d2u * drho * drho + du * d2rho;
+        o.jee = jee0 - R(2) * h * drho * iq;
+    } else {                                   // u = a rho: du/drho = a, d2u/drho2 = 0
+        o.up = t.a * drho;
+        o.upp = t.a * d2rho;
+        o.jee = jee0;
+    }
     return o;
 }
 

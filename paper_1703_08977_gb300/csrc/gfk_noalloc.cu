@@ -168,8 +168,8 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     bm.begin[1] = nblk;
     const int64_t rec_cap = (int64_t)((GFK_NOALLOC_SCRATCH_BYTES - kHeaderBytes) / sizeof(PartialRec));
     int64_t rows_fit = rec_cap / nblk;
-    rows_fit = rows_fit > 1024 ? 1024 : (rows_fit / kRing) * kRing;
-    if (rows_fit < kRing) return GFK_EINVAL;   // cannot happen below GFK_NOALLOC_MAX_WALKERS
+    rows_fit = rows_fit > 1024 ? 1024 : (rows_fit / 16) * 16;
+    if (rows_fit < 16) return GFK_EINVAL;      // cannot happen below GFK_NOALLOC_MAX_WALKERS
 
     StateMixed sm;
     sm.p0 = (float4*)dev_p0;

@@ -68,7 +68,7 @@ struct StateMixed {
 
 // Steps between flushes of the per-step block sums; also the mixed path's
 // fold period of the FP32 log-weight increments into the FP64 base.
-constexpr int kRing = 32;
+constexpr int kRing = 64;
 constexpr int kMaxThreads = 512;
 constexpr int kMaxWarps = kMaxThreads / 32;
 

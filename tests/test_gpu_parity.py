@@ -126,18 +126,18 @@ def test_fp64_launch_shape_does_not_change_walkers(gfk_lib, threads):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_resume_is_bitwise(gfk_lib, prec):
-    """Counter-based randomness: chunked propagation (multiples of 32 steps), and a
+    """Counter-based randomness: chunked propagation (multiples of 64 steps), and a
     checkpoint restored into a fresh context, reproduce the uninterrupted run bit for bit."""
     gfk = gfk_lib
     p = wl.triplet_2s3()
     d = gfk.InstanceDesc(n_walkers=3000, dt=0.01, e_trial=-2.17, seed=5, prec=prec)
-    one = gfk.Context([d], trials=[(1, p)]).propagate(160)
-    two = gfk.Context([d], trials=[(1, p)]).propagate(32).propagate(64)
+    one = gfk.Context([d], trials=[(1, p)]).propagate(320)
+    two = gfk.Context([d], trials=[(1, p)]).propagate(64).propagate(128)
     blob = two.checkpoint()
     three = gfk.Context([d], trials=[(1, p)])
     three.restore(blob)
-    three.propagate(64)
-    two.propagate(64)
+    three.propagate(128)
+    two.propagate(128)
     for c in (two, three):
         for u, v in zip(one.walkers(), c.walkers()):
             np.testing.assert_array_equal(u, v)
