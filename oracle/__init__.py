@@ -21,6 +21,13 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                     <E_L> = Z^2 - 27 Z / 8 at stationarity, node invariants,
                     the growth identity d ln z / dt = -(E - E_T) + O(dt).
   neumaier_sum      pinned: math.fsum (exactly rounded) on cancelling inputs.
+  superduper_next,
+  bernoulli_eps,
+  move_bernoulli    pinned: the closed form S_k = a^k S_0 + (a^k - 1)/(a - 1) mod 2^32
+                    of the congruential recurrence (exact integers), the paper's
+                    threshold at 2^31, balance and independence of the +-1 steps.
+  run (noise 1)     pinned: a hand-computed Bernoulli step, exact weights for an
+                    exact eigenfunction, and the stationary <E_L> closed form.
 """
 from __future__ import annotations
 
@@ -83,8 +90,16 @@ def _load():
                                 c.c_int64, c.POINTER(c.c_uint32),
                                 dp, dp, dp, c.POINTER(c.c_uint8), c.POINTER(c.c_int8),
                                 c.c_uint32, c.c_int64, c.c_int,
-                                dp, c.POINTER(c.c_int64)]
+                                dp, c.POINTER(c.c_int64), c.c_int, c.POINTER(c.c_uint32)]
         lib.orc_run.restype = c.c_int
+        lib.orc_superduper_next.argtypes = [c.c_uint32]
+        lib.orc_superduper_next.restype = c.c_uint32
+        lib.orc_bernoulli_eps.argtypes = [c.c_uint32]
+        lib.orc_bernoulli_eps.restype = c.c_int
+        lib.orc_superduper_seed.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32]
+        lib.orc_superduper_seed.restype = c.c_uint32
+        lib.orc_move_bernoulli.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, dp]
+        lib.orc_move_bernoulli.restype = None
         _lib = lib
         return lib
 
@@ -123,6 +138,33 @@ def init_normals(seed: int, walker: int, inst: int) -> np.ndarray:
     return out
 
 
+NOISE_GAUSSIAN = 0
+NOISE_BERNOULLI = 1
+
+
+def superduper_next(state: int) -> int:
+    """One step of the "Superduper" generator: (69069 S + 1) mod 2^32."""
+    return int(_load().orc_superduper_next(int(state)))
+
+
+def bernoulli_eps(state: int) -> int:
+    """The +-1 increment a generator output gives (+1 iff S > 2^31)."""
+    return int(_load().orc_bernoulli_eps(int(state)))
+
+
+def superduper_seed(seed: int, walker: int, inst: int) -> int:
+    """Initial generator state S_0 of walker `walker` (instance stream `inst`)."""
+    return int(_load().orc_superduper_seed(int(seed), int(walker), int(inst)))
+
+
+def move_bernoulli(seed: int, walker: int, step: int, inst: int) -> np.ndarray:
+    """The six +-1 increments of move `step` of walker `walker` (serial replay)."""
+    out = np.zeros(6)
+    _load().orc_move_bernoulli(int(seed), int(walker), int(step), int(inst),
+                               _ptr(out, ctypes.c_double))
+    return out
+
+
 def trial_eval(kind: int, params, x, ee_on: bool = True):
     """(sign, drift b (6,), E_L, ln|psi|) of the trial function at X (6,)."""
     lib = _load()
@@ -155,7 +197,7 @@ class Walk:
     """
 
     def __init__(self, kind, params, *, n_walkers=None, ids=None, dt, e_trial, seed,
-                 inst=0, sigma=0.5, ee_on=True):
+                 inst=0, sigma=0.5, ee_on=True, noise=NOISE_GAUSSIAN):
         if ids is None:
             ids = np.arange(int(n_walkers), dtype=np.uint32)
         self.ids = np.ascontiguousarray(ids, dtype=np.uint32)
@@ -164,6 +206,8 @@ class Walk:
         self.params = np.ascontiguousarray(params, dtype=np.float64)
         self.dt, self.e_trial, self.seed = float(dt), float(e_trial), int(seed)
         self.inst, self.sigma, self.ee_on = int(inst), float(sigma), bool(ee_on)
+        self.noise = int(noise)
+        self.lcg = np.zeros(n, dtype=np.uint32)     # Superduper states (noise 1)
         self.x = np.zeros((n, 6))
         self.logw = np.zeros(n)
         self.el = np.zeros(n)
@@ -185,7 +229,8 @@ class Walk:
                          _ptr(self.x, ctypes.c_double), _ptr(self.logw, ctypes.c_double),
                          _ptr(self.el, ctypes.c_double), _ptr(self.alive, ctypes.c_uint8),
                          _ptr(self.sgn, ctypes.c_int8), self.step, int(n_steps), int(do_init),
-                         _ptr(stats, ctypes.c_double), _ptr(self.counters, ctypes.c_int64))
+                         _ptr(stats, ctypes.c_double), _ptr(self.counters, ctypes.c_int64),
+                         self.noise, _ptr(self.lcg, ctypes.c_uint32))
         if rc != 0:
             raise ValueError("oracle: bad walk parameters")
         self.rows.extend(stats[:nrows])

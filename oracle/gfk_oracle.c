@@ -29,9 +29,11 @@
  *    introduction and before the trial-function list): a walker whose trial
  *    function changes sign (or becomes exactly zero) is killed.
  *
- * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
- * random numbers: as easy as 1, 2, 3", SC'11) replaces the paper's Bernoulli
- * steps drawn from the "Superduper" congruential generator.  The counter is
+ * Random numbers: two noise modes.  Mode 0 (Gaussian increments): Philox4x32-10
+ * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+ * SC'11) with Box-Muller normals.  Mode 1 (the paper's own scheme): Bernoulli
+ * +-1 increments from the "Superduper" congruential generator, one generator
+ * per walker (section "Bernoulli steps" below).  For mode 0 the counter is
  * (walker id, pair index, instance id, tag), the key the two halves of the
  * 64-bit seed.  Moves 2m and 2m+1 share the three blocks of pair index m,
  * tags 0, 1, 2 (12 words): move 2m takes words 0-5, move 2m+1 words 6-11.
@@ -132,6 +134,67 @@ void orc_init_normals(uint64_t seed, uint32_t walker, uint32_t inst, double xi[6
     uint32_t words[12];
     orc_pair_words(seed, walker, 0u, inst, 3u, words);
     orc_normals_from_words(words, xi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bernoulli steps from the "Superduper" congruential generator             */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper's own discretisation of the Brownian motion (the construction of
+ * W(l) before the invariance principle, and the generator paragraph after the
+ * space-averaging remarks): every coordinate moves by eps / sqrt(n) per time
+ * step 1/n, with eps = +1 or -1 independently and with equal probability.  With
+ * the time step written dt = 1/n the increment is sqrt(dt) eps, so this mode
+ * replaces the Gaussian xi of the Euler-Maruyama move by eps and nothing else.
+ *
+ * eps comes from the congruential generator the paper calls "Superduper",
+ * S_i = (69069 S_{i-1} + 1) mod 2^32, with eps_i = +1 if S_i > 2^31 and
+ * eps_i = -1 otherwise (so S_i = 2^31 gives -1).
+ *
+ * The paper names one initial seed S_0 but not how the draws are shared among
+ * paths.  Here every walker runs its own generator: its S_0 is word 0 of the
+ * Philox block (walker, 0, inst, 5), and move `step` uses the outputs
+ * S_{6 step + 1} .. S_{6 step + 6} for the coordinates x1, y1, z1, x2, y2, z2 in
+ * that order.  The oracle steps each generator serially, one output at a time.
+ */
+#define ORC_SUPERDUPER_MULT 69069u
+
+uint32_t orc_superduper_next(uint32_t s)
+{
+    /* unsigned 32-bit arithmetic wraps modulo 2^32 */
+    return (uint32_t)(ORC_SUPERDUPER_MULT * s + 1u);
+}
+
+int orc_bernoulli_eps(uint32_t s)
+{
+    return s > 2147483648u ? 1 : -1;
+}
+
+uint32_t orc_superduper_seed(uint64_t seed, uint32_t walker, uint32_t inst)
+{
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { walker, 0u, inst, 5u };
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+/* The six increments of one move: advances *state by six outputs. */
+static void orc_bernoulli_step(uint32_t* state, double eps[6])
+{
+    for (int d = 0; d < 6; ++d) {
+        *state = orc_superduper_next(*state);
+        eps[d] = (double)orc_bernoulli_eps(*state);
+    }
+}
+
+/* The six increments of move `step` of a walker, by stepping its generator
+ * from S_0 through all earlier moves (cost proportional to step). */
+void orc_move_bernoulli(uint64_t seed, uint32_t walker, uint32_t step, uint32_t inst,
+                        double eps[6])
+{
+    uint32_t s = orc_superduper_seed(seed, walker, inst);
+    for (uint32_t k = 0; k <= step; ++k) orc_bernoulli_step(&s, eps);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -395,6 +458,10 @@ static void orc_population_sums(int64_t n, const double* logw, const double* el,
  *    one stats row for the initial population (all weights 1).
  *  - then n_steps moves with global step counters step0 .. step0+n_steps-1,
  *    each followed by one stats row.
+ * noise: 0 = Gaussian increments (Philox normals), 1 = Bernoulli increments
+ *   from each walker's Superduper generator, whose state lcg[i] is set at
+ *   initialisation and advanced by six outputs per move of an alive walker
+ *   (lcg may be NULL for noise 0).
  * stats: (n_steps + (do_init ? 1 : 0)) rows of 6 doubles (see above), or NULL.
  * counters (may be NULL): [0] non-finite kills, [1] node kills,
  *   [2] coalescence events (r1, r2 or r12 below 1e-10 after a move).
@@ -405,11 +472,12 @@ int orc_run(int kind, const double* params, int n_params, int ee_on,
             int64_t n, const uint32_t* ids,
             double* x, double* logw, double* el, uint8_t* alive, int8_t* sgn,
             uint32_t step0, int64_t n_steps, int do_init,
-            double* stats, int64_t* counters)
+            double* stats, int64_t* counters, int noise, uint32_t* lcg)
 {
     orc_trial t;
     if (orc_trial_parse(kind, params, n_params, &t) != 0) return -1;
     if (n < 0 || n_steps < 0 || !(dt > 0.0)) return -1;
+    if (noise != 0 && (noise != 1 || !lcg)) return -1;
     int64_t cnt[3] = { 0, 0, 0 };
     double sqrt_dt = sqrt(dt);
     int64_t row = 0;
@@ -419,6 +487,7 @@ int orc_run(int kind, const double* params, int n_params, int ee_on,
             uint32_t id = ids ? ids[i] : (uint32_t)i;
             double xi[6];
             orc_init_normals(seed, id, inst, xi);
+            if (noise == 1) lcg[i] = orc_superduper_seed(seed, id, inst);
             double* xw = x + 6 * i;
             for (int d = 0; d < 6; ++d) xw[d] = sigma * xi[d];
             int s;
@@ -448,9 +517,13 @@ int orc_run(int kind, const double* params, int n_params, int ee_on,
             int s0;
             double b[6], e0, lp;
             orc_eval(&t, ee_on, xw, &s0, b, &e0, &lp);
-            /* Euler-Maruyama move X <- X + b dt + sqrt(dt) xi */
+            /* Euler-Maruyama move X <- X + b dt + sqrt(dt) xi; in the Bernoulli
+             * mode xi is the walker's next six +-1 increments */
             double xi[6];
-            orc_move_normals(seed, id, step, inst, xi);
+            if (noise == 1)
+                orc_bernoulli_step(&lcg[i], xi);
+            else
+                orc_move_normals(seed, id, step, inst, xi);
             for (int d = 0; d < 6; ++d) xw[d] = xw[d] + b[d] * dt + sqrt_dt * xi[d];
             /* trial function at the new position */
             int s1;

@@ -408,11 +408,11 @@ def test_resume_is_bitwise():
     np.testing.assert_array_equal(np.array(one.rows), np.array(two.rows))
 
 
-def _stationary_mean_el(kind, p, n, steps, burn, dt, seed, ee_on=True, sigma=0.5):
+def _stationary_mean_el(kind, p, n, steps, burn, dt, seed, ee_on=True, sigma=0.5, noise=0):
     """Unweighted time-and-space average of E_L after burn-in, and its standard error
     from the spread of per-walker time averages (walkers are independent)."""
     w = oracle.Walk(kind, p, n_walkers=n, dt=dt, e_trial=0.0, seed=seed, ee_on=ee_on,
-                    sigma=sigma)
+                    sigma=sigma, noise=noise)
     w.advance(burn)
     acc = np.zeros(n)
     cnt = np.zeros(n)
@@ -511,3 +511,141 @@ def test_grad_oracle_gradient_matches_finite_differences():
             fd = (float(og.walk_loss(torch.tensor(tp), loss_kind=loss_kind, **kw)) -
                   float(og.walk_loss(torch.tensor(tm), loss_kind=loss_kind, **kw))) / (2 * h)
             assert abs(fd - g[k]) <= 1e-6 * max(1.0, np.abs(g).max()), (loss_kind, k, fd, g[k])
+
+
+# --------------------------------------------------------------------------
+# Bernoulli steps from the "Superduper" congruential generator
+# --------------------------------------------------------------------------
+
+_SD_A, _SD_M = 69069, 1 << 32
+
+
+def _sd_closed_form(s0, k):
+    """S_k of S_i = (a S_{i-1} + 1) mod 2^32 in closed form: a^k S_0 + (a^k - 1)/(a - 1),
+    the geometric series summed exactly in Python integers before the reduction."""
+    ak = _SD_A ** k
+    return (ak * s0 + (ak - 1) // (_SD_A - 1)) % _SD_M
+
+
+def _affine_pow_mod(k):
+    """(A, C) with S_k = A S_0 + C mod 2^32, by binary powering of the affine map
+    S -> a S + 1 (an independent route to the same numbers, usable at k = 2^32)."""
+    A, C = 1, 0                   # identity
+    a, c = _SD_A, 1               # the map applied 2^j times
+    while k:
+        if k & 1:
+            A, C = (a * A) % _SD_M, (a * C + c) % _SD_M
+        a, c = (a * a) % _SD_M, (a * c + c) % _SD_M
+        k >>= 1
+    return A, C
+
+
+def test_superduper_recurrence_matches_closed_form():
+    """Outputs of the oracle's generator equal the closed form of the congruential
+    recurrence (a dropped increment, a wrong multiplier or a lost wrap-around fails)."""
+    rng = np.random.default_rng(12)
+    for s0 in [0, 1, 2 ** 31, 2 ** 32 - 1, *rng.integers(0, 2 ** 32, 4).tolist()]:
+        s = int(s0)
+        for k in range(1, 2001):
+            s = oracle.superduper_next(s)
+            if k in (1, 2, 3, 17, 640, 2000):
+                assert s == _sd_closed_form(int(s0), k), (s0, k)
+    assert oracle.superduper_next(1) == 69070
+
+
+def test_superduper_has_the_full_period():
+    """The generator's cycle is 2^32 (the paper chooses a cycle of 2^32): the affine map
+    composed 2^32 times is the identity and 2^31 times is not (Hull-Dobell: c odd,
+    a = 1 mod 4); and the binary powering agrees with the closed form at small k."""
+    for k in (1, 5, 100, 999):
+        A, C = _affine_pow_mod(k)
+        assert (A * 12345 + C) % _SD_M == _sd_closed_form(12345, k)
+    assert _affine_pow_mod(1 << 32) == (1, 0)
+    assert _affine_pow_mod(1 << 31) != (1, 0)
+    assert _SD_A % 4 == 1
+
+
+def test_bernoulli_threshold_is_the_papers():
+    """eps = +1 if S > 2^31, else -1 (so S = 2^31 itself gives -1)."""
+    cases = {0: -1, 1: -1, 2 ** 31 - 1: -1, 2 ** 31: -1, 2 ** 31 + 1: 1, 2 ** 32 - 1: 1}
+    for st, e in cases.items():
+        assert oracle.bernoulli_eps(st) == e, st
+
+
+def test_bernoulli_move_consumes_six_outputs_per_move():
+    """Move `step` of a walker uses outputs 6 step + 1 .. 6 step + 6 of its generator,
+    which starts at word 0 of the Philox block (walker, 0, stream, 5)."""
+    for seed, walker, step, inst in [(0, 0, 0, 0), (5, 17, 3, 2), (2 ** 40 + 7, 999, 250, 7)]:
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        s0 = int(oracle.philox4x32_10([walker, 0, inst, 5], key)[0])
+        assert oracle.superduper_seed(seed, walker, inst) == s0
+        want = [1.0 if _sd_closed_form(s0, 6 * step + d + 1) > 2 ** 31 else -1.0
+                for d in range(6)]
+        np.testing.assert_array_equal(oracle.move_bernoulli(seed, walker, step, inst), want)
+
+
+def test_bernoulli_increments_are_balanced_and_independent():
+    """+1 and -1 equally likely, no correlation between coordinates, between the
+    consecutive moves of a walker, or between neighbouring walkers (4 standard errors)."""
+    n = 3000
+    e = np.array([[oracle.move_bernoulli(3, i, st, 1) for st in (0, 1)] for i in range(n)])
+    tol = 4.0 / math.sqrt(n)
+    assert abs(e.mean()) < 4.0 / math.sqrt(e.size)
+    c = np.corrcoef(e[:, 0, :].T)
+    assert np.abs(c - np.eye(6)).max() < tol
+    for d in range(6):
+        assert abs(np.corrcoef(e[:, 0, d], e[:, 1, d])[0, 1]) < tol
+        assert abs(np.corrcoef(e[:-1, 0, d], e[1:, 0, d])[0, 1]) < tol
+
+
+def test_bernoulli_single_step_by_hand():
+    """X1 = X0 + b(X0) dt + sqrt(dt) eps, logw1 = -(E_L(X1) - E_T) dt, with b and E_L from
+    50-digit finite differences of ln psi and eps from the pinned generator."""
+    kind, p = TRIALS["ground_jastrow_poly"]
+    dt, et, seed, sigma, wid, inst = 1.0 / 900.0, -2.9, 41, 0.5, 9, 1
+    w = oracle.Walk(kind, p, ids=[wid], dt=dt, e_trial=et, seed=seed, inst=inst, sigma=sigma,
+                    noise=oracle.NOISE_BERNOULLI)
+    X = sigma * oracle.init_normals(seed, wid, inst)
+    np.testing.assert_array_equal(w.x[0], X)
+    logw = 0.0
+    for step in range(3):
+        b, _, _ = _mp_drift_el(kind, p, X)
+        X = X + b * dt + math.sqrt(dt) * oracle.move_bernoulli(seed, wid, step, inst)
+        _, el, _ = _mp_drift_el(kind, p, X)
+        logw -= (el - et) * dt
+        w.advance(1)
+        np.testing.assert_allclose(w.x[0], X, rtol=1e-12, atol=1e-12)
+        assert abs(w.logw[0] - logw) <= 1e-12
+        assert abs(w.el[0] - el) <= 1e-10 * abs(el)
+
+
+def test_bernoulli_exact_eigenfunction_gives_exact_weights():
+    p = wl.ground(Z=2.0, a=0.0)
+    dt = 1.0 / 900.0
+    w = oracle.Walk(0, p, n_walkers=64, dt=dt, e_trial=-3.5, seed=3, ee_on=False,
+                    noise=oracle.NOISE_BERNOULLI)
+    w.advance(200)
+    s = w.series()
+    np.testing.assert_allclose(s["E"], -4.0, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(s["ln_z"], (4.0 - 3.5) * np.arange(201) * dt, rtol=0, atol=1e-11)
+    assert w.alive.all()
+
+
+def test_bernoulli_walk_resume_is_bitwise():
+    kind, p = TRIALS["triplet_2s3"]
+    kw = dict(dt=0.0025, e_trial=-2.17, seed=8, inst=3, noise=oracle.NOISE_BERNOULLI)
+    one = oracle.Walk(kind, p, n_walkers=50, **kw).advance(40)
+    two = oracle.Walk(kind, p, n_walkers=50, **kw).advance(15).advance(25)
+    np.testing.assert_array_equal(one.x, two.x)
+    np.testing.assert_array_equal(one.lcg, two.lcg)
+    np.testing.assert_array_equal(np.array(one.rows), np.array(two.rows))
+
+
+def test_bernoulli_walk_samples_psi_squared():
+    """By the invariance principle the +-1 walk converges to the drifted diffusion, whose
+    stationary law is psi^2: for psi = exp(-2 (r1 + r2)) with e-e repulsion,
+    <E_L> = 4 - 27/4 = -2.75 (textbook closed form), within 5 standard errors plus an
+    O(dt) allowance."""
+    mean, se = _stationary_mean_el(0, wl.ground(Z=2.0, a=0.0), n=1000, steps=600, burn=200,
+                                   dt=0.002, seed=23, noise=oracle.NOISE_BERNOULLI)
+    assert abs(mean - (4.0 - 27.0 / 4.0)) < 5 * se + 0.01, (mean, se)
