@@ -40,20 +40,24 @@ WORKLOADS = {
     "adjoint": ("gradient of the final space-averaged 1^1S energy w.r.t. [Z, a, beta, c1..c4]: "
                 "2^18 walkers x 2000 moves, dt=0.005, checkpoints every 64 moves, FP32 forward "
                 "with FP64 weights (gfk_grad: forward + recompute + reverse sweep)"),
+    "bernoulli": ("He 1^1S with the paper's own +-1 walk: 2^20 walkers x 20000 moves, "
+                  "dt=1/900 (scale 30, step length 1/30), Superduper generators "
+                  "S=(69069 S+1) mod 2^32 per walker, same trial and E_T as ground, mixed"),
     "batched": ("12 instances {1^1S, 2^3S, P_z} x dt {0.01,0.005,0.0025,0.00125}, walker counts "
                 "round(2^U), U~U[16,21] (numpy default_rng(1)), sum 7.75e6 walkers x 10000 moves, "
                 "one launch per chunk, mixed"),
 }
 SEED = 0
 
-# Algorithmic ALU work of one walker-step of the mixed path for the kind-0 trial,
-# counted from the method's definition (one op per multiply, add, compare,
-# reciprocal, square root, log, exp, sine, cosine; a 32x32->64 multiply is one
-# op): Philox4x32-10 at 1.5 blocks per move (120),
-# Box-Muller x3 (42), move (12), trial evaluation, weight and sums (11).  The
-# trial evaluation is 105 ops for the ground-state product (kind 0) and 220 for
-# a two-term orbital-pair function (kind 1).
-OPS_PER_WALKER_STEP = {0: 290, 1: 405}
+# Algorithmic ALU work of one walker-step of the mixed path, counted from the
+# method's definition (one op per multiply, add, compare, reciprocal, square
+# root, log, exp, sine, cosine; a 32x32->64 multiply is one op): with Gaussian
+# noise, Philox4x32-10 at 1.5 blocks per move (120) and Box-Muller x3 (42); with
+# Bernoulli noise, six generator steps (multiply, add) and six threshold
+# compares (18); then the move (12), the trial evaluation (105 ops for the
+# ground-state product, kind 0; 220 for a two-term orbital-pair function,
+# kind 1), the weight and the sums (11).  Keyed by (noise, kind).
+OPS_PER_WALKER_STEP = {(0, 0): 290, (0, 1): 405, (1, 0): 146, (1, 1): 261}
 # Lanes that can issue an ALU instruction per SM per clock (4 schedulers x 32).
 LANES_PER_SM_CLK = 128
 # DRAM traffic of the walk kernel per launch from an ncu capture, valid only for
@@ -138,10 +142,12 @@ def run_reference(args):
     import oracle
     oracle.build()
     n_sample, moves = 4096, 100
-    kind, params, dt, et = 0, [2.0, 0.5, 0.5], 0.005, -2.9037
+    name = args.workload if args.workload in ("ground", "bernoulli") else "ground"
+    kind, params, dt, et, noise = _oracle_case(name)
 
     def one():
-        w = oracle.Walk(kind, params, n_walkers=n_sample, dt=dt, e_trial=et, seed=SEED)
+        w = oracle.Walk(kind, params, n_walkers=n_sample, dt=dt, e_trial=et, seed=SEED,
+                        noise=noise)
         w.advance(moves)
         return w
 
@@ -157,7 +163,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOADS["ground"], "name": "ground",
+        "data": "synthetic", "config": {"workload": WORKLOADS[name], "name": name,
                                         "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -165,13 +171,20 @@ def run_reference(args):
     }), flush=True)
 
 
-def cpu_baseline():
+def _oracle_case(name):
+    """(kind, params, dt, E_T, noise) of the ground-state workloads for the oracle."""
+    if name == "bernoulli":
+        return 0, [2.0, 0.5, 0.5], 1.0 / 900.0, -2.9037, 1
+    return 0, [2.0, 0.5, 0.5], 0.005, -2.9037, 0
+
+
+def cpu_baseline(name="ground"):
     import oracle
     oracle.build()
     n_sample, moves = 1 << 14, 600
-    kind, params, dt, et = 0, [2.0, 0.5, 0.5], 0.005, -2.9037
+    kind, params, dt, et, noise = _oracle_case(name)
     t0 = time.perf_counter()
-    w = oracle.Walk(kind, params, n_walkers=n_sample, dt=dt, e_trial=et, seed=SEED)
+    w = oracle.Walk(kind, params, n_walkers=n_sample, dt=dt, e_trial=et, seed=SEED, noise=noise)
     w.advance(moves)
     el = time.perf_counter() - t0
     return {"value": n_sample * moves / el, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -185,6 +198,8 @@ def _workload(name, rank):
         insts, moves = wl.ground_at_scale(0.005)
     elif name == "triplet":
         insts, moves = wl.triplet_at_scale()
+    elif name == "bernoulli":
+        insts, moves = wl.bernoulli_at_scale()
     else:
         insts, moves = wl.batched()
     for d in insts:
@@ -264,7 +279,8 @@ def run_ours(args):
     def descs(prec):
         return [gfk.InstanceDesc(n_walkers=d["n_walkers"], dt=d["dt"], e_trial=d["e_trial"],
                                  seed=d["seed"], state=d["state"], prec=prec,
-                                 rng_stream=d["rng_stream"], walker_id0=d["walker_id0"])
+                                 rng_stream=d["rng_stream"], walker_id0=d["walker_id0"],
+                                 noise=d["noise"])
                 for d in insts]
 
     ctx = gfk.Context(descs(gfk.GFK_PREC_MIXED), trials=trials)
@@ -352,7 +368,8 @@ def run_ours(args):
         ws_per_launch = walk_ws / max(1, walk_launches)
         sm_max = clk.get("sm_max_mhz") or 2070.0
         peak = n_sm * LANES_PER_SM_CLK * sm_max * 1e6 / 1e9      # Gop/s
-        ops = sum(OPS_PER_WALKER_STEP[d["kind"]] * d["n_walkers"] for d in insts) / n_walkers
+        ops = sum(OPS_PER_WALKER_STEP[(d["noise"], d["kind"])] * d["n_walkers"]
+                  for d in insts) / n_walkers
         achieved = ops * ws_per_launch / (avg_launch_ms / 1e3) / 1e9
         traffic = None
         if WALK_TRAFFIC["src_sha"] == _src_sha() and WALK_TRAFFIC["bytes_per_launch"]:
@@ -388,7 +405,7 @@ def run_ours(args):
             out["roofline"]["measured_ffma_lane_ops_per_s"] = gfk.gfk_measure_peak("ffma")
         except Exception:
             pass
-        if args.workload == "ground":
+        if args.workload in ("ground", "bernoulli"):
             # ---- the FP64 path on the same seeds, and the mixed path's energy error ----
             n_cmp = args.fp64_moves
             c64 = gfk.Context(descs(gfk.GFK_PREC_FP64), trials=trials)
@@ -417,7 +434,7 @@ def run_ours(args):
         if merged_e_final is not None:
             out["merged_E_final_all_ranks"] = merged_e_final
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.barrier()

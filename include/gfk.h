@@ -57,6 +57,20 @@ typedef enum { GFK_1S = 0, GFK_2S3 = 1, GFK_PZ = 2 } gfk_state;
  *                 FP64 above it, compensated (TwoSum) across blocks. */
 typedef enum { GFK_PREC_FP64 = 0, GFK_PREC_MIXED = 1 } gfk_prec;
 
+/* Increments of the walk, X <- X + b dt + sqrt(dt) xi.
+ * GFK_NOISE_GAUSSIAN:  xi = six N(0,1) normals (the Brownian increment of the
+ *   drifted diffusion written under Eq. 4) from Philox4x32-10 words by Box-Muller.
+ * GFK_NOISE_BERNOULLI: xi = six signs +-1, the paper's own random walk (the
+ *   construction of W(l) before the invariance principle: each coordinate moves
+ *   by eps/sqrt(n) per time step 1/n, so dt = 1/n and the paper's step length
+ *   1/scale is sqrt(dt)).  eps comes from the "Superduper" congruential generator
+ *   S_i = (69069 S_{i-1} + 1) mod 2^32, eps_i = +1 if S_i > 2^31, else -1.  Each
+ *   walker runs its own generator, seeded with word 0 of the Philox block
+ *   (walker id, 0, rng_stream, 5); move `step` uses outputs 6 step + 1 ..
+ *   6 step + 6 for x1, y1, z1, x2, y2, z2.  The initial positions are Gaussian
+ *   in both modes.  The generator's period is 2^32 outputs. */
+typedef enum { GFK_NOISE_GAUSSIAN = 0, GFK_NOISE_BERNOULLI = 1 } gfk_noise;
+
 /* Trial-function families, psi = Phi(r1_vec, r2_vec) * exp(u(r12)) with the
  * Jastrow factor u(r) = a rho + sum_{k=1..4} c_k rho^(k+1), rho = r/(1+beta r).
  *
@@ -83,8 +97,8 @@ typedef enum { GFK_TRIAL_JASTROW_PRODUCT = 0, GFK_TRIAL_ORBITAL_PAIRS = 1 } gfk_
  * function), the time step dt, the number of replications N_rep and a seed.
  * Random numbers are Philox4x32-10 with counter (walker id, m, rng_stream,
  * tag) and key (seed low, seed high): moves 2m and 2m+1 take words 0-5 and
- * 6-11 of the blocks with tags 0, 1, 2; the walker id is walker_id0 + the
- * walker's index.  The same (seed, rng_stream, walker id) gives the same
+ * 6-11 of the blocks with tags 0, 1, 2 (Gaussian noise; see gfk_noise for the
+ * Bernoulli mode); the walker id is walker_id0 + the walker's index.  The same (seed, rng_stream, walker id) gives the same
  * trajectory in any context and any launch configuration. */
 typedef struct {
     int32_t  state;          /* gfk_state                                         */
@@ -100,7 +114,7 @@ typedef struct {
                                 of one population on several GPUs take disjoint
                                 id ranges and together reproduce it exactly;
                                 id0 + n_walkers must not exceed 2^32             */
-    int32_t  reserved;       /* 0                                                  */
+    int32_t  noise;          /* gfk_noise; all instances of a context share it    */
 } gfk_instance_desc;
 
 /* Create a context holding n_inst instances (1 .. GFK_MAX_INSTANCES).

@@ -10,7 +10,9 @@ with the drift and the Laplacian taken by autograd from ln psi itself; the walk
 X_{n+1} = X_n + b(X_n) dt + sqrt(dt) xi_n (the SDE under Eq. 4), log-weights
 by the right-point rule, and the space-averaged loss at the last step.  The
 normals are the C oracle's Philox / Box-Muller stream (pinned separately), so
-the trajectories are the C oracle's.  d(loss)/d(theta) is autograd's.
+the trajectories are the C oracle's; with noise = 1 the increments are the C
+oracle's Bernoulli +-1 steps from each walker's Superduper generator.
+d(loss)/d(theta) is autograd's.
 
 Parity status: pinned by tests/test_oracle_pins.py (drift and E_L equal the C
 oracle's at random points; the loss equals the C oracle walk's E(t_S); the
@@ -21,7 +23,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import init_normals, move_normals
+from . import init_normals, move_bernoulli, move_normals
 
 THETA_NAMES = ("Z", "a", "beta", "c1", "c2", "c3", "c4")
 
@@ -57,7 +59,7 @@ def drift_and_local_energy(X: torch.Tensor, theta: torch.Tensor, ee_on: bool = T
 
 
 def walk_loss(theta, *, n_walkers, n_steps, dt, e_trial, seed, inst=0, sigma=0.5,
-              loss_kind=0, ee_on=True):
+              loss_kind=0, ee_on=True, noise=0):
     """The walk from a fresh population and its loss at the last step (differentiable
     in theta): loss 0 = sum w E_L / sum w, loss 1 = the weighted variance of E_L."""
     n = int(n_walkers)
@@ -67,7 +69,8 @@ def walk_loss(theta, *, n_walkers, n_steps, dt, e_trial, seed, inst=0, sigma=0.5
     b, el = drift_and_local_energy(X, theta, ee_on)
     sdt = float(np.sqrt(dt))
     for step in range(n_steps):
-        xi = torch.tensor(np.array([move_normals(seed, i, step, inst) for i in range(n)]),
+        draw = move_bernoulli if noise == 1 else move_normals
+        xi = torch.tensor(np.array([draw(seed, i, step, inst) for i in range(n)]),
                           dtype=torch.float64)
         X = X + b * dt + sdt * xi
         b, el = drift_and_local_energy(X, theta, ee_on)

@@ -19,8 +19,9 @@
 //
 // Positions are not stored for the whole walk: the forward keeps them every K
 // moves (checkpoints), and the backward recomputes each K-move segment from
-// its checkpoint with the same Philox words and the same arithmetic as the
-// forward kernel of its precision, then sweeps it in reverse.
+// its checkpoint with the same noise (Philox words, or the walker's Superduper
+// generator skipped ahead to the segment's first move) and the same arithmetic
+// as the forward kernel of its precision, then sweeps it in reverse.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -243,13 +244,22 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 T x[6];
                 PosIO<T>::load(ckpt + (int64_t)j * PosIO<T>::kWords * n, n, i, x);
                 PosIO<T>::store(seg, n, i, x);
+                uint32_t lcg = 0u;
+                if (inst->noise == GFK_NOISE_BERNOULLI)
+                    lcg = superduper_at(inst->id0 + (uint32_t)i, inst->stream, inst->k0, inst->k1,
+                                        (uint32_t)n_lo);
                 for (int m = n_lo; m < n_hi; ++m) {
                     EvalOut<T> ev;
                     eval_kind0<T>(tp, x, ev);
-                    uint32_t words[6];
-                    move_words(inst->id0 + (uint32_t)i, (uint32_t)m, inst->stream, inst->k0, inst->k1, words);
                     T xi[6];
-                    adj_normals(words, xi);
+                    if (inst->noise == GFK_NOISE_BERNOULLI) {
+                        bernoulli6<T>(lcg, xi);
+                    } else {
+                        uint32_t words[6];
+                        move_words(inst->id0 + (uint32_t)i, (uint32_t)m, inst->stream, inst->k0,
+                                   inst->k1, words);
+                        adj_normals(words, xi);
+                    }
                     adj_move(x, ev.b, xi, dt, sdt);
                     PosIO<T>::store(seg + (int64_t)(m - n_lo + 1) * PosIO<T>::kWords * n, n, i, x);
                 }

@@ -14,41 +14,9 @@
 #include <string>
 #include <vector>
 
+#include "gfk_launch.h"
 #include "gfk_types.h"
 
-namespace gfk {
-cudaError_t launch_init_fp64(int kind, int threads, int nblk, const InstDev* insts,
-                             const BlockMap& bm, const StateF64& st, PartialRec* part,
-                             unsigned long long* counters, cudaStream_t stream);
-cudaError_t launch_walk_fp64(int kind, int threads, int nblk, const InstDev* insts,
-                             const BlockMap& bm, const StateF64& st, uint32_t step0, int nsteps,
-                             PartialRec* part, unsigned long long* counters, cudaStream_t stream);
-cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
-                              const BlockMap& bm, const StateMixed& st, PartialRec* part,
-                              unsigned long long* counters, cudaStream_t stream);
-cudaError_t launch_walk_mixed(int kind, int wpt, int threads, int nblk, const InstDev* insts,
-                              const BlockMap& bm, const StateMixed& st, uint32_t step0,
-                              int nsteps, PartialRec* part, unsigned long long* counters,
-                              cudaStream_t stream);
-cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
-                               SeriesRow* series, int64_t series_cap, int64_t row_base,
-                               cudaStream_t stream);
-cudaError_t launch_finalize(const SeriesRow* rows, int64_t n, double n0, double* e, double* lnz,
-                            double* ess, cudaStream_t stream);
-cudaError_t launch_export(bool mixed, const StateF64& s64, const StateMixed& smx, int64_t off,
-                          int64_t n, double* x6, double* logw, uint8_t* alive,
-                          cudaStream_t stream);
-cudaError_t launch_adjoint_f64(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
-                               const double* ckpt, double* seg, const double* pos_final,
-                               const double* logw_final, double* ew, double* part_max,
-                               double* part_sums, double* part_theta, void* term, double* grad,
-                               cudaStream_t stream);
-cudaError_t launch_adjoint_f32(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
-                               const float* ckpt, float* seg, const float* pos_final,
-                               const double* logw_final, double* ew, double* part_max,
-                               double* part_sums, double* part_theta, void* term, double* grad,
-                               cudaStream_t stream);
-}  // namespace gfk
 
 using namespace gfk;
 
@@ -56,6 +24,7 @@ struct gfk_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int prec = GFK_PREC_FP64;
+    int noise = GFK_NOISE_GAUSSIAN;     // shared by every instance
     int n_inst = 0;
     std::vector<gfk_instance_desc> desc;
     std::vector<TrialHost> trial;
@@ -267,6 +236,7 @@ gfk_status upload_instances(gfk_ctx* ctx) {
         v.stream = d.rng_stream;
         v.id0 = d.walker_id0;
         v.ee_on = d.ee_on ? 1 : 0;
+        v.noise = d.noise;
         v.trial = ctx->trial[i];
     }
     GFK_CK(ctx, cudaMemcpyAsync(ctx->d_inst, h.data(), sizeof(InstDev) * ctx->n_inst,
@@ -369,11 +339,11 @@ gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t
         }
         if (ev0) GFK_CK(ctx, cudaEventRecord(ev0, ctx->stream));
         if (ctx->prec == GFK_PREC_FP64) {
-            GFK_CK(ctx, launch_walk_fp64(kind, ctx->threads, (int)nblk, ctx->d_inst, bm, ctx->s64,
-                                         step0, chunk, ctx->part, ctx->counters, ctx->stream));
+            GFK_CK(ctx, launch_walk_fp64(kind, ctx->noise, ctx->threads, (int)nblk, ctx->d_inst,
+                                         bm, ctx->s64, step0, chunk, ctx->part, ctx->counters, ctx->stream));
         } else {
-            GFK_CK(ctx, launch_walk_mixed(kind, ctx->wpt, ctx->threads, (int)nblk, ctx->d_inst, bm,
-                                          ctx->smx, step0, chunk, ctx->part, ctx->counters,
+            GFK_CK(ctx, launch_walk_mixed(kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
+                                          ctx->d_inst, bm, ctx->smx, step0, chunk, ctx->part, ctx->counters,
                                           ctx->stream));
         }
         if (ev1) {
@@ -477,6 +447,7 @@ uint64_t desc_hash(const gfk_ctx* ctx) {
         h = fnv1a(&d.ee_on, sizeof(d.ee_on), h);
         h = fnv1a(&d.init_sigma, sizeof(d.init_sigma), h);
         h = fnv1a(&d.walker_id0, sizeof(d.walker_id0), h);
+        h = fnv1a(&d.noise, sizeof(d.noise), h);
         h = fnv1a(&ctx->trial[i], sizeof(TrialHost), h);
     }
     return h;
@@ -524,7 +495,8 @@ gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_
         if (!(d.init_sigma > 0.0) || !finite_d(d.init_sigma)) return GFK_EINVAL;
         if (d.ee_on != 0 && d.ee_on != 1) return GFK_EINVAL;
         if ((uint64_t)d.walker_id0 + (uint64_t)d.n_walkers > (1ull << 32)) return GFK_EINVAL;
-        if (d.reserved != 0) return GFK_EINVAL;
+        if (d.noise != GFK_NOISE_GAUSSIAN && d.noise != GFK_NOISE_BERNOULLI) return GFK_EINVAL;
+        if (d.noise != inst[0].noise) return GFK_EINVAL;
         total += (d.n_walkers + 31) / 32 * 32;
     }
     if (total > (1ll << 34)) return GFK_EINVAL;
@@ -533,6 +505,7 @@ gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_
     if (!ctx) return GFK_ENOMEM;
     ctx->n_inst = n_inst;
     ctx->prec = inst[0].prec;
+    ctx->noise = inst[0].noise;
     ctx->desc.assign(inst, inst + n_inst);
     ctx->trial.assign(n_inst, TrialHost());
     ctx->has_trial.assign(n_inst, 0);
@@ -767,12 +740,12 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
                 e = cudaEventRecord(a, ctx->stream);
                 if (e != cudaSuccess) break;
                 if (ctx->prec == GFK_PREC_FP64)
-                    e = launch_walk_fp64(kind, ctx->threads, (int)nblk, ctx->d_inst, bm, ctx->s64,
-                                         (uint32_t)ctx->steps, chunk, ctx->part, ctx->counters,
+                    e = launch_walk_fp64(kind, ctx->noise, ctx->threads, (int)nblk, ctx->d_inst,
+                                         bm, ctx->s64, (uint32_t)ctx->steps, chunk, ctx->part, ctx->counters,
                                          ctx->stream);
                 else
-                    e = launch_walk_mixed(kind, ctx->wpt, ctx->threads, (int)nblk, ctx->d_inst, bm,
-                                          ctx->smx, (uint32_t)ctx->steps, chunk, ctx->part,
+                    e = launch_walk_mixed(kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
+                                          ctx->d_inst, bm, ctx->smx, (uint32_t)ctx->steps, chunk, ctx->part,
                                           ctx->counters, ctx->stream);
                 if (e == cudaSuccess)
                     e = launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
@@ -1092,9 +1065,10 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
                             cudaMemcpyDeviceToDevice, ctx->stream);
         const int steps = std::min(K, S - j * K);
         if (e == cudaSuccess)
-            e = f64 ? launch_walk_fp64(kind, shape.threads, (int)nblk, d_inst, bm, s64,
+            e = f64 ? launch_walk_fp64(kind, ctx->noise, shape.threads, (int)nblk, d_inst, bm, s64,
                                        (uint32_t)(j * K), steps, part, cnt, ctx->stream)
-                    : launch_walk_mixed(kind, shape.wpt, shape.threads, (int)nblk, d_inst, bm, smx,
+                    : launch_walk_mixed(kind, ctx->noise, shape.wpt, shape.threads, (int)nblk,
+                                        d_inst, bm, smx,
                                         (uint32_t)(j * K), steps, part, cnt, ctx->stream);
     }
     double* logw_final = (double*)(base + o_logw);

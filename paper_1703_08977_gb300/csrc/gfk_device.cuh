@@ -205,6 +205,60 @@ __device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6]) {
 }
 
 // ---------------------------------------------------------------------------
+// Bernoulli increments: the paper's own random walk (each coordinate moves by
+// +-1/sqrt(n) per time step 1/n, the construction of W(l) before the
+// invariance principle), with eps drawn from the "Superduper" congruential
+// generator S_i = (69069 S_{i-1} + 1) mod 2^32, eps_i = +1 if S_i > 2^31 and
+// -1 otherwise.  Every walker runs its own generator: S_0 is word 0 of the
+// Philox block (walker, 0, stream, 5), and move `step` takes the outputs
+// 6 step + 1 .. 6 step + 6 for x1, y1, z1, x2, y2, z2.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSuperduperMult = 69069u;
+
+__device__ __forceinline__ uint32_t superduper_seed(uint32_t walker, uint32_t stream,
+                                                    uint32_t k0, uint32_t k1) {
+    return philox10(walker, 0u, stream, 5u, k0, k1).w[0];
+}
+
+__device__ __forceinline__ uint32_t superduper_next(uint32_t s) {
+    return kSuperduperMult * s + 1u;              // unsigned arithmetic wraps mod 2^32
+}
+
+// The state n outputs later: the affine map x -> a x + 1 composed n times by
+// binary powering.  The generator's period is 2^32 (c odd, a = 1 mod 4), so the
+// count is taken mod 2^32.
+__device__ __forceinline__ uint32_t superduper_skip(uint32_t s, uint32_t n) {
+    uint32_t A = 1u, C = 0u;                      // the accumulated map
+    uint32_t a = kSuperduperMult, c = 1u;         // the map composed 2^j times
+    while (n != 0u) {
+        if (n & 1u) {
+            A = a * A;
+            C = a * C + c;
+        }
+        c = a * c + c;
+        a = a * a;
+        n >>= 1;
+    }
+    return A * s + C;
+}
+
+// Generator state at the start of move `step` (before its six outputs).
+__device__ __forceinline__ uint32_t superduper_at(uint32_t walker, uint32_t stream, uint32_t k0,
+                                                  uint32_t k1, uint32_t step) {
+    return superduper_skip(superduper_seed(walker, stream, k0, k1), 6u * step);
+}
+
+// The six increments of one move; advances the state by six outputs.
+template <typename R>
+__device__ __forceinline__ void bernoulli6(uint32_t& s, R eps[6]) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        s = superduper_next(s);
+        eps[d] = s > 0x80000000u ? R(1) : R(-1);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Precision helpers
 // ---------------------------------------------------------------------------
 // Distance and inverse distance from a squared distance.  FP32: one hardware

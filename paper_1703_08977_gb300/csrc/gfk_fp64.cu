@@ -6,7 +6,8 @@
 // One thread advances one walker for a whole chunk of steps with its state in
 // registers.  Per step (the discretised Eq. 4 with the drifted diffusion under
 // it):
-//   xi       <- six N(0,1) from Philox4x32-10 words (three blocks per two moves)
+//   xi       <- six N(0,1) from Philox4x32-10 words (three blocks per two moves),
+//               or (NOISE = 1) six signs +-1 from the walker's Superduper generator
 //   X        <- X + b(X) dt + sqrt(dt) xi                       (Euler-Maruyama)
 //   b, E_L   <- trial function at the new X
 //   node     :  sign psi changed (or psi = 0) -> walker killed
@@ -19,6 +20,7 @@
 
 #include "gfk_block.cuh"
 #include "gfk_device.cuh"
+#include "gfk_launch.h"
 #include "gfk_types.h"
 
 namespace gfk {
@@ -91,7 +93,7 @@ init_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
     flush_counters(counters, inst, n_nonfinite, n_node, 0u);
 }
 
-template <int KIND>
+template <int KIND, int NOISE>
 __global__ void __launch_bounds__(kMaxThreads)
 walk_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
                  uint32_t step0, int nsteps, PartialRec* __restrict__ part, int nblk,
@@ -127,6 +129,7 @@ walk_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
     }
     EvalOut<double> ev;
     if (sg != 0) eval_trial<KIND, double>(t, x, ev);
+    uint32_t lcg = NOISE == 1 ? superduper_at(I.id0 + (uint32_t)id, stream, k0, k1, step0) : 0u;
     unsigned n_nonfinite = 0, n_node = 0, n_coal = 0;
     double c = block_max_shift(sg != 0 ? logw : -INFINITY, s_red);
 
@@ -135,9 +138,13 @@ walk_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
         double q[5] = {0, 0, 0, 0, 0};
         if (sg != 0) {
             double xi[6];
-            uint32_t words[6];
-            move_words(I.id0 + (uint32_t)id, step, stream, k0, k1, words);
-            normals6_f64(words, xi);
+            if (NOISE == 1) {
+                bernoulli6<double>(lcg, xi);
+            } else {
+                uint32_t words[6];
+                move_words(I.id0 + (uint32_t)id, step, stream, k0, k1, words);
+                normals6_f64(words, xi);
+            }
 #pragma unroll
             for (int d = 0; d < 6; ++d) x[d] = x[d] + ev.b[d] * dt + sdt * xi[d];
             eval_trial<KIND, double>(t, x, ev);
@@ -210,19 +217,32 @@ cudaError_t launch_init_fp64(int kind, int threads, int nblk, const InstDev* ins
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk_fp64(int kind, int threads, int nblk, const InstDev* insts,
+template <int NOISE>
+static void launch_walk_fp64_n(int kind, int threads, int nblk, const InstDev* insts,
+                               const BlockMap& bm, const StateF64& st, uint32_t step0,
+                               int nsteps, PartialRec* part, unsigned long long* counters,
+                               cudaStream_t stream) {
+    if (kind == 0)
+        walk_fp64_kernel<0, NOISE><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
+                                                                 part, nblk, counters);
+    else if (kind == 1)
+        walk_fp64_kernel<1, NOISE><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
+                                                                 part, nblk, counters);
+    else
+        walk_fp64_kernel<2, NOISE><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
+                                                                 part, nblk, counters);
+}
+
+cudaError_t launch_walk_fp64(int kind, int noise, int threads, int nblk, const InstDev* insts,
                              const BlockMap& bm, const StateF64& st, uint32_t step0, int nsteps,
                              PartialRec* part, unsigned long long* counters,
                              cudaStream_t stream) {
-    if (kind == 0)
-        walk_fp64_kernel<0><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps, part,
-                                                          nblk, counters);
-    else if (kind == 1)
-        walk_fp64_kernel<1><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps, part,
-                                                          nblk, counters);
+    if (noise == GFK_NOISE_BERNOULLI)
+        launch_walk_fp64_n<1>(kind, threads, nblk, insts, bm, st, step0, nsteps, part, counters,
+                              stream);
     else
-        walk_fp64_kernel<2><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps, part,
-                                                          nblk, counters);
+        launch_walk_fp64_n<0>(kind, threads, nblk, insts, bm, st, step0, nsteps, part, counters,
+                              stream);
     return cudaGetLastError();
 }
 

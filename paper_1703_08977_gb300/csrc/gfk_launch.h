@@ -1,0 +1,43 @@
+// Host launchers of the GFK kernels (defined beside their kernels), called by
+// the C ABI layer.  Each queues its kernels on `stream` and returns
+// cudaGetLastError(); `kind` is the trial kind (2 = per-block dispatch).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gfk_types.h"
+
+namespace gfk {
+cudaError_t launch_init_fp64(int kind, int threads, int nblk, const InstDev* insts,
+                             const BlockMap& bm, const StateF64& st, PartialRec* part,
+                             unsigned long long* counters, cudaStream_t stream);
+// noise: gfk_noise of the context (selects the kernel instantiation)
+cudaError_t launch_walk_fp64(int kind, int noise, int threads, int nblk, const InstDev* insts,
+                             const BlockMap& bm, const StateF64& st, uint32_t step0, int nsteps,
+                             PartialRec* part, unsigned long long* counters, cudaStream_t stream);
+cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
+                              const BlockMap& bm, const StateMixed& st, PartialRec* part,
+                              unsigned long long* counters, cudaStream_t stream);
+cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk,
+                              const InstDev* insts, const BlockMap& bm, const StateMixed& st,
+                              uint32_t step0, int nsteps, PartialRec* part,
+                              unsigned long long* counters, cudaStream_t stream);
+cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
+                               SeriesRow* series, int64_t series_cap, int64_t row_base,
+                               cudaStream_t stream);
+cudaError_t launch_finalize(const SeriesRow* rows, int64_t n, double n0, double* e, double* lnz,
+                            double* ess, cudaStream_t stream);
+cudaError_t launch_export(bool mixed, const StateF64& s64, const StateMixed& smx, int64_t off,
+                          int64_t n, double* x6, double* logw, uint8_t* alive,
+                          cudaStream_t stream);
+cudaError_t launch_adjoint_f64(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
+                               const double* ckpt, double* seg, const double* pos_final,
+                               const double* logw_final, double* ew, double* part_max,
+                               double* part_sums, double* part_theta, void* term, double* grad,
+                               cudaStream_t stream);
+cudaError_t launch_adjoint_f32(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
+                               const float* ckpt, float* seg, const float* pos_final,
+                               const double* logw_final, double* ew, double* part_max,
+                               double* part_sums, double* part_theta, void* term, double* grad,
+                               cudaStream_t stream);
+}  // namespace gfk

@@ -6,7 +6,8 @@
 // the state in registers.  Per step and walker (the discretised Eq. 4 and the
 // drifted diffusion under it):
 //   xi     <- six N(0,1): Philox4x32-10 words (three blocks serve two moves),
-//             FP32 Box-Muller on the hardware log2 / rsqrt / sin / cos
+//             FP32 Box-Muller; or (NOISE = 1) six signs +-1 from the walker's
+//             Superduper generator, skipped ahead to the launch's first move
 //   X      <- X + b dt + sqrt(dt) xi                    (FP32, fused multiply-add)
 //   b, E_L <- trial function at X in the cusp-cancelled form (FP32)
 //   node   :  sign psi changed or psi = 0 -> killed
@@ -23,6 +24,7 @@
 
 #include "gfk_block.cuh"
 #include "gfk_device.cuh"
+#include "gfk_launch.h"
 #include "gfk_types.h"
 
 namespace gfk {
@@ -51,6 +53,32 @@ __device__ __forceinline__ void load_mixed(const StateMixed& st, int64_t slot, f
     const long long hi = (long long)__float_as_int(b.w);
     logw = __longlong_as_double((hi << 32) | lo);
     sg = st.sgn[slot];
+}
+
+// Philox words of one move.  The even move of a pair runs the blocks of tags
+// 0 and 1 and keeps tag 1's last two words (carry) for the odd move, which
+// runs tag 2 (and tag 1 again when the launch starts on an odd move).
+__device__ __forceinline__ void pair_move_words(const PhiloxPre& pre, uint32_t carry[2],
+                                                uint32_t step, bool first, uint32_t k0,
+                                                uint32_t k1, uint32_t words[6]) {
+    const uint32_t m = step >> 1;
+    if ((step & 1u) == 0u) {
+        Words4 wa, wb;
+        philox10_pair(pre, m, k0, k1, wa, wb);
+        words[0] = wa.w[0]; words[1] = wa.w[1]; words[2] = wa.w[2]; words[3] = wa.w[3];
+        words[4] = wb.w[0]; words[5] = wb.w[1];
+        carry[0] = wb.w[2];
+        carry[1] = wb.w[3];
+    } else {
+        if (first) {
+            const Words4 wb = philox10_tag(pre, m, 1u, k0, k1);
+            carry[0] = wb.w[2];
+            carry[1] = wb.w[3];
+        }
+        const Words4 wc = philox10_tag(pre, m, 2u, k0, k1);
+        words[0] = carry[0]; words[1] = carry[1];
+        words[2] = wc.w[0]; words[3] = wc.w[1]; words[4] = wc.w[2]; words[5] = wc.w[3];
+    }
 }
 
 template <int KIND>
@@ -119,7 +147,7 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     flush_counters(counters, inst, n_nonfinite, n_node, 0u);
 }
 
-template <int KIND, int WPT>
+template <int KIND, int WPT, int NOISE>
 __global__ void __launch_bounds__(kMaxThreads)
 walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                   uint32_t step0, int nsteps, PartialRec* __restrict__ part, int nblk,
@@ -153,6 +181,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 
     PhiloxPre pre[WPT];
     uint32_t carry[WPT][2];      // tag-1 words 2-3 of the even move, used by the odd one
+    uint32_t lcg[WPT];           // Bernoulli mode: generator state before this move
     int64_t slot[WPT];
     bool valid[WPT];
     float x[WPT][6], b[WPT][6];
@@ -163,7 +192,12 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     for (int k = 0; k < WPT; ++k) {
         const int64_t id = (int64_t)(blk - bm.begin[inst]) * T * WPT + (int64_t)k * T + threadIdx.x;
         valid[k] = id < I.n;
-        pre[k] = philox_pre(I.id0 + (uint32_t)id, I.stream, k0, k1);
+        if (NOISE == 0) {
+            pre[k] = philox_pre(I.id0 + (uint32_t)id, I.stream, k0, k1);
+            lcg[k] = 0u;
+        } else {
+            lcg[k] = superduper_at(I.id0 + (uint32_t)id, I.stream, k0, k1, step0);
+        }
         carry[k][0] = carry[k][1] = 0u;
         slot[k] = I.off + id;
         sg[k] = 0;
@@ -203,30 +237,14 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
             const bool alive = sg[k] != 0;
-            // words of this move: the even move of a pair runs the blocks of
-            // tags 0 and 1 and keeps tag 1's last two words for the odd move,
-            // which runs tag 2 (and tag 1 again if the launch starts on it)
-            uint32_t words[6];
-            const uint32_t m = step >> 1;
-            if ((step & 1u) == 0u) {
-                Words4 wa, wb;
-                philox10_pair(pre[k], m, k0, k1, wa, wb);
-                words[0] = wa.w[0]; words[1] = wa.w[1]; words[2] = wa.w[2]; words[3] = wa.w[3];
-                words[4] = wb.w[0]; words[5] = wb.w[1];
-                carry[k][0] = wb.w[2];
-                carry[k][1] = wb.w[3];
-            } else {
-                if (s == 0) {
-                    const Words4 wb = philox10_tag(pre[k], m, 1u, k0, k1);
-                    carry[k][0] = wb.w[2];
-                    carry[k][1] = wb.w[3];
-                }
-                const Words4 wc = philox10_tag(pre[k], m, 2u, k0, k1);
-                words[0] = carry[k][0]; words[1] = carry[k][1];
-                words[2] = wc.w[0]; words[3] = wc.w[1]; words[4] = wc.w[2]; words[5] = wc.w[3];
-            }
             float xi[6], xn[6];
-            normals6_f32(words, xi);
+            if (NOISE == 1) {
+                bernoulli6<float>(lcg[k], xi);
+            } else {
+                uint32_t words[6];
+                pair_move_words(pre[k], carry[k], step, s == 0, k0, k1, words);
+                normals6_f32(words, xi);
+            }
 #pragma unroll
             for (int d = 0; d < 6; ++d) xn[d] = fmaf(sdt, xi[d], fmaf(b[k][d], dt, x[k][d]));
             EvalOut<float> ev;
@@ -245,7 +263,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 #pragma unroll
             for (int d = 0; d < 6; ++d) {
                 x[k][d] = alive ? xn[d] : x[k][d];      // a walker killed now stays here
-                b[k][d] = stay ? ev.b[d] : b[k][d];
+                b[k][d] = ev.b[d];                      // read only while the walker lives
             }
             sg[k] = stay ? sg[k] : 0;
             // Kahan: S accumulates E_L - E_T since the last fold
@@ -351,40 +369,53 @@ cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* in
     return cudaGetLastError();
 }
 
-template <int KIND>
+template <int KIND, int NOISE>
 static void launch_walk_mixed_k(int wpt, int threads, int nblk, const InstDev* insts,
                                 const BlockMap& bm, const StateMixed& st, uint32_t step0,
                                 int nsteps, PartialRec* part, unsigned long long* counters,
                                 cudaStream_t stream) {
     switch (wpt) {
         case 1:
-            walk_mixed_kernel<KIND, 1><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
-                                                                     part, nblk, counters);
+            walk_mixed_kernel<KIND, 1, NOISE><<<nblk, threads, 0, stream>>>(
+                insts, bm, st, step0, nsteps, part, nblk, counters);
             break;
         case 2:
-            walk_mixed_kernel<KIND, 2><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
-                                                                     part, nblk, counters);
+            walk_mixed_kernel<KIND, 2, NOISE><<<nblk, threads, 0, stream>>>(
+                insts, bm, st, step0, nsteps, part, nblk, counters);
             break;
         default:
-            walk_mixed_kernel<KIND, 4><<<nblk, threads, 0, stream>>>(insts, bm, st, step0, nsteps,
-                                                                     part, nblk, counters);
+            walk_mixed_kernel<KIND, 4, NOISE><<<nblk, threads, 0, stream>>>(
+                insts, bm, st, step0, nsteps, part, nblk, counters);
             break;
     }
 }
 
-cudaError_t launch_walk_mixed(int kind, int wpt, int threads, int nblk, const InstDev* insts,
-                              const BlockMap& bm, const StateMixed& st, uint32_t step0,
-                              int nsteps, PartialRec* part, unsigned long long* counters,
-                              cudaStream_t stream) {
+template <int NOISE>
+static void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, const InstDev* insts,
+                                const BlockMap& bm, const StateMixed& st, uint32_t step0,
+                                int nsteps, PartialRec* part, unsigned long long* counters,
+                                cudaStream_t stream) {
     if (kind == 0)
-        launch_walk_mixed_k<0>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part, counters,
-                               stream);
+        launch_walk_mixed_k<0, NOISE>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
+                                      counters, stream);
     else if (kind == 1)
-        launch_walk_mixed_k<1>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part, counters,
-                               stream);
+        launch_walk_mixed_k<1, NOISE>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
+                                      counters, stream);
     else
-        launch_walk_mixed_k<2>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part, counters,
-                               stream);
+        launch_walk_mixed_k<2, NOISE>(wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
+                                      counters, stream);
+}
+
+cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk,
+                              const InstDev* insts, const BlockMap& bm, const StateMixed& st,
+                              uint32_t step0, int nsteps, PartialRec* part,
+                              unsigned long long* counters, cudaStream_t stream) {
+    if (noise == GFK_NOISE_BERNOULLI)
+        launch_walk_mixed_n<1>(kind, wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
+                               counters, stream);
+    else
+        launch_walk_mixed_n<0>(kind, wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
+                               counters, stream);
     return cudaGetLastError();
 }
 

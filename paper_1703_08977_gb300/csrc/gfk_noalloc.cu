@@ -24,20 +24,9 @@
 #include <cstring>
 #include <mutex>
 
+#include "gfk_launch.h"
 #include "gfk_types.h"
 
-namespace gfk {
-cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
-                              const BlockMap& bm, const StateMixed& st, PartialRec* part,
-                              unsigned long long* counters, cudaStream_t stream);
-cudaError_t launch_walk_mixed(int kind, int wpt, int threads, int nblk, const InstDev* insts,
-                              const BlockMap& bm, const StateMixed& st, uint32_t step0,
-                              int nsteps, PartialRec* part, unsigned long long* counters,
-                              cudaStream_t stream);
-cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
-                               SeriesRow* series, int64_t series_cap, int64_t row_base,
-                               cudaStream_t stream);
-}  // namespace gfk
 
 using namespace gfk;
 
@@ -125,8 +114,8 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     if (!(d.dt > 0.0) || !std::isfinite(d.dt) || !std::isfinite(d.e_trial)) return GFK_EINVAL;
     if (!(d.init_sigma > 0.0) || !std::isfinite(d.init_sigma)) return GFK_EINVAL;
     if (d.ee_on != 0 && d.ee_on != 1) return GFK_EINVAL;
-    if ((uint64_t)d.walker_id0 + (uint64_t)d.n_walkers > (1ull << 32) || d.reserved != 0)
-        return GFK_EINVAL;
+    if ((uint64_t)d.walker_id0 + (uint64_t)d.n_walkers > (1ull << 32)) return GFK_EINVAL;
+    if (d.noise != GFK_NOISE_GAUSSIAN && d.noise != GFK_NOISE_BERNOULLI) return GFK_EINVAL;
     if (n_steps < 0 || step0 < 0 || (init && step0 != 0)) return GFK_EINVAL;
     if (step0 + n_steps > 0xffffffffll) return GFK_EINVAL;
     if (((uintptr_t)dev_p0 | (uintptr_t)dev_p1) & 15u) return GFK_EINVAL;
@@ -154,6 +143,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     inst.stream = d.rng_stream;
     inst.id0 = d.walker_id0;
     inst.ee_on = d.ee_on ? 1 : 0;
+    inst.noise = d.noise;
     inst.trial = trial;
     InstDev* d_inst = (InstDev*)scratch;
     PartialRec* part = (PartialRec*)(scratch + kHeaderBytes);
@@ -195,7 +185,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     int64_t done = 0;
     while (done < n_steps) {
         const int chunk = (int)((n_steps - done) < rows_fit ? (n_steps - done) : rows_fit);
-        NA_CK(launch_walk_mixed(kind, kWpt, kThreads, nblk, d_inst, bm, sm,
+        NA_CK(launch_walk_mixed(kind, d.noise, kWpt, kThreads, nblk, d_inst, bm, sm,
                                 (uint32_t)(step0 + done), chunk, part, dev_counters, stream));
         NA_CK(launch_reduce_rows(part, nblk, bm, chunk, rows, n_rows, (init ? 1 : 0) + done, stream));
         done += chunk;

@@ -31,6 +31,7 @@ struct InstDev {
     uint32_t stream;    // third Philox counter word
     uint32_t id0;       // Philox id of the instance's first walker
     int32_t ee_on;
+    int32_t noise;      // gfk_noise: Gaussian (Philox normals) or Bernoulli (Superduper)
     TrialHost trial;
 };
 

@@ -25,11 +25,12 @@ EXACT = {0: -2.9037243770341195, 1: -2.17522937823679130, 2: -2.123843086498093}
 
 
 def replica_energies(state, dt, t_total, n_walkers, replicas, seed=0, prec=gfk.GFK_PREC_MIXED,
-                     growth_times=None):
+                     growth_times=None, noise=gfk.GFK_NOISE_GAUSSIAN):
     kind, params = workloads.trial_for_state(state)
     et = workloads.E_T[state]
     descs = [gfk.InstanceDesc(n_walkers=n_walkers, dt=dt, e_trial=et, seed=seed, state=state,
-                              prec=prec, rng_stream=100 + r) for r in range(replicas)]
+                              prec=prec, rng_stream=100 + r, noise=noise)
+             for r in range(replicas)]
     n_moves = int(round(t_total / dt))
     with gfk.Context(descs, trials=[(kind, params)] * replicas) as ctx:
         ctx.propagate(n_moves)
@@ -43,6 +44,7 @@ def replica_energies(state, dt, t_total, n_walkers, replicas, seed=0, prec=gfk.G
                 lam.append(analysis.growth_from_series(et, dt, en["ln_z"], growth_times)[0])
     e_mean = np.array(e_mean)
     out = {"state": state, "dt": dt, "t": t_total, "walkers": n_walkers, "replicas": replicas,
+           "noise": noise,
            "E": float(e_mean.mean()), "E_err": float(e_mean.std(ddof=1) / np.sqrt(replicas)),
            "ess_final_over_N": float(np.mean(ess_end)) / n_walkers}
     if lam:
@@ -52,8 +54,10 @@ def replica_energies(state, dt, t_total, n_walkers, replicas, seed=0, prec=gfk.G
     return out
 
 
-def dt_study(state, dts, t_total, n_walkers, replicas, seed=0, prec=gfk.GFK_PREC_MIXED):
-    rows = [replica_energies(state, dt, t_total, n_walkers, replicas, seed, prec) for dt in dts]
+def dt_study(state, dts, t_total, n_walkers, replicas, seed=0, prec=gfk.GFK_PREC_MIXED,
+             noise=gfk.GFK_NOISE_GAUSSIAN):
+    rows = [replica_energies(state, dt, t_total, n_walkers, replicas, seed, prec, noise=noise)
+            for dt in dts]
     e0, err, slope = analysis.dt_extrapolate([r["dt"] for r in rows], [r["E"] for r in rows],
                                              [r["E_err"] for r in rows])
     return {"rows": rows, "E_dt0": e0, "E_dt0_err": err, "slope": slope, "exact": EXACT[state]}
@@ -67,25 +71,27 @@ def paired_bias(state, dt, t_total, n_walkers, replicas, seed=0):
     return {"mixed": a, "fp64": b}
 
 
-def replica_series(state, dt, t_total, n_walkers, replicas, seed, prec):
+def replica_series(state, dt, t_total, n_walkers, replicas, seed, prec,
+                   noise=gfk.GFK_NOISE_GAUSSIAN):
     kind, params = workloads.trial_for_state(state)
     descs = [gfk.InstanceDesc(n_walkers=n_walkers, dt=dt, e_trial=workloads.E_T[state],
-                              seed=seed, state=state, prec=prec, rng_stream=100 + r)
+                              seed=seed, state=state, prec=prec, rng_stream=100 + r, noise=noise)
              for r in range(replicas)]
     with gfk.Context(descs, trials=[(kind, params)] * replicas) as ctx:
         ctx.propagate(int(round(t_total / dt)))
         return np.array([ctx.energy(r)["E"] for r in range(replicas)])
 
 
-def paired_difference(state, dt, t_total, n_walkers, replicas, seed=0):
+def paired_difference(state, dt, t_total, n_walkers, replicas, seed=0,
+                      noise=gfk.GFK_NOISE_GAUSSIAN):
     """Per replica the second-half time average of E_mixed(t) - E_fp64(t) on the same
     walkers and noise; mean and standard error over replicas."""
-    em = replica_series(state, dt, t_total, n_walkers, replicas, seed, gfk.GFK_PREC_MIXED)
-    ef = replica_series(state, dt, t_total, n_walkers, replicas, seed, gfk.GFK_PREC_FP64)
+    em = replica_series(state, dt, t_total, n_walkers, replicas, seed, gfk.GFK_PREC_MIXED, noise)
+    ef = replica_series(state, dt, t_total, n_walkers, replicas, seed, gfk.GFK_PREC_FP64, noise)
     d = em - ef
     per = d[:, d.shape[1] // 2:].mean(axis=1)
     return {"state": state, "dt": dt, "t": t_total, "walkers": n_walkers, "replicas": replicas,
-            "bias": float(per.mean()), "bias_err": float(per.std(ddof=1) / np.sqrt(replicas)),
+            "noise": noise, "bias": float(per.mean()), "bias_err": float(per.std(ddof=1) / np.sqrt(replicas)),
             "max_abs_step_difference": float(np.abs(d).max())}
 
 
@@ -97,8 +103,10 @@ def main():
     ap.add_argument("--t", type=float, default=20.0)
     ap.add_argument("--dts", type=float, nargs="+", default=[0.01, 0.005, 0.0025])
     ap.add_argument("--prec", type=int, default=1)
+    ap.add_argument("--noise", type=int, default=0, help="0 Gaussian, 1 Bernoulli (+-1)")
     a = ap.parse_args()
-    print(json.dumps(dt_study(a.state, a.dts, a.t, a.walkers, a.replicas, prec=a.prec)))
+    print(json.dumps(dt_study(a.state, a.dts, a.t, a.walkers, a.replicas, prec=a.prec,
+                              noise=a.noise)))
 
 
 if __name__ == "__main__":

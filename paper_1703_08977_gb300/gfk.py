@@ -22,6 +22,7 @@ GFK_OK, GFK_EINVAL, GFK_ENOMEM, GFK_ECUDA, GFK_ESTATE, GFK_ENONFINITE, GFK_EOVER
     GFK_ETIMEOUT = range(8)
 GFK_1S, GFK_2S3, GFK_PZ = 0, 1, 2
 GFK_PREC_FP64, GFK_PREC_MIXED = 0, 1
+GFK_NOISE_GAUSSIAN, GFK_NOISE_BERNOULLI = 0, 1
 GFK_TRIAL_JASTROW_PRODUCT, GFK_TRIAL_ORBITAL_PAIRS = 0, 1
 GFK_MAX_TERMS = 4
 GFK_MAX_INSTANCES = 64
@@ -44,7 +45,7 @@ class gfk_instance_desc(ctypes.Structure):
                 ("e_trial", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("rng_stream", ctypes.c_uint32), ("ee_on", ctypes.c_int32),
                 ("init_sigma", ctypes.c_double), ("walker_id0", ctypes.c_uint32),
-                ("reserved", ctypes.c_int32)]
+                ("noise", ctypes.c_int32)]
 
 
 class GfkError(RuntimeError):
@@ -296,13 +297,14 @@ def gfk_autotune(ctx, probe_steps=256):
 
 
 def autotune_cached(ctx, descs, trials, probe_steps=256, path=None):
-    """gfk_autotune with a JSON cache keyed by device, precision, trial kinds and walker
-    counts (in the package's build folder); a cached shape is applied without timing."""
+    """gfk_autotune with a JSON cache keyed by device, precision, noise mode, trial kinds
+    and walker counts (in the package's build folder); a cached shape is applied without
+    timing."""
     import json
     import torch
     path = path or os.path.join(os.path.dirname(_build.LIB), "autotune.json")
     key = json.dumps({"device": torch.cuda.get_device_name(),
-                      "prec": int(descs[0].prec),
+                      "prec": int(descs[0].prec), "noise": int(descs[0].noise),
                       "kinds": [int(k) for k, _ in trials],
                       "walkers": [int(d.n_walkers) for d in descs]}, sort_keys=True)
     cache = {}
@@ -351,12 +353,13 @@ class InstanceDesc:
     ee_on: int = 1
     init_sigma: float = 0.5
     walker_id0: int = 0
+    noise: int = GFK_NOISE_GAUSSIAN
 
     def c(self) -> gfk_instance_desc:
         return gfk_instance_desc(int(self.state), int(self.prec), int(self.n_walkers),
                                  float(self.dt), float(self.e_trial), int(self.seed),
                                  int(self.rng_stream), int(self.ee_on), float(self.init_sigma),
-                                 int(self.walker_id0), 0)
+                                 int(self.walker_id0), int(self.noise))
 
 
 class Context:

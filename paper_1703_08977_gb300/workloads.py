@@ -91,10 +91,11 @@ def trial_for_state(state):
     return {0: (KIND0, ground()), 1: (KIND1, triplet_2s3()), 2: (KIND1, pz_state(+1.0))}[state]
 
 
-def instance(state, n_walkers, dt, seed=0, rng_stream=0):
+def instance(state, n_walkers, dt, seed=0, rng_stream=0, noise=0):
     kind, params = trial_for_state(state)
     return dict(state=state, n_walkers=int(n_walkers), dt=float(dt), e_trial=E_T[state],
-                seed=int(seed), rng_stream=int(rng_stream), kind=kind, params=params)
+                seed=int(seed), rng_stream=int(rng_stream), kind=kind, params=params,
+                noise=int(noise))
 
 
 def ground_fp64_correctness():
@@ -112,6 +113,12 @@ def ground_at_scale(dt=0.005):
 def triplet_at_scale():
     """He 2^3S with the exact node: 2^20 walkers, dt 0.0025, 20000 moves."""
     return [instance(1, 1 << 20, 0.0025)], 20000
+
+
+def bernoulli_at_scale():
+    """He 1^1S walked with the paper's +-1 steps (Superduper generators): 2^20 walkers,
+    20000 moves at dt = 1/900, i.e. the paper's scale 30 (step length 1/30), t = 22.2."""
+    return [instance(0, 1 << 20, 1.0 / 900.0, noise=1)], 20000
 
 
 def batched(seed=1, n_moves=10000, scale=1.0):

@@ -42,7 +42,7 @@ def _desc(**kw):
 @pytest.mark.parametrize("bad", [
     dict(n_walkers=0), dict(n_walkers=-5), dict(n_walkers=2**31), dict(dt=0.0), dict(dt=-1e-3),
     dict(dt=float("nan")), dict(e_trial=float("inf")), dict(init_sigma=0.0), dict(state=7),
-    dict(prec=3), dict(ee_on=2)])
+    dict(prec=3), dict(ee_on=2), dict(noise=2), dict(noise=-1)])
 def test_create_rejects_bad_descriptors(bad):
     lib = gfk.load()
     arr = (gfk.gfk_instance_desc * 1)(_desc(**bad))
@@ -51,11 +51,14 @@ def test_create_rejects_bad_descriptors(bad):
     assert out.value is None
 
 
-def test_create_rejects_bad_counts_and_mixed_precisions():
+def test_create_rejects_bad_counts_and_mixed_precisions_or_noise():
     lib = gfk.load()
     out = ctypes.c_void_p()
     arr = (gfk.gfk_instance_desc * 2)(_desc(prec=0), _desc(prec=1))
     assert lib.gfk_create(arr, 2, None, ctypes.byref(out)) == gfk.GFK_EINVAL
+    mixed_noise = (gfk.gfk_instance_desc * 2)(_desc(noise=gfk.GFK_NOISE_GAUSSIAN),
+                                              _desc(noise=gfk.GFK_NOISE_BERNOULLI))
+    assert lib.gfk_create(mixed_noise, 2, None, ctypes.byref(out)) == gfk.GFK_EINVAL
     assert lib.gfk_create(arr, 0, None, ctypes.byref(out)) == gfk.GFK_EINVAL
     assert lib.gfk_create(None, 1, None, ctypes.byref(out)) == gfk.GFK_EINVAL
     assert lib.gfk_create(arr, 1, None, None) == gfk.GFK_EINVAL

@@ -480,15 +480,18 @@ def test_grad_oracle_drift_and_energy_match_c_oracle():
         assert abs(float(el[i]) - elc) <= 1e-11 * max(1, abs(elc))
 
 
-def test_grad_oracle_loss_matches_c_oracle_walk():
-    """Its walk is the C oracle's walk: same final E(t) and weighted variance."""
+@pytest.mark.parametrize("noise", [0, 1])
+def test_grad_oracle_loss_matches_c_oracle_walk(noise):
+    """Its walk is the C oracle's walk (either noise mode): same final E(t) and weighted
+    variance."""
     torch = pytest.importorskip("torch")
     from oracle import grad as og
     theta = [2.0, 0.5, 0.5, 0.0, 0.0, 0.0, 0.0]
-    kw = dict(n_walkers=24, n_steps=12, dt=0.01, e_trial=-2.9, seed=4, inst=1)
+    kw = dict(n_walkers=24, n_steps=12, dt=0.01, e_trial=-2.9, seed=4, inst=1, noise=noise)
     L = og.walk_loss(torch.tensor(theta, dtype=torch.float64), **kw)
     V = og.walk_loss(torch.tensor(theta, dtype=torch.float64), loss_kind=1, **kw)
-    w = oracle.Walk(0, theta, n_walkers=24, dt=0.01, e_trial=-2.9, seed=4, inst=1).advance(12)
+    w = oracle.Walk(0, theta, n_walkers=24, dt=0.01, e_trial=-2.9, seed=4, inst=1,
+                    noise=noise).advance(12)
     s = w.series()
     assert abs(float(L) - s["E"][-1]) <= 1e-11
     assert abs(float(V) - s["var"][-1]) <= 1e-10

@@ -17,14 +17,15 @@ from paper_1703_08977_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kind,params,et", [(0, wl.ground(), -2.9),
-                                            (1, wl.triplet_2s3(), -2.175)])
-def test_noalloc_matches_propagate_on_two_calls(gfk_lib, kind, params, et):
+@pytest.mark.parametrize("kind,params,et,noise", [(0, wl.ground(), -2.9, 0),
+                                                  (1, wl.triplet_2s3(), -2.175, 0),
+                                                  (0, wl.ground(), -2.9, 1)])
+def test_noalloc_matches_propagate_on_two_calls(gfk_lib, kind, params, et, noise):
     import torch
     gfk = gfk_lib
     n, m1, m2 = 5000 + 7, 48, 80
     desc = gfk.InstanceDesc(n_walkers=n, dt=0.01, e_trial=et, seed=3, prec=gfk.GFK_PREC_MIXED,
-                            rng_stream=2)
+                            rng_stream=2, noise=noise)
 
     # the ordinary path: the library allocates
     with gfk.Context([desc], trials=[(kind, params)], launch=(256, 2)) as ctx:
