@@ -60,9 +60,14 @@ SEED = 0
 OPS_PER_WALKER_STEP = {(0, 0): 290, (0, 1): 405, (1, 0): 146, (1, 1): 261}
 # Lanes that can issue an ALU instruction per SM per clock (4 schedulers x 32).
 LANES_PER_SM_CLK = 128
-# DRAM traffic of the walk kernel per launch from an ncu capture, valid only for
-# the kernel sources it was taken on (sha256 prefix of csrc/*); None otherwise.
-WALK_TRAFFIC = {"src_sha": None, "bytes_per_launch": None}
+# DRAM traffic (read + write) of the walk kernel per walker-step, from one ncu
+# capture of a launch of the bench's shape (2^20 walkers x 1024 moves, the
+# launch shape the bench uses), valid only for the kernel sources it was taken
+# on (sha256 prefix of csrc/*); scaled by the walker-steps of an average launch.
+WALK_TRAFFIC = {       # workload -> capture
+    "ground": {"src_sha": "5898b30ed7f6bf3a", "bytes_per_walker_step": 0.19997},
+    "bernoulli": {"src_sha": "5898b30ed7f6bf3a", "bytes_per_walker_step": 0.11120},
+}
 
 
 def _src_sha() -> str:
@@ -372,8 +377,9 @@ def run_ours(args):
                   for d in insts) / n_walkers
         achieved = ops * ws_per_launch / (avg_launch_ms / 1e3) / 1e9
         traffic = None
-        if WALK_TRAFFIC["src_sha"] == _src_sha() and WALK_TRAFFIC["bytes_per_launch"]:
-            traffic = WALK_TRAFFIC["bytes_per_launch"]
+        tr = WALK_TRAFFIC.get(args.workload)
+        if tr and tr["src_sha"] == _src_sha():
+            traffic = tr["bytes_per_walker_step"] * ws_per_launch
         launches_per_step = 2 * walk_launches / args.steps + 2
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -443,21 +449,26 @@ def run_ours(args):
 
 
 def profile_case(args):
-    """A small case for ncu captures: 2^22 walkers (state 128 MB, > L2) advanced 64
-    moves per launch on the mixed path (or the FP64 path with --prec 0)."""
+    """A small case for ncu captures: the ground-state trial, two launches of
+    --profile-moves moves each (default 64) on --profile-walkers walkers (default
+    2^22 mixed, 2^20 FP64; the state is larger than L2 either way), mixed path (or
+    FP64 with --prec 0), Gaussian or Bernoulli noise (--noise)."""
     import torch
     from paper_1703_08977_gb300 import gfk
     kind, params = 0, [2.0, 0.5, 0.5]
-    n = 1 << 22 if args.prec == 1 else 1 << 20
-    d = gfk.InstanceDesc(n_walkers=n, dt=0.005, e_trial=-2.9037, seed=SEED, prec=args.prec)
+    n = args.profile_walkers or (1 << 22 if args.prec == 1 else 1 << 20)
+    dt = 1.0 / 900.0 if args.noise == 1 else 0.005
+    d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=-2.9037, seed=SEED, prec=args.prec,
+                         noise=args.noise)
     launch = (args.threads or 128, args.wpt or 2) if args.prec == 1 else (128, 1)
+    m = args.profile_moves
     with gfk.Context([d], trials=[(kind, params)], launch=launch) as ctx:
-        ctx.propagate(64)
-        ctx.propagate(64)
+        ctx.propagate(m)
+        ctx.propagate(m)
         torch.cuda.synchronize()
         e = ctx.energy(0)["E"]
-    print(json.dumps({"profile_case": True, "walkers": n, "moves": 128, "prec": args.prec,
-                      "E_final": float(e[-1])}))
+    print(json.dumps({"profile_case": True, "walkers": n, "moves": 2 * m, "prec": args.prec,
+                      "noise": args.noise, "launch": launch, "E_final": float(e[-1])}))
 
 
 def main():
@@ -474,6 +485,9 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small ncu capture case instead of the benchmark")
     ap.add_argument("--prec", type=int, default=1, help="profile case: 1 mixed, 0 FP64")
+    ap.add_argument("--noise", type=int, default=0, help="profile case: 0 Gaussian, 1 Bernoulli")
+    ap.add_argument("--profile-walkers", type=int, default=0)
+    ap.add_argument("--profile-moves", type=int, default=64)
     ap.add_argument("--adam", action="store_true", help="adjoint workload: run 50 Adam steps")
     args = ap.parse_args()
     if args.profile_case:
