@@ -54,6 +54,7 @@ struct gfk_ctx {
     struct GraphEntry {
         int64_t step0, n_steps, nblk;
         int init, threads, wpt;
+        uint64_t trial_hash;            // single-instance walks take the trial as an argument
         const void* series;
         const void* part;
         cudaGraphExec_t exec;
@@ -153,6 +154,12 @@ struct DeviceGuard {
 };
 
 bool finite_d(double v) { return std::isfinite(v); }
+
+// The trial function of a single-instance context (the walk kernels then take it
+// as a launch argument), or NULL when the context holds several instances.
+const TrialHost* one_trial(const gfk_ctx* ctx) {
+    return ctx->n_inst == 1 ? &ctx->trial[0] : nullptr;
+}
 
 gfk_status parse_trial(int kind, const double* p, int np, TrialHost* t) {
     std::memset(t, 0, sizeof(*t));
@@ -344,7 +351,7 @@ gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t
         } else {
             GFK_CK(ctx, launch_walk_mixed(kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
                                           ctx->d_inst, bm, ctx->smx, step0, chunk, ctx->part, ctx->counters,
-                                          ctx->stream));
+                                          one_trial(ctx), ctx->desc[0].ee_on, ctx->stream));
         }
         if (ev1) {
             GFK_CK(ctx, cudaEventRecord(ev1, ctx->stream));
@@ -616,10 +623,11 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
         GFK_CK(ctx, cudaEventRecord(ctx->graph_fork, user));
         GFK_CK(ctx, cudaStreamWaitEvent(ctx->graph_stream, ctx->graph_fork, 0));
         gfk_ctx::GraphEntry* hit = nullptr;
+        const uint64_t th = fnv1a(ctx->trial.data(), sizeof(TrialHost) * ctx->trial.size());
         for (auto& e : ctx->graphs)
             if (e.step0 == step_begin && e.n_steps == n_steps && e.nblk == nblk &&
                 e.init == (init ? 1 : 0) && e.threads == ctx->threads && e.wpt == ctx->wpt &&
-                e.series == ctx->series && e.part == ctx->part) {
+                e.trial_hash == th && e.series == ctx->series && e.part == ctx->part) {
                 hit = &e;
                 break;
             }
@@ -646,7 +654,7 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
                 ctx->graphs.erase(ctx->graphs.begin());
             }
             ctx->graphs.push_back({step_begin, n_steps, nblk, init ? 1 : 0, ctx->threads, ctx->wpt,
-                                   ctx->series, ctx->part, exec});
+                                   th, ctx->series, ctx->part, exec});
             hit = &ctx->graphs.back();
         }
         GFK_CK(ctx, cudaGraphLaunch(hit->exec, ctx->graph_stream));
@@ -746,7 +754,8 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
                 else
                     e = launch_walk_mixed(kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
                                           ctx->d_inst, bm, ctx->smx, (uint32_t)ctx->steps, chunk, ctx->part,
-                                          ctx->counters, ctx->stream);
+                                          ctx->counters, one_trial(ctx), ctx->desc[0].ee_on,
+                                          ctx->stream);
                 if (e == cudaSuccess)
                     e = launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
                                            ctx->series_cap, ctx->steps + 1, ctx->stream);
@@ -1068,8 +1077,8 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
             e = f64 ? launch_walk_fp64(kind, ctx->noise, shape.threads, (int)nblk, d_inst, bm, s64,
                                        (uint32_t)(j * K), steps, part, cnt, ctx->stream)
                     : launch_walk_mixed(kind, ctx->noise, shape.wpt, shape.threads, (int)nblk,
-                                        d_inst, bm, smx,
-                                        (uint32_t)(j * K), steps, part, cnt, ctx->stream);
+                                        d_inst, bm, smx, (uint32_t)(j * K), steps, part, cnt,
+                                        &ctx->trial[inst], ctx->desc[inst].ee_on, ctx->stream);
     }
     double* logw_final = (double*)(base + o_logw);
     if (e == cudaSuccess) {

@@ -301,7 +301,7 @@ struct TrialDev {
 };
 
 template <typename R>
-__device__ __forceinline__ void load_trial(const TrialHost& h, int ee_on, TrialDev<R>& t) {
+__host__ __device__ __forceinline__ void load_trial(const TrialHost& h, int ee_on, TrialDev<R>& t) {
     t.kind = h.kind;
     t.nterms = h.nterms;
     t.poly = (h.ck[0] != 0.0 || h.ck[1] != 0.0 || h.ck[2] != 0.0 || h.ck[3] != 0.0) ? 1 : 0;
@@ -426,7 +426,56 @@ __device__ __forceinline__ void eval_kind0(const TD& t, const R x[6], EvalOut<R>
 //   E_L = T / Phi - u' (grad_1 Phi - grad_2 Phi) . e12 / Phi - u'' - u'^2
 //         + (ee - 2u')/r12,
 //   T = sum_t s_t [K_A p_B + p_A K_B] g_A g_B.
+// One term s_t f_A f_B of the orbital-pair trial function: its contribution
+// to Phi, to the kinetic sum T and to the gradients G1, G2 (see eval_kind1).
 template <typename R>
+struct Kind1Acc {
+    R Phi = R(0), T = R(0);
+    R G1[3] = {R(0), R(0), R(0)}, G2[3] = {R(0), R(0), R(0)};
+};
+
+template <typename R>
+__device__ __forceinline__ void kind1_term(const TrialDev<R>& t, int k, R r1, R r2, const R rr[2],
+                                           const R ir[2], const R zz[2], const R h1[3],
+                                           const R h2[3], R emax, Kind1Acc<R>& acc) {
+    constexpr bool kF64 = sizeof(R) == 8;
+    R gA = R(1), gB = R(1), g;
+    if (kF64) {
+        gA = expn(-t.al[k][0] * r1);
+        gB = expn(-t.al[k][1] * r2);
+        g = gA * gB;
+    } else {
+        g = expn(-(t.al[k][0] * r1 + t.al[k][1] * r2) - emax);
+    }
+    R p[2], K[2], gr[2][3];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const R* hh = e == 0 ? h1 : h2;
+        R al = t.al[k][e], c1 = t.c1[k][e], cz = t.cz[k][e];
+        R pe = t.c0[k][e] + c1 * rr[e] + cz * zz[e];
+        R radial = c1 - al * pe;                      // coefficient of r_hat
+        gr[e][0] = radial * hh[0];
+        gr[e][1] = radial * hh[1];
+        gr[e][2] = radial * hh[2] + cz;
+        K[e] = -c1 * ir[e] + al * (c1 + cz * zz[e] * ir[e]) - t.hal2[k][e] * pe +
+               t.km2[k][e] * pe * ir[e];
+        p[e] = pe;
+    }
+    R sg = t.s[k] * g;
+    if (kF64) acc.Phi += t.s[k] * (p[0] * gA) * (p[1] * gB);
+    else acc.Phi += sg * p[0] * p[1];
+    acc.T += sg * (K[0] * p[1] + p[0] * K[1]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        acc.G1[d] += sg * gr[0][d] * p[1];
+        acc.G2[d] += sg * p[0] * gr[1][d];
+    }
+}
+
+// UNROLL: the term loops run to GFK_MAX_TERMS with a uniform early exit, so
+// every parameter index is a compile-time constant (for a trial held in the
+// kernel's parameter bank); otherwise they run to t.nterms (fewer registers).
+template <typename R, bool UNROLL = false>
 __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
     R s1 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
@@ -451,45 +500,32 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
     R emax = R(0);
     if (!kF64) {
         emax = -(t.al[0][0] * r1 + t.al[0][1] * r2);
-        for (int k = 1; k < t.nterms; ++k)
-            emax = fmax(emax, -(t.al[k][0] * r1 + t.al[k][1] * r2));
+        if constexpr (UNROLL) {
+#pragma unroll
+            for (int k = 1; k < GFK_MAX_TERMS; ++k) {
+                if (k >= t.nterms) break;
+                emax = fmax(emax, -(t.al[k][0] * r1 + t.al[k][1] * r2));
+            }
+        } else {
+            for (int k = 1; k < t.nterms; ++k)
+                emax = fmax(emax, -(t.al[k][0] * r1 + t.al[k][1] * r2));
+        }
     }
 
-    R Phi = R(0), T = R(0);
-    R G1[3] = {R(0), R(0), R(0)}, G2[3] = {R(0), R(0), R(0)};
-    for (int k = 0; k < t.nterms; ++k) {
-        R gA = R(1), gB = R(1), g;
-        if (kF64) {
-            gA = expn(-t.al[k][0] * r1);
-            gB = expn(-t.al[k][1] * r2);
-            g = gA * gB;
-        } else {
-            g = expn(-(t.al[k][0] * r1 + t.al[k][1] * r2) - emax);
-        }
-        R p[2], K[2], gr[2][3];
+    Kind1Acc<R> acc;
+    if constexpr (UNROLL) {
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const R* hh = e == 0 ? h1 : h2;
-            R al = t.al[k][e], c1 = t.c1[k][e], cz = t.cz[k][e];
-            R pe = t.c0[k][e] + c1 * rr[e] + cz * zz[e];
-            R radial = c1 - al * pe;                      // coefficient of r_hat
-            gr[e][0] = radial * hh[0];
-            gr[e][1] = radial * hh[1];
-            gr[e][2] = radial * hh[2] + cz;
-            K[e] = -c1 * ir[e] + al * (c1 + cz * zz[e] * ir[e]) - t.hal2[k][e] * pe +
-                   t.km2[k][e] * pe * ir[e];
-            p[e] = pe;
+        for (int k = 0; k < GFK_MAX_TERMS; ++k) {
+            if (k >= t.nterms) break;
+            kind1_term<R>(t, k, r1, r2, rr, ir, zz, h1, h2, emax, acc);
         }
-        R sg = t.s[k] * g;
-        if (kF64) Phi += t.s[k] * (p[0] * gA) * (p[1] * gB);
-        else Phi += sg * p[0] * p[1];
-        T += sg * (K[0] * p[1] + p[0] * K[1]);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            G1[d] += sg * gr[0][d] * p[1];
-            G2[d] += sg * p[0] * gr[1][d];
-        }
+    } else {
+        for (int k = 0; k < t.nterms; ++k)
+            kind1_term<R>(t, k, r1, r2, rr, ir, zz, h1, h2, emax, acc);
     }
+    const R Phi = acc.Phi, T = acc.T;
+    const R* G1 = acc.G1;
+    const R* G2 = acc.G2;
     JastrowOut<R> j = jastrow<R>(t, r12, i12);
     R iP = rcp(Phi);
     o.b[0] = G1[0] * iP + j.up * ex;
@@ -506,10 +542,10 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
 
 // KIND 0 / 1 select the family at compile time; KIND 2 dispatches on t.kind
 // (used when one launch covers instances of both families).
-template <int KIND, typename R>
+template <int KIND, typename R, bool UNROLL = false>
 __device__ __forceinline__ void eval_trial(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
     if (KIND == 0) eval_kind0<R>(t, x, o);
-    else if (KIND == 1) eval_kind1<R>(t, x, o);
+    else if (KIND == 1) eval_kind1<R, UNROLL>(t, x, o);
     else if (t.kind == 0) eval_kind0<R>(t, x, o);
     else eval_kind1<R>(t, x, o);
 }

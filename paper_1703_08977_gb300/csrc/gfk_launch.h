@@ -18,10 +18,13 @@ cudaError_t launch_walk_fp64(int kind, int noise, int threads, int nblk, const I
 cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
                               const BlockMap& bm, const StateMixed& st, PartialRec* part,
                               unsigned long long* counters, cudaStream_t stream);
+// one_trial: when the launch covers a single instance, its trial function (and
+// ee_on); the kernel then takes it as a launch argument.  NULL otherwise.
 cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk,
                               const InstDev* insts, const BlockMap& bm, const StateMixed& st,
                               uint32_t step0, int nsteps, PartialRec* part,
-                              unsigned long long* counters, cudaStream_t stream);
+                              unsigned long long* counters, const TrialHost* one_trial,
+                              int ee_on, cudaStream_t stream);
 cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
                                SeriesRow* series, int64_t series_cap, int64_t row_base,
                                cudaStream_t stream);
