@@ -299,6 +299,16 @@ typedef enum {
 } gfk_peak_op;
 gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* lane_ops_per_s);
 
+/* Exhaustive check of the FP32 Box-Muller radius (the Gaussian noise of the
+ * GFK_PREC_MIXED walk): the mean, over all 2^32 radius words w, of
+ * r2(w) - (-2 ln((w + 1/2) 2^-32)), the second term in FP64.  The normals'
+ * variance is E[r2]/2, so mean/2 is the relative error of the walk's
+ * diffusion constant.  method 0: the kernels' r2 (hardware log2 plus its
+ * mean-error correction); 1: the hardware log2 alone; 2: the library logf.
+ * Runs on the current device and stream `cuda_stream`; synchronises it.
+ * GFK_EINVAL for a bad method or a NULL output. */
+gfk_status gfk_radius_mean_error(int32_t method, void* cuda_stream, double* mean_error);
+
 /* Forget the population: the next gfk_propagate re-initialises it (step 0). */
 gfk_status gfk_reset(gfk_ctx* ctx);
 

@@ -179,22 +179,38 @@ __device__ __forceinline__ void philox10_pair(const PhiloxPre& p, uint32_t m, ui
 // u_b - 1/2 = ((1 + k 2^-23) - 3/2) + 2^-24 with k = w >> 9, built exactly
 // from the bit pattern 0x3F800000 | k (= 1 + k 2^-23); an equally spaced grid
 // of angles keeps cos^2 and sin^2 at mean 1/2 exactly.  The radius takes the
-// library logarithm (about 1 ulp): the hardware log2's error does not average
-// to zero over u, and a mean relative error of 2e-8 in -ln u is a 2e-8 error
-// in the diffusion constant, measured as a 6e-8 hartree shift of E.  Then the
-// hardware square root, sine and cosine; the angle is taken as
+// hardware log2 with its mean error over the 2^32 words removed (radius2_f32
+// below).  Then the hardware square root, sine and cosine; the angle is taken as
 // 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine are most
 // accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
-__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6]) {
+// The squared Box-Muller radius -2 ln u_a of the FP32 path from its word w,
+// u_a = fl(fl(w) 2^-32 + 2^-33).  The logarithm is the hardware base-2 one
+// (a single MUFU operation) scaled by -2 ln 2.  Its error is a deterministic
+// function of w, and what the walk is sensitive to is its mean over the 2^32
+// words: the normals' variance -- the diffusion constant -- is E[-2 ln u]/2.
+// Measured exhaustively on sm_103a against -2 ln((w + 1/2) 2^-32) in FP64,
+// that mean error is -1.6307e-7 (a variance 8.2e-8 too small, which moved the
+// mixed-path energy by ~6e-8 hartree); kRadius2MeanFix adds it back inside the
+// same multiply-add.  gfk_radius_mean_error re-measures the corrected mean.
+constexpr float kRadius2MeanFix = 1.630718e-7f;
+
+__device__ __forceinline__ float radius2_f32(uint32_t w) {
     constexpr float kInv32 = 1.0f / 4294967296.0f;                        // 2^-32
     constexpr float kHalfInv32 = 0.5f / 4294967296.0f;                    // 2^-33
+    constexpr float kMinus2Ln2 = -1.3862943611198906f;
+    const float ua = fmaf((float)w, kInv32, kHalfInv32);
+    float l2;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(ua));
+    return fmaxf(fmaf(kMinus2Ln2, l2, kRadius2MeanFix), 0.0f);           // -2 ln u >= 0
+}
+
+__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6]) {
     constexpr float kHalfUlp = 1.0f / 16777216.0f;                        // 2^-24
     constexpr float kTwoPi = 6.2831853071795865f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float ua = fmaf((float)w[2 * j], kInv32, kHalfInv32);
         const float ubc = (__int_as_float(0x3F800000 | (w[2 * j + 1] >> 9)) - 1.5f) + kHalfUlp;
-        const float r2 = fmaxf(-2.0f * logf(ua), 0.0f);                    // -2 ln u >= 0
+        const float r2 = radius2_f32(w[2 * j]);
         float rho;
         asm("sqrt.approx.f32 %0, %1;" : "=f"(rho) : "f"(r2));
         float s, c;

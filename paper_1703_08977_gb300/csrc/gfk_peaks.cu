@@ -10,6 +10,7 @@
 
 #include <cstdint>
 
+#include "gfk_device.cuh"
 #include "gfk_types.h"
 
 namespace {
@@ -126,5 +127,76 @@ extern "C" gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* la
     if (e != cudaSuccess) return GFK_ECUDA;
     const double ops = (double)blocks * kThreads * kChains * kIters * (op == GFK_PEAK_F2F ? 2 : 1);
     *lane_ops_per_s = ops / (ms * 1e-3);
+    return GFK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gfk_radius_mean_error: the FP32 Box-Muller radius against FP64, summed over
+// every radius word.  One FP64 partial per thread, one atomic add per block.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ float radius2_variant(uint32_t w, int method) {
+    constexpr float kInv32 = 1.0f / 4294967296.0f;
+    constexpr float kHalfInv32 = 0.5f / 4294967296.0f;
+    const float ua = fmaf((float)w, kInv32, kHalfInv32);
+    if (method == 0) return gfk::radius2_f32(w);
+    if (method == 1) {
+        float l2;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(ua));
+        return fmaxf(-1.3862943611198906f * l2, 0.0f);
+    }
+    return fmaxf(-2.0f * logf(ua), 0.0f);
+}
+
+__global__ void radius_error_kernel(int method, double* __restrict__ out) {
+    __shared__ double s_part[8];
+    const uint64_t n = 1ull << 32;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    double acc = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t w = (uint32_t)i;
+        const double exact = -2.0 * log(((double)w + 0.5) * (1.0 / 4294967296.0));
+        acc += (double)radius2_variant(w, method) - exact;
+    }
+    acc = gfk::warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b += s_part[k];
+        atomicAdd(out, b);
+    }
+}
+
+}  // namespace
+
+extern "C" gfk_status gfk_radius_mean_error(int32_t method, void* cuda_stream,
+                                            double* mean_error) {
+    if (!mean_error || method < 0 || method > 2) return GFK_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GFK_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GFK_ECUDA;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    double* d = nullptr;
+    if (cudaMalloc(&d, sizeof(double)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GFK_ENOMEM;
+    }
+    double h = 0.0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double), stream);
+    if (e == cudaSuccess) {
+        radius_error_kernel<<<sms * 8, 256, 0, stream>>>(method, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GFK_ECUDA;
+    }
+    *mean_error = h / 4294967296.0;
     return GFK_OK;
 }

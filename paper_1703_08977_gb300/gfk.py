@@ -32,7 +32,8 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_energy", "gfk_sums", "gfk_get_walkers", "gfk_counters", "gfk_checkpoint_size",
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
            "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc",
-           "gfk_measure_peak", "gfk_set_graph", "gfk_autotune", "gfk_grad")
+           "gfk_measure_peak", "gfk_set_graph", "gfk_autotune", "gfk_grad",
+           "gfk_radius_mean_error")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
             "i2f", "f2f")
 GFK_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -99,6 +100,7 @@ def load(build_if_needed: bool = True):
             "gfk_status_string": ([c.c_int], c.c_char_p),
             "gfk_last_error": ([P], c.c_char_p),
             "gfk_measure_peak": ([c.c_int32, P, dp], c.c_int),
+            "gfk_radius_mean_error": ([c.c_int32, P, dp], c.c_int),
             "gfk_set_graph": ([P, c.c_int32], c.c_int),
             "gfk_grad": ([P, c.c_int32, c.c_int32, c.c_int64, c.c_int32, dp, c.c_int32, dp],
                          c.c_int),
@@ -335,6 +337,21 @@ def gfk_measure_peak(op, stream=None) -> float:
         stream = _current_stream_ptr()
     v = ctypes.c_double()
     _check(load().gfk_measure_peak(int(op), stream, ctypes.byref(v)), "gfk_measure_peak")
+    return v.value
+
+
+RADIUS_METHODS = ("kernel", "hw_log2", "logf")
+
+
+def gfk_radius_mean_error(method="kernel", stream=None) -> float:
+    """Mean over all 2^32 radius words of the FP32 Box-Muller r2 minus -2 ln u in FP64."""
+    if isinstance(method, str):
+        method = RADIUS_METHODS.index(method)
+    if stream is None:
+        stream = _current_stream_ptr()
+    v = ctypes.c_double()
+    _check(load().gfk_radius_mean_error(int(method), stream, ctypes.byref(v)),
+           "gfk_radius_mean_error")
     return v.value
 
 

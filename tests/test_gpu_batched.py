@@ -41,6 +41,34 @@ def test_graph_replay_matches_direct_launches(gfk_lib, prec):
     b.close()
 
 
+@pytest.mark.parametrize("kind,p1,p2", [
+    (1, wl.triplet_2s3(), wl.fn3()),
+    (0, wl.ground(), wl.ground(Z=1.85, a=0.5, beta=0.37, c=(0.11, -0.07, 0.05, 0.02)))])
+def test_graph_replay_follows_a_new_trial_function(gfk_lib, kind, p1, p2):
+    """A single-instance walk takes its trial function as a launch argument, which a
+    captured graph holds: after a reset and gfk_set_trial with other parameters, the
+    replay must walk the new trial (bitwise equal to direct launches with it)."""
+    gfk = gfk_lib
+    d = gfk.InstanceDesc(n_walkers=3000, dt=0.01, e_trial=-2.5, seed=4, prec=1)
+    g = gfk.Context([d], trials=[(kind, p1)])
+    g.set_graph(True)
+    g.propagate(96)
+    g.reset()
+    g.set_trial(0, kind, p2)
+    g.propagate(96)
+    ref = gfk.Context([d], trials=[(kind, p2)]).propagate(96)
+    for u, v in zip(ref.walkers(0), g.walkers(0)):
+        np.testing.assert_array_equal(u, v)
+    np.testing.assert_array_equal(ref.sums(0), g.sums(0))
+    g.reset()
+    g.set_trial(0, kind, p1)
+    g.propagate(96)                 # back to the first trial's cached graph
+    first = gfk.Context([d], trials=[(kind, p1)]).propagate(96)
+    np.testing.assert_array_equal(first.sums(0), g.sums(0))
+    for c in (g, ref, first):
+        c.close()
+
+
 def test_batched_mixed_instances_match_single(gfk_lib):
     """The twelve-instance mix in one context (mixed path, one launch per chunk with the
     trial family dispatched per block) reproduces each instance run alone, walker by

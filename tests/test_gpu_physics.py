@@ -31,3 +31,18 @@ def test_triplet_energy_extrapolates_to_exact(gfk_lib):
     from paper_1703_08977_gb300 import experiments as ex
     r = ex.dt_study(1, [0.005, 0.0025, 0.00125], 60.0, 1 << 16, 16)
     assert abs(r["E_dt0"] - ex.EXACT[1]) < 4 * r["E_dt0_err"] + 1e-4, r
+
+
+def test_fp32_box_muller_radius_mean_is_exact(gfk_lib):
+    """Exhaustive over the 2^32 radius words: the mixed path's squared radius r2 has a
+    mean error below 5e-9 against -2 ln((w + 1/2) 2^-32) in FP64, so the normals'
+    variance (the diffusion constant, E[r2]/2) is right to 2.5e-9 relative.  The
+    uncorrected hardware log2 is short by the constant the kernels add back, and the
+    library logarithm is shown beside it."""
+    gfk = gfk_lib
+    m_kernel = gfk.gfk_radius_mean_error("kernel")
+    m_hw = gfk.gfk_radius_mean_error("hw_log2")
+    m_lib = gfk.gfk_radius_mean_error("logf")
+    assert abs(m_kernel) < 5e-9, m_kernel
+    assert abs(m_hw + 1.630718e-7) < 2e-9, m_hw
+    assert abs(m_lib) < 2e-8, m_lib
