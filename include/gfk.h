@@ -299,15 +299,20 @@ typedef enum {
 } gfk_peak_op;
 gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* lane_ops_per_s);
 
-/* Exhaustive check of the FP32 Box-Muller radius (the Gaussian noise of the
- * GFK_PREC_MIXED walk): the mean, over all 2^32 radius words w, of
- * r2(w) - (-2 ln((w + 1/2) 2^-32)), the second term in FP64.  The normals'
- * variance is E[r2]/2, so mean/2 is the relative error of the walk's
- * diffusion constant.  method 0: the kernels' r2 (hardware log2 plus its
- * mean-error correction); 1: the hardware log2 alone; 2: the library logf.
- * Runs on the current device and stream `cuda_stream`; synchronises it.
- * GFK_EINVAL for a bad method or a NULL output. */
-gfk_status gfk_radius_mean_error(int32_t method, void* cuda_stream, double* mean_error);
+/* Exhaustive moments of the FP32 Box-Muller normals of the GFK_PREC_MIXED walk
+ * (Gaussian noise), against FP64.  Over all 2^32 radius words w, with
+ * r2(w) the squared radius and rho = sqrt(r2) as the kernels compute them and
+ * R2(w) = -2 ln((w + 1/2) 2^-32) in FP64:
+ *   moments[0] = mean of r2 - R2,   moments[1] = mean of rho^2 - R2;
+ * over all 2^23 angles of the grid, with c, s the kernels' cosine and sine:
+ *   moments[2] = mean c^2 - 1/2,    moments[3] = mean s^2 - 1/2,
+ *   moments[4] = mean c,            moments[5] = mean s.
+ * The normals' variances are (2 + moments[1]) (1/2 + moments[2]) and
+ * (2 + moments[1]) (1/2 + moments[3]).  method selects r2: 0 the kernels'
+ * (hardware log2 plus its mean-error correction), 1 the hardware log2 alone,
+ * 2 the library logf.  Runs on the current device and on `cuda_stream`, which
+ * it synchronises.  GFK_EINVAL for a bad method or a NULL output. */
+gfk_status gfk_normal_moments(int32_t method, void* cuda_stream, double* moments);
 
 /* Forget the population: the next gfk_propagate re-initialises it (step 0). */
 gfk_status gfk_reset(gfk_ctx* ctx);

@@ -71,18 +71,40 @@ template <> struct PosIO<float> {
 
 // The forward move of the precision, written exactly as the walk kernel of
 // that precision writes it (so the recomputed positions are the forward's).
+// FP64: X + b dt + sdt xi for both noise modes (xi = +-1 for Bernoulli).
+// FP32: the mixed kernel's helpers; for Bernoulli xi already holds +-sdt.
 __device__ __forceinline__ void adj_move(double x[6], const double b[6], const double xi[6],
-                                         double dt, double sdt) {
+                                         double dt, double sdt, bool) {
 #pragma unroll
     for (int d = 0; d < 6; ++d) x[d] = x[d] + b[d] * dt + sdt * xi[d];
 }
 __device__ __forceinline__ void adj_move(float x[6], const float b[6], const float xi[6],
-                                         float dt, float sdt) {
+                                         float dt, float sdt, bool bern) {
 #pragma unroll
-    for (int d = 0; d < 6; ++d) x[d] = fmaf(sdt, xi[d], fmaf(b[d], dt, x[d]));
+    for (int d = 0; d < 6; ++d)
+        x[d] = bern ? move_bern_f32(x[d], b[d], xi[d], dt) : move_gauss_f32(x[d], b[d], xi[d], dt, sdt);
 }
-__device__ __forceinline__ void adj_normals(const uint32_t w[6], double xi[6]) { normals6_f64(w, xi); }
-__device__ __forceinline__ void adj_normals(const uint32_t w[6], float xi[6]) { normals6_f32(w, xi); }
+__device__ __forceinline__ void adj_normals(const uint32_t w[6], double xi[6], const InstDev*) {
+    normals6_f64(w, xi);
+}
+__device__ __forceinline__ void adj_normals(const uint32_t w[6], float xi[6], const InstDev* inst) {
+    normals6_f32(w, xi, inst->r2_fix);
+}
+__device__ __forceinline__ void adj_bernoulli(uint32_t& s, double, double xi[6]) {
+    bernoulli6<double>(s, xi);
+}
+__device__ __forceinline__ void adj_bernoulli(uint32_t& s, float sdt, float xi[6]) {
+    bernoulli6_steps(s, sdt, xi);
+}
+// The time step and noise scale the forward walk of the precision uses.
+__device__ __forceinline__ void adj_steps(const InstDev* inst, double& dt, double& sdt) {
+    dt = inst->dt;
+    sdt = inst->sqrt_dt;
+}
+__device__ __forceinline__ void adj_steps(const InstDev* inst, float& dt, float& sdt) {
+    dt = inst->dt_f32;
+    sdt = inst->sdt_f32;
+}
 
 template <typename T>
 __device__ __forceinline__ void load_trial0_dual(const TrialHost& h, int ee_on,
@@ -216,7 +238,9 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
     TrialDev0<D> td;
     load_trial0_dual<T>(inst->trial, inst->ee_on, td);
     const TrialDev<T>& tp = s_trial;
-    const T dt = (T)inst->dt, sdt = (T)inst->sqrt_dt;
+    T dt, sdt;
+    adj_steps(inst, dt, sdt);
+    const bool bern = inst->noise == GFK_NOISE_BERNOULLI;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double theta[kNumTheta];
 #pragma unroll
@@ -253,14 +277,14 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                     eval_kind0<T>(tp, x, ev);
                     T xi[6];
                     if (inst->noise == GFK_NOISE_BERNOULLI) {
-                        bernoulli6<T>(lcg, xi);
+                        adj_bernoulli(lcg, sdt, xi);
                     } else {
                         uint32_t words[6];
                         move_words(inst->id0 + (uint32_t)i, (uint32_t)m, inst->stream, inst->k0,
                                    inst->k1, words);
-                        adj_normals(words, xi);
+                        adj_normals(words, xi, inst);
                     }
-                    adj_move(x, ev.b, xi, dt, sdt);
+                    adj_move(x, ev.b, xi, dt, sdt, bern);
                     PosIO<T>::store(seg + (int64_t)(m - n_lo + 1) * PosIO<T>::kWords * n, n, i, x);
                 }
                 // sweep it backwards

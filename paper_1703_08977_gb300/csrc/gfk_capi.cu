@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "gfk_launch.h"
+#include "gfk_mixed_consts.h"
 #include "gfk_types.h"
 
 
@@ -244,6 +245,13 @@ gfk_status upload_instances(gfk_ctx* ctx) {
         v.id0 = d.walker_id0;
         v.ee_on = d.ee_on ? 1 : 0;
         v.noise = d.noise;
+        const MixedConsts mc = mixed_consts(d.dt, d.e_trial, d.noise);
+        v.dt_f32 = mc.dt;
+        v.sdt_f32 = mc.sdt;
+        v.r2_fix = mc.r2_fix;
+        v.et_f32 = mc.et;
+        v.dt_log2e = mc.dt_log2e;
+        v.et_fix = mc.et_fix;
         v.trial = ctx->trial[i];
     }
     GFK_CK(ctx, cudaMemcpyAsync(ctx->d_inst, h.data(), sizeof(InstDev) * ctx->n_inst,

@@ -185,36 +185,43 @@ __device__ __forceinline__ void philox10_pair(const PhiloxPre& p, uint32_t m, ui
 // accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
 // The squared Box-Muller radius -2 ln u_a of the FP32 path from its word w,
 // u_a = fl(fl(w) 2^-32 + 2^-33).  The logarithm is the hardware base-2 one
-// (a single MUFU operation) scaled by -2 ln 2.  Its error is a deterministic
-// function of w, and what the walk is sensitive to is its mean over the 2^32
-// words: the normals' variance -- the diffusion constant -- is E[-2 ln u]/2.
-// Measured exhaustively on sm_103a against -2 ln((w + 1/2) 2^-32) in FP64,
-// that mean error is -1.6307e-7 (a variance 8.2e-8 too small, which moved the
-// mixed-path energy by ~6e-8 hartree); kRadius2MeanFix adds it back inside the
-// same multiply-add.  gfk_radius_mean_error re-measures the corrected mean.
-constexpr float kRadius2MeanFix = 1.630718e-7f;
-
-__device__ __forceinline__ float radius2_f32(uint32_t w) {
+// (a single MUFU operation) scaled by -2 ln 2, plus r2_fix.  The walk sees the
+// radius only through the normals' variance, and r2_fix (set per instance on
+// the host, gfk_mixed_consts.h) cancels the mean errors of this logarithm, of
+// the hardware square root and of the hardware cosine and sine, measured
+// exhaustively over all radius words and angles, and matches the variance to
+// the drift's FP32 time step.
+__device__ __forceinline__ float radius2_f32(uint32_t w, float r2_fix) {
     constexpr float kInv32 = 1.0f / 4294967296.0f;                        // 2^-32
     constexpr float kHalfInv32 = 0.5f / 4294967296.0f;                    // 2^-33
     constexpr float kMinus2Ln2 = -1.3862943611198906f;
     const float ua = fmaf((float)w, kInv32, kHalfInv32);
     float l2;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(ua));
-    return fmaxf(fmaf(kMinus2Ln2, l2, kRadius2MeanFix), 0.0f);           // -2 ln u >= 0
+    return fmaxf(fmaf(kMinus2Ln2, l2, r2_fix), 0.0f);                    // -2 ln u >= 0
 }
 
-__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6]) {
+// The Box-Muller radius from its square (hardware square root; 0 gives 0).
+__device__ __forceinline__ float radius_f32(float r2) {
+    float rho;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(rho) : "f"(r2));
+    return rho;
+}
+
+// Cosine and sine of the angle 2 pi (u_b - 1/2) from its word (23-bit grid).
+__device__ __forceinline__ void angle_f32(uint32_t w, float& s, float& c) {
     constexpr float kHalfUlp = 1.0f / 16777216.0f;                        // 2^-24
     constexpr float kTwoPi = 6.2831853071795865f;
+    const float ubc = (__int_as_float(0x3F800000 | (w >> 9)) - 1.5f) + kHalfUlp;
+    __sincosf(kTwoPi * ubc, &s, &c);
+}
+
+__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6], float r2_fix) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float ubc = (__int_as_float(0x3F800000 | (w[2 * j + 1] >> 9)) - 1.5f) + kHalfUlp;
-        const float r2 = radius2_f32(w[2 * j]);
-        float rho;
-        asm("sqrt.approx.f32 %0, %1;" : "=f"(rho) : "f"(r2));
+        const float rho = radius_f32(radius2_f32(w[2 * j], r2_fix));
         float s, c;
-        __sincosf(kTwoPi * ubc, &s, &c);
+        angle_f32(w[2 * j + 1], s, c);
         xi[2 * j] = -rho * c;
         xi[2 * j + 1] = -rho * s;
     }
@@ -272,6 +279,29 @@ __device__ __forceinline__ void bernoulli6(uint32_t& s, R eps[6]) {
         s = superduper_next(s);
         eps[d] = s > 0x80000000u ? R(1) : R(-1);
     }
+}
+
+// The same six increments already scaled: +-sdt.
+__device__ __forceinline__ void bernoulli6_steps(uint32_t& s, float sdt, float step[6]) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        s = superduper_next(s);
+        step[d] = s > 0x80000000u ? sdt : -sdt;
+    }
+}
+
+// The FP32 move of the mixed path (the forward walk and the adjoint's segment
+// recompute both use these, so their positions agree bit for bit).
+// Gaussian: X + b dt + sdt xi with one rounding per multiply-add.
+// Bernoulli: X + (b dt +- sdt).  The step is formed first: adding a fixed
+// step sdt straight to X would round it to the grid of X's binade each time,
+// a binade-dependent step length (a systematic diffusion error of up to
+// ulp(X)/sdt); with the drift folded in, the one rounding is unbiased.
+__device__ __forceinline__ float move_gauss_f32(float x, float b, float xi, float dt, float sdt) {
+    return fmaf(sdt, xi, fmaf(b, dt, x));
+}
+__device__ __forceinline__ float move_bern_f32(float x, float b, float step, float dt) {
+    return x + fmaf(b, dt, step);
 }
 
 // ---------------------------------------------------------------------------

@@ -8,7 +8,8 @@
 //   xi     <- six N(0,1): Philox4x32-10 words (three blocks serve two moves),
 //             FP32 Box-Muller; or (NOISE = 1) six signs +-1 from the walker's
 //             Superduper generator, skipped ahead to the launch's first move
-//   X      <- X + b dt + sqrt(dt) xi                    (FP32, fused multiply-add)
+//   X      <- X + b dt + sqrt(dt) xi                    (FP32, fused multiply-add;
+//             Bernoulli: X + (b dt +- sqrt(dt)))
 //   b, E_L <- trial function at X in the cusp-cancelled form (FP32)
 //   node   :  sign psi changed or psi = 0 -> killed
 //   S      <- S + (E_L - E_T)            (FP32 Kahan sum since the last fold)
@@ -176,13 +177,15 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     if (!PARAM && KIND == 0) t_local = s_trial;
     const TrialDev<float>& t = PARAM ? tk : ((KIND == 0) ? t_local : s_trial);
 
-    const float dt = (float)I.dt, sdt = (float)I.sqrt_dt;
-    const float et = (float)I.e_trial;
+    // FP32 time step, noise scale and radius constant chosen on the host so the
+    // diffusion matches the drift, and the other derived constants, all formed
+    // on the host (gfk_mixed_consts.h)
+    const float dt = I.dt_f32, sdt = I.sdt_f32, r2_fix = I.r2_fix;
+    const float et = I.et_f32;
     const double dt64 = I.dt;
-    // per-move E_T rounding, restored in FP64 at each fold
-    const double et_fix = ((double)et - I.e_trial);
+    const double et_fix = I.et_fix;          // per-move E_T rounding, restored at each fold
     constexpr float kLog2e = 1.4426950408889634f;
-    const float dt_log2e = dt * kLog2e;
+    const float dt_log2e = I.dt_log2e;
     const uint32_t k0 = I.k0, k1 = I.k1;
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -248,14 +251,16 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             const bool alive = sg[k] != 0;
             float xi[6], xn[6];
             if (NOISE == 1) {
-                bernoulli6<float>(lcg[k], xi);
+                bernoulli6_steps(lcg[k], sdt, xi);        // +-sdt
             } else {
                 uint32_t words[6];
                 pair_move_words(pre[k], carry[k], step, s == 0, k0, k1, words);
-                normals6_f32(words, xi);
+                normals6_f32(words, xi, r2_fix);
             }
 #pragma unroll
-            for (int d = 0; d < 6; ++d) xn[d] = fmaf(sdt, xi[d], fmaf(b[k][d], dt, x[k][d]));
+            for (int d = 0; d < 6; ++d)
+                xn[d] = NOISE == 1 ? move_bern_f32(x[k][d], b[k][d], xi[d], dt)
+                                   : move_gauss_f32(x[k][d], b[k][d], xi[d], dt, sdt);
             EvalOut<float> ev;
             eval_trial<KIND, float, PARAM>(t, xn, ev);
             // a non-finite position is a non-finite kill, then a sign change a

@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "gfk_launch.h"
+#include "gfk_mixed_consts.h"
 #include "gfk_types.h"
 
 
@@ -144,6 +145,13 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     inst.id0 = d.walker_id0;
     inst.ee_on = d.ee_on ? 1 : 0;
     inst.noise = d.noise;
+    const MixedConsts mc = mixed_consts(d.dt, d.e_trial, d.noise);
+    inst.dt_f32 = mc.dt;
+    inst.sdt_f32 = mc.sdt;
+    inst.r2_fix = mc.r2_fix;
+    inst.et_f32 = mc.et;
+    inst.dt_log2e = mc.dt_log2e;
+    inst.et_fix = mc.et_fix;
     inst.trial = trial;
     InstDev* d_inst = (InstDev*)scratch;
     PartialRec* part = (PartialRec*)(scratch + kHeaderBytes);

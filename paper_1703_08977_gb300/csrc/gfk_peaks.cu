@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "gfk_device.cuh"
+#include "gfk_mixed_consts.h"
 #include "gfk_types.h"
 
 namespace {
@@ -131,16 +132,19 @@ extern "C" gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* la
 }
 
 // ---------------------------------------------------------------------------
-// gfk_radius_mean_error: the FP32 Box-Muller radius against FP64, summed over
-// every radius word.  One FP64 partial per thread, one atomic add per block.
+// gfk_normal_moments: the FP32 Box-Muller generator against FP64, summed over
+// every radius word (2^32) and every angle of the 23-bit grid.  One FP64
+// partial per thread and quantity, one atomic add per block and quantity.
 // ---------------------------------------------------------------------------
 namespace {
 
-__device__ __forceinline__ float radius2_variant(uint32_t w, int method) {
+constexpr int kNumMoments = 6;
+
+__device__ __forceinline__ float radius2_variant(uint32_t w, int method, float r2_fix) {
     constexpr float kInv32 = 1.0f / 4294967296.0f;
     constexpr float kHalfInv32 = 0.5f / 4294967296.0f;
     const float ua = fmaf((float)w, kInv32, kHalfInv32);
-    if (method == 0) return gfk::radius2_f32(w);
+    if (method == 0) return gfk::radius2_f32(w, r2_fix);
     if (method == 1) {
         float l2;
         asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(ua));
@@ -149,18 +153,10 @@ __device__ __forceinline__ float radius2_variant(uint32_t w, int method) {
     return fmaxf(-2.0f * logf(ua), 0.0f);
 }
 
-__global__ void radius_error_kernel(int method, double* __restrict__ out) {
-    __shared__ double s_part[8];
-    const uint64_t n = 1ull << 32;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    double acc = 0.0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t w = (uint32_t)i;
-        const double exact = -2.0 * log(((double)w + 0.5) * (1.0 / 4294967296.0));
-        acc += (double)radius2_variant(w, method) - exact;
-    }
-    acc = gfk::warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+__device__ __forceinline__ void block_add(double v, double* s_part, double* out) {
+    v = gfk::warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         double b = 0.0;
@@ -169,34 +165,65 @@ __global__ void radius_error_kernel(int method, double* __restrict__ out) {
     }
 }
 
+__global__ void normal_moments_kernel(int method, float r2_fix, double* __restrict__ out) {
+    __shared__ double s_part[8];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e_r2 = 0.0, e_rho2 = 0.0;
+    for (uint64_t i = first; i < (1ull << 32); i += stride) {
+        const uint32_t w = (uint32_t)i;
+        const double exact = -2.0 * log(((double)w + 0.5) * (1.0 / 4294967296.0));
+        const float r2 = radius2_variant(w, method, r2_fix);
+        const double rho = (double)gfk::radius_f32(r2);
+        e_r2 += (double)r2 - exact;
+        e_rho2 += rho * rho - exact;
+    }
+    double c2 = 0.0, s2 = 0.0, c1 = 0.0, s1 = 0.0;
+    for (uint64_t k = first; k < (1ull << 23); k += stride) {
+        float s, c;
+        gfk::angle_f32((uint32_t)k << 9, s, c);
+        c2 += (double)c * (double)c - 0.5;
+        s2 += (double)s * (double)s - 0.5;
+        c1 += (double)c;
+        s1 += (double)s;
+    }
+    const double v[kNumMoments] = {e_r2, e_rho2, c2, s2, c1, s1};
+    for (int q = 0; q < kNumMoments; ++q) block_add(v[q], s_part, out + q);
+}
+
 }  // namespace
 
-extern "C" gfk_status gfk_radius_mean_error(int32_t method, void* cuda_stream,
-                                            double* mean_error) {
-    if (!mean_error || method < 0 || method > 2) return GFK_EINVAL;
+extern "C" gfk_status gfk_normal_moments(int32_t method, void* cuda_stream, double* moments) {
+    if (!moments || method < 0 || method > 2) return GFK_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GFK_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return GFK_ECUDA;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     double* d = nullptr;
-    if (cudaMalloc(&d, sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&d, sizeof(double) * kNumMoments) != cudaSuccess) {
         (void)cudaGetLastError();
         return GFK_ENOMEM;
     }
-    double h = 0.0;
-    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double), stream);
+    double h[kNumMoments] = {0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double) * kNumMoments, stream);
     if (e == cudaSuccess) {
-        radius_error_kernel<<<sms * 8, 256, 0, stream>>>(method, d);
+        // the kernels' radius constant for a variance of exactly 1
+        const float r2_fix = (float)gfk::gaussian_r2_fix(0.0);
+        normal_moments_kernel<<<sms * 8, 256, 0, stream>>>(method, r2_fix, d);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     cudaFree(d);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return GFK_ECUDA;
     }
-    *mean_error = h / 4294967296.0;
+    const double n_radius = 4294967296.0, n_angle = 8388608.0;
+    moments[0] = h[0] / n_radius;
+    moments[1] = h[1] / n_radius;
+    for (int q = 2; q < kNumMoments; ++q) moments[q] = h[q] / n_angle;
     return GFK_OK;
 }

@@ -32,6 +32,12 @@ struct InstDev {
     uint32_t id0;       // Philox id of the instance's first walker
     int32_t ee_on;
     int32_t noise;      // gfk_noise: Gaussian (Philox normals) or Bernoulli (Superduper)
+    float dt_f32;       // mixed path: the drift's time step,
+    float sdt_f32;      //   the noise scale sqrt(dt),
+    float r2_fix;       //   the Box-Muller radius constant (gfk_mixed_consts.h),
+    float et_f32;       //   E_T in FP32,
+    float dt_log2e;     //   dt log2(e) in FP32,
+    double et_fix;      //   and et_f32 - E_T in FP64
     TrialHost trial;
 };
 

@@ -33,7 +33,7 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
            "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc",
            "gfk_measure_peak", "gfk_set_graph", "gfk_autotune", "gfk_grad",
-           "gfk_radius_mean_error")
+           "gfk_normal_moments")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
             "i2f", "f2f")
 GFK_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -100,7 +100,7 @@ def load(build_if_needed: bool = True):
             "gfk_status_string": ([c.c_int], c.c_char_p),
             "gfk_last_error": ([P], c.c_char_p),
             "gfk_measure_peak": ([c.c_int32, P, dp], c.c_int),
-            "gfk_radius_mean_error": ([c.c_int32, P, dp], c.c_int),
+            "gfk_normal_moments": ([c.c_int32, P, dp], c.c_int),
             "gfk_set_graph": ([P, c.c_int32], c.c_int),
             "gfk_grad": ([P, c.c_int32, c.c_int32, c.c_int64, c.c_int32, dp, c.c_int32, dp],
                          c.c_int),
@@ -343,16 +343,18 @@ def gfk_measure_peak(op, stream=None) -> float:
 RADIUS_METHODS = ("kernel", "hw_log2", "logf")
 
 
-def gfk_radius_mean_error(method="kernel", stream=None) -> float:
-    """Mean over all 2^32 radius words of the FP32 Box-Muller r2 minus -2 ln u in FP64."""
+MOMENT_NAMES = ("r2_err", "rho2_err", "cos2_err", "sin2_err", "cos_mean", "sin_mean")
+
+
+def gfk_normal_moments(method="kernel", stream=None) -> dict:
+    """Exhaustive moments of the FP32 Box-Muller normals against FP64 (see gfk.h)."""
     if isinstance(method, str):
         method = RADIUS_METHODS.index(method)
     if stream is None:
         stream = _current_stream_ptr()
-    v = ctypes.c_double()
-    _check(load().gfk_radius_mean_error(int(method), stream, ctypes.byref(v)),
-           "gfk_radius_mean_error")
-    return v.value
+    v = (ctypes.c_double * 6)()
+    _check(load().gfk_normal_moments(int(method), stream, v), "gfk_normal_moments")
+    return dict(zip(MOMENT_NAMES, list(v)))
 
 
 # ----------------------------------------------------------------------------

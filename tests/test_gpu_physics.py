@@ -33,16 +33,20 @@ def test_triplet_energy_extrapolates_to_exact(gfk_lib):
     assert abs(r["E_dt0"] - ex.EXACT[1]) < 4 * r["E_dt0_err"] + 1e-4, r
 
 
-def test_fp32_box_muller_radius_mean_is_exact(gfk_lib):
-    """Exhaustive over the 2^32 radius words: the mixed path's squared radius r2 has a
-    mean error below 5e-9 against -2 ln((w + 1/2) 2^-32) in FP64, so the normals'
-    variance (the diffusion constant, E[r2]/2) is right to 2.5e-9 relative.  The
-    uncorrected hardware log2 is short by the constant the kernels add back, and the
-    library logarithm is shown beside it."""
+def test_fp32_box_muller_normals_have_unit_variance(gfk_lib):
+    """Exhaustive over the 2^32 radius words and the 2^23 angles: the mixed path's FP32
+    normals xi_a = -rho cos, xi_b = -rho sin have variance (2 + E[rho^2 - R2]) (1/2 +
+    E[cos^2 - 1/2]) = 1 to 5e-9 (the diffusion constant of the walk), with the radius
+    constant the kernels use for an FP32 time step that needs no correction.  Beside
+    it: the bare hardware log2 radius is short by the constant the host folds in, the
+    library logarithm is within 2e-8, and the angle grid's cosine and sine average to 0."""
     gfk = gfk_lib
-    m_kernel = gfk.gfk_radius_mean_error("kernel")
-    m_hw = gfk.gfk_radius_mean_error("hw_log2")
-    m_lib = gfk.gfk_radius_mean_error("logf")
-    assert abs(m_kernel) < 5e-9, m_kernel
-    assert abs(m_hw + 1.630718e-7) < 2e-9, m_hw
-    assert abs(m_lib) < 2e-8, m_lib
+    m = gfk.gfk_normal_moments("kernel")
+    var_a = (2.0 + m["rho2_err"]) * (0.5 + m["cos2_err"]) - 1.0
+    var_b = (2.0 + m["rho2_err"]) * (0.5 + m["sin2_err"]) - 1.0
+    assert abs(var_a) < 5e-9 and abs(var_b) < 5e-9, (var_a, var_b, m)
+    m_hw = gfk.gfk_normal_moments("hw_log2")
+    m_lib = gfk.gfk_normal_moments("logf")
+    assert abs(m_hw["r2_err"] + 1.630718e-7) < 2e-9, m_hw
+    assert abs(m_lib["r2_err"]) < 2e-8, m_lib
+    assert abs(m["cos_mean"]) < 1e-7 and abs(m["sin_mean"]) < 1e-7, m
