@@ -72,17 +72,19 @@ template <> struct PosIO<float> {
 // The forward move of the precision, written exactly as the walk kernel of
 // that precision writes it (so the recomputed positions are the forward's).
 // FP64: X + b dt + sdt xi for both noise modes (xi = +-1 for Bernoulli).
-// FP32: the mixed kernel's helpers; for Bernoulli xi already holds +-sdt.
+// FP32: the mixed kernel's helpers; for Bernoulli xi already holds +-sdt and
+// xlo +-sdt_lo.
 __device__ __forceinline__ void adj_move(double x[6], const double b[6], const double xi[6],
-                                         double dt, double sdt, bool) {
+                                         const double*, double dt, double sdt, bool) {
 #pragma unroll
     for (int d = 0; d < 6; ++d) x[d] = x[d] + b[d] * dt + sdt * xi[d];
 }
 __device__ __forceinline__ void adj_move(float x[6], const float b[6], const float xi[6],
-                                         float dt, float sdt, bool bern) {
+                                         const float xlo[6], float dt, float sdt, bool bern) {
 #pragma unroll
     for (int d = 0; d < 6; ++d)
-        x[d] = bern ? move_bern_f32(x[d], b[d], xi[d], dt) : move_gauss_f32(x[d], b[d], xi[d], dt, sdt);
+        x[d] = bern ? move_bern_f32(x[d], b[d], xi[d], xlo[d], dt)
+                    : move_gauss_f32(x[d], b[d], xi[d], dt, sdt);
 }
 __device__ __forceinline__ void adj_normals(const uint32_t w[6], double xi[6], const InstDev*) {
     normals6_f64(w, xi);
@@ -90,11 +92,13 @@ __device__ __forceinline__ void adj_normals(const uint32_t w[6], double xi[6], c
 __device__ __forceinline__ void adj_normals(const uint32_t w[6], float xi[6], const InstDev* inst) {
     normals6_f32(w, xi, inst->r2_fix);
 }
-__device__ __forceinline__ void adj_bernoulli(uint32_t& s, double, double xi[6]) {
+__device__ __forceinline__ void adj_bernoulli(uint32_t& s, double, const InstDev*, double xi[6],
+                                              double*) {
     bernoulli6<double>(s, xi);
 }
-__device__ __forceinline__ void adj_bernoulli(uint32_t& s, float sdt, float xi[6]) {
-    bernoulli6_steps(s, sdt, xi);
+__device__ __forceinline__ void adj_bernoulli(uint32_t& s, float sdt, const InstDev* inst,
+                                              float xi[6], float xlo[6]) {
+    bernoulli6_steps(s, sdt, inst->sdt_lo, xi, xlo);
 }
 // The time step and noise scale the forward walk of the precision uses.
 __device__ __forceinline__ void adj_steps(const InstDev* inst, double& dt, double& sdt) {
@@ -275,16 +279,16 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 for (int m = n_lo; m < n_hi; ++m) {
                     EvalOut<T> ev;
                     eval_kind0<T>(tp, x, ev);
-                    T xi[6];
+                    T xi[6], xlo[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                     if (inst->noise == GFK_NOISE_BERNOULLI) {
-                        adj_bernoulli(lcg, sdt, xi);
+                        adj_bernoulli(lcg, sdt, inst, xi, xlo);
                     } else {
                         uint32_t words[6];
                         move_words(inst->id0 + (uint32_t)i, (uint32_t)m, inst->stream, inst->k0,
                                    inst->k1, words);
                         adj_normals(words, xi, inst);
                     }
-                    adj_move(x, ev.b, xi, dt, sdt, bern);
+                    adj_move(x, ev.b, xi, xlo, dt, sdt, bern);
                     PosIO<T>::store(seg + (int64_t)(m - n_lo + 1) * PosIO<T>::kWords * n, n, i, x);
                 }
                 // sweep it backwards

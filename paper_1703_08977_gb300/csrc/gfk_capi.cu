@@ -248,6 +248,7 @@ gfk_status upload_instances(gfk_ctx* ctx) {
         const MixedConsts mc = mixed_consts(d.dt, d.e_trial, d.noise);
         v.dt_f32 = mc.dt;
         v.sdt_f32 = mc.sdt;
+        v.sdt_lo = mc.sdt_lo;
         v.r2_fix = mc.r2_fix;
         v.et_f32 = mc.et;
         v.dt_log2e = mc.dt_log2e;

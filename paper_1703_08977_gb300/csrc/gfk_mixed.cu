@@ -180,7 +180,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     // FP32 time step, noise scale and radius constant chosen on the host so the
     // diffusion matches the drift, and the other derived constants, all formed
     // on the host (gfk_mixed_consts.h)
-    const float dt = I.dt_f32, sdt = I.sdt_f32, r2_fix = I.r2_fix;
+    const float dt = I.dt_f32, sdt = I.sdt_f32, sdt_lo = I.sdt_lo, r2_fix = I.r2_fix;
     const float et = I.et_f32;
     const double dt64 = I.dt;
     const double et_fix = I.et_fix;          // per-move E_T rounding, restored at each fold
@@ -249,9 +249,9 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
             const bool alive = sg[k] != 0;
-            float xi[6], xn[6];
+            float xi[6], xlo[6], xn[6];
             if (NOISE == 1) {
-                bernoulli6_steps(lcg[k], sdt, xi);        // +-sdt
+                bernoulli6_steps(lcg[k], sdt, sdt_lo, xi, xlo);   // +-sdt, +-sdt_lo
             } else {
                 uint32_t words[6];
                 pair_move_words(pre[k], carry[k], step, s == 0, k0, k1, words);
@@ -259,7 +259,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             }
 #pragma unroll
             for (int d = 0; d < 6; ++d)
-                xn[d] = NOISE == 1 ? move_bern_f32(x[k][d], b[k][d], xi[d], dt)
+                xn[d] = NOISE == 1 ? move_bern_f32(x[k][d], b[k][d], xi[d], xlo[d], dt)
                                    : move_gauss_f32(x[k][d], b[k][d], xi[d], dt, sdt);
             EvalOut<float> ev;
             eval_trial<KIND, float, PARAM>(t, xn, ev);

@@ -148,6 +148,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     const MixedConsts mc = mixed_consts(d.dt, d.e_trial, d.noise);
     inst.dt_f32 = mc.dt;
     inst.sdt_f32 = mc.sdt;
+    inst.sdt_lo = mc.sdt_lo;
     inst.r2_fix = mc.r2_fix;
     inst.et_f32 = mc.et;
     inst.dt_log2e = mc.dt_log2e;

@@ -34,6 +34,7 @@ struct InstDev {
     int32_t noise;      // gfk_noise: Gaussian (Philox normals) or Bernoulli (Superduper)
     float dt_f32;       // mixed path: the drift's time step,
     float sdt_f32;      //   the noise scale sqrt(dt),
+    float sdt_lo;       //   Bernoulli: the step length's sub-ulp part,
     float r2_fix;       //   the Box-Muller radius constant (gfk_mixed_consts.h),
     float et_f32;       //   E_T in FP32,
     float dt_log2e;     //   dt log2(e) in FP32,
