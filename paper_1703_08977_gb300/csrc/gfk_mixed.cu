@@ -163,11 +163,13 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                   unsigned long long* __restrict__ counters,
                   const __grid_constant__ TrialDev<float> tk) {
     __shared__ TrialDev<float> s_trial;
-    // double-buffered ring of per-warp sums (W, P, Q, R) and alive counts, and
-    // the per-warp log-weight shift each buffer's window used
-    __shared__ float s_ring[2][kRing][4][kMaxWarps];
-    __shared__ unsigned s_cnt[2][kRing][kMaxWarps];
+    // the per-warp log-weight shift each ring buffer's window used
     __shared__ double s_shift[2][kMaxWarps];
+    // dynamic shared memory (walk_smem_bytes):
+    //   ring  [2][kRing][4][nwarps] float:  per-warp sums (W, P, Q, R), double-buffered
+    //   cnt   [2][kRing][nwarps] unsigned:   per-warp alive counts
+    //   stage [nwarps][16][kStageStride] float: each lane's four sums of up to four moves
+    extern __shared__ float s_dyn[];
     const int blk = blockIdx.x;
     const int inst = block_instance(bm, blk);
     const InstDev& I = insts[inst];
@@ -190,6 +192,9 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = T >> 5;
+    float* const s_ring = s_dyn;
+    unsigned* const s_cnt = reinterpret_cast<unsigned*>(s_dyn + 2 * kRing * 4 * nwarps);
+    float* const s_stage = s_dyn + 2 * kRing * 5 * nwarps + warp * 16 * kStageStride;
 
     PhiloxPre pre[WPT];
     uint32_t carry[WPT][2];      // tag-1 words 2-3 of the even move, used by the odd one
@@ -294,18 +299,39 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             q3 += we * el;
             na += stay ? 1u : 0u;
         }
-        q0 = warp_sum(q0);
-        q1 = warp_sum(q1);
-        q2 = warp_sum(q2);
-        q3 = warp_sum(q3);
+        // the lane's four sums go to the warp's staging rows (column = move of
+        // the group x 4 + quantity); every fourth move, and at the end of a
+        // window, the warp adds the columns up (half a column per lane, the
+        // halves joined by one shuffle) and writes them to the ring
+        const int m4 = s & 3;
+        s_stage[(m4 * 4 + 0) * kStageStride + lane] = q0;
+        s_stage[(m4 * 4 + 1) * kStageStride + lane] = q1;
+        s_stage[(m4 * 4 + 2) * kStageStride + lane] = q2;
+        s_stage[(m4 * 4 + 3) * kStageStride + lane] = q3;
         na = __reduce_add_sync(0xffffffffu, na);
         const int r = s % kRing;
-        if (lane == 0) {
-            s_ring[buf][r][0][warp] = q0;
-            s_ring[buf][r][1][warp] = q1;
-            s_ring[buf][r][2][warp] = q2;
-            s_ring[buf][r][3][warp] = q3;
-            s_cnt[buf][r][warp] = na;
+        if (lane == 0) s_cnt[(buf * kRing + r) * nwarps + warp] = na;
+        if (m4 == 3 || r == kRing - 1 || s == nsteps - 1) {
+            __syncwarp();
+            const int col = lane & 15, half = lane >> 4;
+            const bool staged = (col >> 2) <= m4;
+            float v = 0.f;
+            if (staged) {
+                const float* src = s_stage + col * kStageStride + 16 * half;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+                for (int t = 0; t < 16; t += 4) {
+                    a0 += src[t];
+                    a1 += src[t + 1];
+                    a2 += src[t + 2];
+                    a3 += src[t + 3];
+                }
+                v = (a0 + a1) + (a2 + a3);
+            }
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            if (half == 0 && staged)
+                s_ring[((buf * kRing + r - m4 + (col >> 2)) * 4 + (col & 3)) * nwarps + warp] = v;
+            __syncwarp();                        // the staging rows are rewritten next move
         }
         ++fold_len;
         if (r == kRing - 1 || s == nsteps - 1) {
@@ -335,13 +361,15 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             if ((int)threadIdx.x < rows) {
                 const int rr = threadIdx.x;
                 double cb = -INFINITY;
+                const unsigned* cnt = s_cnt + (buf * kRing + rr) * nwarps;
+                const float* ring = s_ring + (buf * kRing + rr) * 4 * nwarps;
                 for (int w = 0; w < nwarps; ++w)
-                    if (s_cnt[buf][rr][w] != 0u) cb = fmax(cb, s_shift[buf][w]);
+                    if (cnt[w] != 0u) cb = fmax(cb, s_shift[buf][w]);
                 double acc[4] = {0, 0, 0, 0};
                 unsigned n_alive = 0;
                 if (isfinite(cb)) {
                     for (int w = 0; w < nwarps; ++w) {
-                        const unsigned nw = s_cnt[buf][rr][w];
+                        const unsigned nw = cnt[w];
                         if (nw == 0u) continue;
                         n_alive += nw;
                         // warp shift relative to the block's: exact in FP64, then
@@ -350,7 +378,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             const float fk = k == 2 ? f * f : f;
-                            acc[k] += (double)(s_ring[buf][rr][k][w] * fk);
+                            acc[k] += (double)(ring[k * nwarps + w] * fk);
                         }
                     }
                 } else {
@@ -383,6 +411,24 @@ cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* in
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of the walk kernel for `threads` threads per block.
+static size_t walk_smem_bytes(int threads) {
+    const size_t nwarps = (size_t)threads / 32;
+    return 4 * (2 * kRing * 5 * nwarps + nwarps * 16 * kStageStride);
+}
+
+template <typename K>
+static void launch_walk(K kernel, int nblk, int threads, cudaStream_t stream,
+                        const InstDev* insts, const BlockMap& bm, const StateMixed& st,
+                        uint32_t step0, int nsteps, PartialRec* part,
+                        unsigned long long* counters, const TrialDev<float>& tk) {
+    const size_t smem = walk_smem_bytes(threads);
+    if (smem > 48 * 1024)       // above the default limit (512-thread blocks): opt in
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kernel<<<nblk, threads, smem, stream>>>(insts, bm, st, step0, nsteps, part, nblk, counters,
+                                            tk);
+}
+
 template <int KIND, int NOISE, bool PARAM>
 static void launch_walk_mixed_k(int wpt, int threads, int nblk, const InstDev* insts,
                                 const BlockMap& bm, const StateMixed& st, uint32_t step0,
@@ -390,16 +436,16 @@ static void launch_walk_mixed_k(int wpt, int threads, int nblk, const InstDev* i
                                 const TrialDev<float>& tk, cudaStream_t stream) {
     switch (wpt) {
         case 1:
-            walk_mixed_kernel<KIND, 1, NOISE, PARAM><<<nblk, threads, 0, stream>>>(
-                insts, bm, st, step0, nsteps, part, nblk, counters, tk);
+            launch_walk(walk_mixed_kernel<KIND, 1, NOISE, PARAM>, nblk, threads, stream, insts, bm,
+                        st, step0, nsteps, part, counters, tk);
             break;
         case 2:
-            walk_mixed_kernel<KIND, 2, NOISE, PARAM><<<nblk, threads, 0, stream>>>(
-                insts, bm, st, step0, nsteps, part, nblk, counters, tk);
+            launch_walk(walk_mixed_kernel<KIND, 2, NOISE, PARAM>, nblk, threads, stream, insts, bm,
+                        st, step0, nsteps, part, counters, tk);
             break;
         default:
-            walk_mixed_kernel<KIND, 4, NOISE, PARAM><<<nblk, threads, 0, stream>>>(
-                insts, bm, st, step0, nsteps, part, nblk, counters, tk);
+            launch_walk(walk_mixed_kernel<KIND, 4, NOISE, PARAM>, nblk, threads, stream, insts, bm,
+                        st, step0, nsteps, part, counters, tk);
             break;
     }
 }

@@ -79,6 +79,9 @@ struct StateMixed {
 constexpr int kRing = 64;
 constexpr int kMaxThreads = 512;
 constexpr int kMaxWarps = kMaxThreads / 32;
+// Row stride (floats) of the mixed walk's per-warp staging rows: 32 lanes plus
+// one, so that reading a column across the warp hits 32 distinct banks.
+constexpr int kStageStride = 33;
 
 // Counters per instance: [0] non-finite kills, [1] node kills, [2] coalescences.
 constexpr int kNumCounters = 3;
