@@ -61,12 +61,12 @@ OPS_PER_WALKER_STEP = {(0, 0): 290, (0, 1): 405, (1, 0): 146, (1, 1): 261}
 # Lanes that can issue an ALU instruction per SM per clock (4 schedulers x 32).
 LANES_PER_SM_CLK = 128
 # DRAM traffic (read + write) of the walk kernel per walker-step, from one ncu
-# capture of a launch of the bench's shape (2^20 walkers x 1024 moves, the
-# launch shape the bench uses), valid only for the kernel sources it was taken
+# capture of a launch of the bench's shape (2^20 walkers x 1024 moves, 128
+# threads x 2 walkers, the launch shape the bench autotunes to), valid only for the kernel sources it was taken
 # on (sha256 prefix of csrc/*); scaled by the walker-steps of an average launch.
 WALK_TRAFFIC = {       # workload -> capture
-    "ground": {"src_sha": "5898b30ed7f6bf3a", "bytes_per_walker_step": 0.19997},
-    "bernoulli": {"src_sha": "5898b30ed7f6bf3a", "bytes_per_walker_step": 0.11120},
+    "ground": {"src_sha": "86b345cf8219dc66", "bytes_per_walker_step": 0.20091},
+    "bernoulli": {"src_sha": "86b345cf8219dc66", "bytes_per_walker_step": 0.19919},
 }
 
 
