@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -96,7 +97,10 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # scratch file of the samples (the JSON line carries their summary);
+        # GFK_CLOCKS_DIR keeps it somewhere else than the system temp folder
+        self.path = os.path.join(os.environ.get("GFK_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"gfk_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
