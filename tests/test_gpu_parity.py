@@ -263,3 +263,43 @@ def test_walker_id_shards_reproduce_one_population(gfk_lib, prec):
     np.testing.assert_array_equal(merged[:, 5], full.sums()[:, 5])
     for c in parts + [full]:
         c.close()
+
+
+@pytest.mark.parametrize("noise,dt", [(0, 0.005), (1, 1.0 / 900.0)])
+def test_full_size_sampled_walkers_match_oracle(gfk_lib, noise, dt):
+    """The benchmark's workload size and launch shape (2^20 walkers, ground-state
+    trial, 128 threads x 2 walkers per thread; one full 1024-move launch): 64
+    sampled walkers -- block edges, the last walker and random ids -- recomputed one
+    by one by the oracle.  The FP64 path matches them to 1e-12 per walker; the
+    mixed (benchmarked) path keeps them alive exactly when the oracle does and at
+    FP32-level distance; over the whole population its E(t) stays within 2e-7
+    hartree of the FP64 path's at every step."""
+    gfk = gfk_lib
+    n, moves, et, seed = 1 << 20, 1024, -2.9037, 0
+    p = wl.ground()
+    rng = np.random.default_rng(5)
+    ids = np.unique(np.concatenate([[0, 1, 127, 128, 255, 256, 511, 512, n - 256, n - 1],
+                                    rng.integers(0, n, 54)])).astype(np.uint32)
+    d64 = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=et, seed=seed, prec=0, noise=noise)
+    d32 = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=et, seed=seed, prec=1, noise=noise)
+    with gfk.Context([d64], trials=[(0, p)]) as c64:
+        c64.propagate(moves)
+        x64, lw64, al64 = c64.walkers(0)
+        e64 = c64.energy(0)["E"]
+        n64 = c64.sums(0)[:, 5]
+    with gfk.Context([d32], trials=[(0, p)], launch=(128, 2)) as c32:
+        c32.propagate(moves)
+        x32, lw32, al32 = c32.walkers(0)
+        e32 = c32.energy(0)["E"]
+        n32 = c32.sums(0)[:, 5]
+    w = oracle.Walk(0, p, ids=ids, dt=dt, e_trial=et, seed=seed, noise=noise).advance(moves)
+    a = w.alive.astype(bool)
+    np.testing.assert_array_equal(al64[ids].astype(bool), a)
+    np.testing.assert_array_equal(al32[ids].astype(bool), a)
+    dx64 = np.abs(x64[ids] - w.x).max(axis=1) / np.maximum(1.0, np.abs(w.x).max(axis=1))
+    assert dx64.max() <= REL_WALKER, dx64.max()
+    assert np.abs(lw64[ids][a] - w.logw[a]).max() <= REL_WALKER * max(1.0, np.abs(w.logw[a]).max())
+    dx32 = np.abs(x32[ids] - w.x).max(axis=1)
+    assert np.median(dx32) < 1e-4 and dx32.max() < 1e-2, (np.median(dx32), dx32.max())
+    assert np.abs(e32 - e64).max() < 2e-7, np.abs(e32 - e64).max()
+    np.testing.assert_array_equal(n32, n64)
