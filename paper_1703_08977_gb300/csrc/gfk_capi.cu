@@ -332,7 +332,7 @@ gfk_status enqueue_init(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk) {
                                       ctx->part, ctx->counters, ctx->stream));
     }
     GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, 1, ctx->series, ctx->series_cap, 0,
-                                   ctx->stream));
+                                   ctx->prec == GFK_PREC_FP64, ctx->stream));
     return GFK_OK;
 }
 
@@ -368,7 +368,8 @@ gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t
             ctx->prof_walker_steps += (double)walkers * chunk;
         }
         GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
-                                       ctx->series_cap, step_begin + done + 1, ctx->stream));
+                                       ctx->series_cap, step_begin + done + 1,
+                                       ctx->prec == GFK_PREC_FP64, ctx->stream));
         done += chunk;
     }
     return GFK_OK;
@@ -767,7 +768,8 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
                                           ctx->stream);
                 if (e == cudaSuccess)
                     e = launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
-                                           ctx->series_cap, ctx->steps + 1, ctx->stream);
+                                           ctx->series_cap, ctx->steps + 1,
+                                           ctx->prec == GFK_PREC_FP64, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(b);
                 float ms = 0.f;

@@ -25,9 +25,10 @@ cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nbl
                               uint32_t step0, int nsteps, PartialRec* part,
                               unsigned long long* counters, const TrialHost* one_trial,
                               int ee_on, cudaStream_t stream);
+// compensated: double-double W and P (the FP64 path); plain FP64 sums otherwise
 cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
                                SeriesRow* series, int64_t series_cap, int64_t row_base,
-                               cudaStream_t stream);
+                               bool compensated, cudaStream_t stream);
 cudaError_t launch_finalize(const SeriesRow* rows, int64_t n, double n0, double* e, double* lnz,
                             double* ess, cudaStream_t stream);
 cudaError_t launch_export(bool mixed, const StateF64& s64, const StateMixed& smx, int64_t off,

@@ -189,7 +189,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     if (init) {
         NA_CK(cudaMemsetAsync(dev_counters, 0, sizeof(unsigned long long) * kNumCounters, stream));
         NA_CK(launch_init_mixed(kind, kThreads, nblk, d_inst, bm, sm, part, dev_counters, stream));
-        NA_CK(launch_reduce_rows(part, nblk, bm, 1, rows, n_rows, 0, stream));
+        NA_CK(launch_reduce_rows(part, nblk, bm, 1, rows, n_rows, 0, false, stream));
     }
     int64_t done = 0;
     while (done < n_steps) {
@@ -197,7 +197,8 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
         NA_CK(launch_walk_mixed(kind, d.noise, kWpt, kThreads, nblk, d_inst, bm, sm,
                                 (uint32_t)(step0 + done), chunk, part, dev_counters, &trial,
                                 inst.ee_on, stream));
-        NA_CK(launch_reduce_rows(part, nblk, bm, chunk, rows, n_rows, (init ? 1 : 0) + done, stream));
+        NA_CK(launch_reduce_rows(part, nblk, bm, chunk, rows, n_rows, (init ? 1 : 0) + done, false,
+                                 stream));
         done += chunk;
     }
 #undef NA_CK

@@ -5,10 +5,14 @@
 // block records {c_b, W_b, P_b, Q_b, R_b, n_b} into
 //   C = max_b c_b,  W = sum_b W_b e^{c_b - C},  P = sum_b P_b e^{c_b - C},
 //   Q = sum_b Q_b e^{2 (c_b - C)},  R = sum_b R_b e^{c_b - C},  n = sum_b n_b.
-// W and P (the energy's denominator and numerator) are carried as
-// unevaluated double-doubles (Neumaier compensation per thread, TwoSum across
-// threads), so E = P / W is the quotient of correctly rounded sums up to
-// O(2^-100); Q and R (effective sample size, variance) are plain FP64 sums;
+// On the FP64 path (COMP) W and P (the energy's denominator and numerator) are
+// carried as unevaluated double-doubles (Neumaier compensation per thread,
+// TwoSum across threads), so E = P / W is the quotient of correctly rounded
+// sums up to O(2^-100).  The mixed path's block sums are FP32-accurate, so it
+// adds W and P in plain FP64 (relative error ~1e-13 over thousands of blocks,
+// far below its 1e-9 hartree energy error) at half the FP64 arithmetic, which
+// is what bounds this kernel here.  Q and R (effective sample size, variance)
+// are plain FP64 sums;
 // n is an integer count, exact in FP64.  The shifts c_b are integer-valued, so
 // a thread recomputes the factor e^{c_b - C} only when the integer changes.
 // finalize_kernel turns merged rows into E(t) = P/W, ln z(t) = C + ln W - ln N
@@ -41,6 +45,7 @@ __device__ __forceinline__ DD dd_shfl_xor(DD v, int o) {
 
 constexpr int kReduceThreads = 256;
 
+template <bool COMP>
 __global__ void __launch_bounds__(kReduceThreads)
 reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
                    SeriesRow* __restrict__ series, int64_t series_cap, int64_t row_base) {
@@ -74,12 +79,17 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
             last_k = k;
         }
         const double w = r.W * f, p = r.P * f;
-        double t = sW + w;
-        cW += fabs(sW) >= fabs(w) ? (sW - t) + w : (w - t) + sW;
-        sW = t;
-        t = sP + p;
-        cP += fabs(sP) >= fabs(p) ? (sP - t) + p : (p - t) + sP;
-        sP = t;
+        if (COMP) {
+            double t = sW + w;
+            cW += fabs(sW) >= fabs(w) ? (sW - t) + w : (w - t) + sW;
+            sW = t;
+            t = sP + p;
+            cP += fabs(sP) >= fabs(p) ? (sP - t) + p : (p - t) + sP;
+            sP = t;
+        } else {
+            sW += w;
+            sP += p;
+        }
         sQ += r.Q * f * f;
         sR += r.R * f;
         sN += r.n;
@@ -87,7 +97,7 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
     DD acc[5] = {{sW, cW}, {sP, cP}, {sQ, 0.0}, {sR, 0.0}, {sN, 0.0}};
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        if (k < 2) {
+        if (COMP && k < 2) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc[k] = dd_add(acc[k], dd_shfl_xor(acc[k], o));
         } else {
@@ -101,7 +111,7 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
         for (int k = 0; k < 5; ++k) {
             tot[k] = s_acc[k][0];
             for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-                if (k < 2) tot[k] = dd_add(tot[k], s_acc[k][w]);
+                if (COMP && k < 2) tot[k] = dd_add(tot[k], s_acc[k][w]);
                 else tot[k].hi += s_acc[k][w].hi;
             }
         }
@@ -164,10 +174,14 @@ __global__ void export_mixed_kernel(StateMixed st, int64_t off, int64_t n, doubl
 
 cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
                                SeriesRow* series, int64_t series_cap, int64_t row_base,
-                               cudaStream_t stream) {
+                               bool compensated, cudaStream_t stream) {
     dim3 grid(rows, bm.n_inst);
-    reduce_rows_kernel<<<grid, kReduceThreads, 0, stream>>>(part, nblk, bm, series, series_cap,
-                                                             row_base);
+    if (compensated)
+        reduce_rows_kernel<true><<<grid, kReduceThreads, 0, stream>>>(part, nblk, bm, series,
+                                                                      series_cap, row_base);
+    else
+        reduce_rows_kernel<false><<<grid, kReduceThreads, 0, stream>>>(part, nblk, bm, series,
+                                                                       series_cap, row_base);
     return cudaGetLastError();
 }
 
