@@ -143,41 +143,75 @@ class Clocks:
 
 # ----------------------------------------------------------------------------
 def run_reference(args):
-    """The oracle (plain FP64 C, one host thread) on a bounded sample of the workload."""
+    """The oracle (plain FP64 C, unchanged) on a bounded sample of the workload, on all
+    host cores: one spawned process per core walks a disjoint block of walker ids."""
     ws, rank, _ = _dist_env()
     if rank != 0:
         return
-    import numpy as np
     import oracle
     oracle.build()
-    n_sample, moves = 4096, 100
     name = args.workload if args.workload in ("ground", "bernoulli") else "ground"
-    kind, params, dt, et, noise = _oracle_case(name)
-
-    def one():
-        w = oracle.Walk(kind, params, n_walkers=n_sample, dt=dt, e_trial=et, seed=SEED,
-                        noise=noise)
-        w.advance(moves)
-        return w
-
-    for _ in range(args.warmup):
-        one()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        one()
-    dt_s = time.perf_counter() - t0
+    n_sample, moves = 1 << 14, 100
+    with OraclePool() as pool:
+        for _ in range(args.warmup):
+            pool.walk(name, n_sample, moves)
+        t = [pool.walk(name, n_sample, moves) for _ in range(args.steps)]
+        cores = pool.n
+    dt_s = sum(t)
     value = n_sample * moves * args.steps / dt_s
-    sample = f"{n_sample} walkers x {moves} moves per step (a slice of the 2^20 x 20000 workload)"
+    sample = (f"{n_sample} walkers x {moves} moves per step (a slice of the 2^20 x 20000 "
+              f"workload), {cores} processes over disjoint walker ids")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOADS[name], "name": name,
                                         "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def _oracle_block(job):
+    """One process's share of an oracle timing: walker ids [lo, hi) for `moves` moves;
+    returns the seconds it took (module level, so spawned processes can run it)."""
+    name, lo, hi, moves = job
+    import numpy as np
+    import oracle
+    kind, params, dt, et, noise = _oracle_case(name)
+    t0 = time.perf_counter()
+    w = oracle.Walk(kind, params, ids=np.arange(lo, hi, dtype=np.uint32), dt=dt, e_trial=et,
+                    seed=SEED, noise=noise)
+    w.advance(moves)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """Spawned worker processes (spawn: the parent may already hold a CUDA context)."""
+
+    def __init__(self, n=None):
+        self.n = n or max(1, os.cpu_count() or 1)
+
+    def __enter__(self):
+        import multiprocessing as mp
+        self.pool = mp.get_context("spawn").Pool(self.n)
+        # each worker imports the oracle once before anything is timed
+        self.pool.map(_oracle_block, [("ground", 0, 1, 1)] * self.n)
+        return self
+
+    def __exit__(self, *exc):
+        self.pool.close()
+        self.pool.join()
+
+    def walk(self, name, n_walkers, moves):
+        """Wall-clock seconds for n_walkers x moves, split into one block per process."""
+        edges = [n_walkers * i // self.n for i in range(self.n + 1)]
+        jobs = [(name, edges[i], edges[i + 1], moves) for i in range(self.n)
+                if edges[i + 1] > edges[i]]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_block, jobs, chunksize=1)
+        return time.perf_counter() - t0
 
 
 def _oracle_case(name):
@@ -188,17 +222,21 @@ def _oracle_case(name):
 
 
 def cpu_baseline(name="ground"):
+    """The oracle on the host: all cores (one spawned process per core, disjoint walker
+    ids; the reported value) and one thread (reported beside it)."""
     import oracle
     oracle.build()
-    n_sample, moves = 1 << 14, 600
-    kind, params, dt, et, noise = _oracle_case(name)
-    t0 = time.perf_counter()
-    w = oracle.Walk(kind, params, n_walkers=n_sample, dt=dt, e_trial=et, seed=SEED, noise=noise)
-    w.advance(moves)
-    el = time.perf_counter() - t0
-    return {"value": n_sample * moves / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"2^14 walkers x {moves} moves of the same workload, one host thread "
-                      f"({os.cpu_count()} cores on the host)"}
+    moves = 600
+    t1 = _oracle_block((name, 0, 1 << 13, moves))
+    single = (1 << 13) * moves / t1
+    with OraclePool() as pool:
+        n_par = (1 << 13) * pool.n
+        tp = pool.walk(name, n_par, moves)
+        cores = pool.n
+    return {"value": n_par * moves / tp, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_par} walkers x {moves} moves of the same workload, {cores} processes "
+                      "over disjoint walker ids (2^13 each)",
+            "single_thread": {"value": single, "sample": f"2^13 walkers x {moves} moves"}}
 
 
 def _workload(name, rank):
