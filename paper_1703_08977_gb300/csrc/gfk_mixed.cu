@@ -8,8 +8,8 @@
 //   xi     <- six N(0,1): Philox4x32-10 words (three blocks serve two moves),
 //             FP32 Box-Muller; or (NOISE = 1) six signs +-1 from the walker's
 //             Superduper generator, skipped ahead to the launch's first move
-//   X      <- X + b dt + sqrt(dt) xi                    (FP32, fused multiply-add;
-//             Bernoulli: X + (b dt +- sqrt(dt)))
+//   X      <- X + (b dt + sqrt(dt) xi)   (FP32, the increment formed first;
+//             Bernoulli: X + ((b dt +- s_lo) +- s), gfk_device.cuh)
 //   b, E_L <- trial function at X in the cusp-cancelled form (FP32)
 //   node   :  sign psi changed or psi = 0 -> killed
 //   S      <- S + (E_L - E_T)            (FP32 Kahan sum since the last fold)
@@ -17,10 +17,13 @@
 // Every kRing steps the FP32 sums are folded into the FP64 base,
 //   L <- L - (S + kRing (E_T,fp32 - E_T)) dt            (FP64),
 // the warp's shift c is reset to the floor of its largest L and d = (float)(L - c).
-// Per step each warp adds its (w, w E_L, w^2, w E_L^2) in FP32 and counts its
-// live walkers; every kRing steps, after one block barrier, the block rescales
-// each warp's sums to the block's largest shift and adds them in FP64, writing
-// one PartialRec per step; a deferred kernel merges the blocks (double-double).
+// Per step each lane stages its (w, w E_L, w^2, w E_L^2) in shared memory and
+// the warp counts its live walkers; every fourth step the warp adds the staged
+// columns in FP32.  Every kRing steps, after one block barrier, the block
+// rescales each warp's sums to the block's largest shift and adds them in FP64,
+// writing one PartialRec per step; a deferred kernel merges the blocks.  The
+// FP32 constants (dt, sqrt(dt), the Box-Muller radius constant, E_T) come from
+// the host (gfk_mixed_consts.h), chosen so that the diffusion matches the drift.
 #include <cuda_runtime.h>
 
 #include <cstring>
