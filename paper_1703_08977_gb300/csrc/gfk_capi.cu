@@ -642,6 +642,9 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
                 break;
             }
         if (!hit) {
+            if (ctx->prec == GFK_PREC_MIXED)
+                GFK_CK(ctx, prepare_walk_mixed(launch_kind(ctx), ctx->noise, ctx->wpt,
+                                               ctx->threads, one_trial(ctx) != nullptr));
             GFK_CK(ctx, cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeThreadLocal));
             ctx->stream = ctx->graph_stream;          // the enqueue helpers use ctx->stream
             gfk_status cs = GFK_OK;

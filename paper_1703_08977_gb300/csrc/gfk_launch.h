@@ -25,6 +25,10 @@ cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nbl
                               uint32_t step0, int nsteps, PartialRec* part,
                               unsigned long long* counters, const TrialHost* one_trial,
                               int ee_on, cudaStream_t stream);
+// Sets what the mixed walk kernel of this launch shape needs before it can be
+// launched (the shared-memory opt-in of 512-thread blocks); called before a
+// stream capture, where it could not happen.
+cudaError_t prepare_walk_mixed(int kind, int noise, int wpt, int threads, bool one_trial);
 // compensated: double-double W and P (the FP64 path); plain FP64 sums otherwise
 cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
                                SeriesRow* series, int64_t series_cap, int64_t row_base,

@@ -420,35 +420,38 @@ static size_t walk_smem_bytes(int threads) {
     return 4 * (2 * kRing * 5 * nwarps + nwarps * 16 * kStageStride);
 }
 
+// run = false only prepares the kernel (the shared-memory opt-in), so that it
+// can happen before a stream capture rather than inside it.
 template <typename K>
 static void launch_walk(K kernel, int nblk, int threads, cudaStream_t stream,
                         const InstDev* insts, const BlockMap& bm, const StateMixed& st,
                         uint32_t step0, int nsteps, PartialRec* part,
-                        unsigned long long* counters, const TrialDev<float>& tk) {
+                        unsigned long long* counters, const TrialDev<float>& tk, bool run) {
     const size_t smem = walk_smem_bytes(threads);
     if (smem > 48 * 1024)       // above the default limit (512-thread blocks): opt in
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kernel<<<nblk, threads, smem, stream>>>(insts, bm, st, step0, nsteps, part, nblk, counters,
-                                            tk);
+    if (run)
+        kernel<<<nblk, threads, smem, stream>>>(insts, bm, st, step0, nsteps, part, nblk,
+                                                counters, tk);
 }
 
 template <int KIND, int NOISE, bool PARAM>
 static void launch_walk_mixed_k(int wpt, int threads, int nblk, const InstDev* insts,
                                 const BlockMap& bm, const StateMixed& st, uint32_t step0,
                                 int nsteps, PartialRec* part, unsigned long long* counters,
-                                const TrialDev<float>& tk, cudaStream_t stream) {
+                                const TrialDev<float>& tk, cudaStream_t stream, bool run) {
     switch (wpt) {
         case 1:
             launch_walk(walk_mixed_kernel<KIND, 1, NOISE, PARAM>, nblk, threads, stream, insts, bm,
-                        st, step0, nsteps, part, counters, tk);
+                        st, step0, nsteps, part, counters, tk, run);
             break;
         case 2:
             launch_walk(walk_mixed_kernel<KIND, 2, NOISE, PARAM>, nblk, threads, stream, insts, bm,
-                        st, step0, nsteps, part, counters, tk);
+                        st, step0, nsteps, part, counters, tk, run);
             break;
         default:
             launch_walk(walk_mixed_kernel<KIND, 4, NOISE, PARAM>, nblk, threads, stream, insts, bm,
-                        st, step0, nsteps, part, counters, tk);
+                        st, step0, nsteps, part, counters, tk, run);
             break;
     }
 }
@@ -457,22 +460,23 @@ template <int NOISE>
 static void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, const InstDev* insts,
                                 const BlockMap& bm, const StateMixed& st, uint32_t step0,
                                 int nsteps, PartialRec* part, unsigned long long* counters,
-                                const TrialHost* one_trial, int ee_on, cudaStream_t stream) {
+                                const TrialHost* one_trial, int ee_on, cudaStream_t stream,
+                                bool run) {
     TrialDev<float> tk;
     std::memset(&tk, 0, sizeof(tk));
     if (one_trial) load_trial<float>(*one_trial, ee_on, tk);
     if (one_trial && kind == 1)
         launch_walk_mixed_k<1, NOISE, true>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
-                                            part, counters, tk, stream);
+                                            part, counters, tk, stream, run);
     else if (kind == 0)
         launch_walk_mixed_k<0, NOISE, false>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
-                                             part, counters, tk, stream);
+                                             part, counters, tk, stream, run);
     else if (kind == 1)
         launch_walk_mixed_k<1, NOISE, false>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
-                                             part, counters, tk, stream);
+                                             part, counters, tk, stream, run);
     else
         launch_walk_mixed_k<2, NOISE, false>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
-                                             part, counters, tk, stream);
+                                             part, counters, tk, stream, run);
 }
 
 cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk,
@@ -482,10 +486,26 @@ cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nbl
                               int ee_on, cudaStream_t stream) {
     if (noise == GFK_NOISE_BERNOULLI)
         launch_walk_mixed_n<1>(kind, wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
-                               counters, one_trial, ee_on, stream);
+                               counters, one_trial, ee_on, stream, true);
     else
         launch_walk_mixed_n<0>(kind, wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
-                               counters, one_trial, ee_on, stream);
+                               counters, one_trial, ee_on, stream, true);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_walk_mixed(int kind, int noise, int wpt, int threads, bool one_trial) {
+    TrialHost dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    BlockMap bm;
+    std::memset(&bm, 0, sizeof(bm));
+    StateMixed st{};
+    const TrialHost* t = one_trial ? &dummy : nullptr;
+    if (noise == GFK_NOISE_BERNOULLI)
+        launch_walk_mixed_n<1>(kind, wpt, threads, 0, nullptr, bm, st, 0u, 0, nullptr, nullptr, t,
+                               0, nullptr, false);
+    else
+        launch_walk_mixed_n<0>(kind, wpt, threads, 0, nullptr, bm, st, 0u, 0, nullptr, nullptr, t,
+                               0, nullptr, false);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,28 @@ def test_graph_replay_follows_a_new_trial_function(gfk_lib, kind, p1, p2):
         c.close()
 
 
+@pytest.mark.parametrize("noise", [0, 1])
+def test_graph_capture_at_512_threads(gfk_lib, noise):
+    """512-thread blocks need more than the default 48 KB of dynamic shared memory; the
+    opt-in is made before the capture starts, so a graph captured at that launch shape
+    (in a fresh process this may be the first launch of the kernel) reproduces direct
+    launches bitwise, on its first capture and on replay."""
+    gfk = gfk_lib
+    d = gfk.InstanceDesc(n_walkers=20000, dt=0.005, e_trial=-2.9, seed=6, prec=1, noise=noise)
+    direct = gfk.Context([d], trials=[(0, wl.ground())], launch=(512, 2)).propagate(200)
+    g = gfk.Context([d], trials=[(0, wl.ground())], launch=(512, 2))
+    g.set_graph(True)
+    g.propagate(200)
+    for u, v in zip(direct.walkers(0), g.walkers(0)):
+        np.testing.assert_array_equal(u, v)
+    np.testing.assert_array_equal(direct.sums(0), g.sums(0))
+    g.reset()
+    g.propagate(200)                  # replay
+    np.testing.assert_array_equal(direct.sums(0), g.sums(0))
+    direct.close()
+    g.close()
+
+
 def test_batched_mixed_instances_match_single(gfk_lib):
     """The twelve-instance mix in one context (mixed path, one launch per chunk with the
     trial family dispatched per block) reproduces each instance run alone, walker by
