@@ -227,6 +227,11 @@ int launch_kind(const gfk_ctx* ctx) {
     return k;
 }
 
+// The kind the mixed walk kernels are launched with (gfk_launch.h).
+int mixed_kind(const gfk_ctx* ctx) {
+    return mixed_walk_kind(launch_kind(ctx), ctx->trial.data(), ctx->n_inst);
+}
+
 gfk_status upload_instances(gfk_ctx* ctx) {
     std::vector<InstDev> h(ctx->n_inst);
     for (int i = 0; i < ctx->n_inst; ++i) {
@@ -358,7 +363,7 @@ gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t
             GFK_CK(ctx, launch_walk_fp64(kind, ctx->noise, ctx->threads, (int)nblk, ctx->d_inst,
                                          bm, ctx->s64, step0, chunk, ctx->part, ctx->counters, ctx->stream));
         } else {
-            GFK_CK(ctx, launch_walk_mixed(kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
+            GFK_CK(ctx, launch_walk_mixed(mixed_kind(ctx), ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
                                           ctx->d_inst, bm, ctx->smx, step0, chunk, ctx->part, ctx->counters,
                                           one_trial(ctx), ctx->desc[0].ee_on, ctx->stream));
         }
@@ -643,7 +648,7 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
             }
         if (!hit) {
             if (ctx->prec == GFK_PREC_MIXED)
-                GFK_CK(ctx, prepare_walk_mixed(launch_kind(ctx), ctx->noise, ctx->wpt,
+                GFK_CK(ctx, prepare_walk_mixed(mixed_kind(ctx), ctx->noise, ctx->wpt,
                                                ctx->threads, one_trial(ctx) != nullptr));
             GFK_CK(ctx, cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeThreadLocal));
             ctx->stream = ctx->graph_stream;          // the enqueue helpers use ctx->stream
@@ -765,7 +770,7 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
                                          bm, ctx->s64, (uint32_t)ctx->steps, chunk, ctx->part, ctx->counters,
                                          ctx->stream);
                 else
-                    e = launch_walk_mixed(kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
+                    e = launch_walk_mixed(mixed_kind(ctx), ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
                                           ctx->d_inst, bm, ctx->smx, (uint32_t)ctx->steps, chunk, ctx->part,
                                           ctx->counters, one_trial(ctx), ctx->desc[0].ee_on,
                                           ctx->stream);

@@ -489,7 +489,9 @@ struct Kind1Acc {
     R G1[3] = {R(0), R(0), R(0)}, G2[3] = {R(0), R(0), R(0)};
 };
 
-template <typename R>
+// PLAIN: every orbital is c0 e^{-alpha r} (no r or z prefactor terms), so the
+// prefactor terms, which would be exact zeros, are left out.
+template <typename R, bool PLAIN = false>
 __device__ __forceinline__ void kind1_term(const TrialDev<R>& t, int k, R r1, R r2, const R rr[2],
                                            const R ir[2], const R zz[2], const R h1[3],
                                            const R h2[3], R emax, Kind1Acc<R>& acc) {
@@ -506,6 +508,16 @@ __device__ __forceinline__ void kind1_term(const TrialDev<R>& t, int k, R r1, R 
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const R* hh = e == 0 ? h1 : h2;
+        if (PLAIN) {
+            const R c0 = t.c0[k][e];
+            const R radial = -t.al[k][e] * c0;
+            gr[e][0] = radial * hh[0];
+            gr[e][1] = radial * hh[1];
+            gr[e][2] = radial * hh[2];
+            K[e] = c0 * (t.km2[k][e] * ir[e] - t.hal2[k][e]);
+            p[e] = c0;
+            continue;
+        }
         R al = t.al[k][e], c1 = t.c1[k][e], cz = t.cz[k][e];
         R pe = t.c0[k][e] + c1 * rr[e] + cz * zz[e];
         R radial = c1 - al * pe;                      // coefficient of r_hat
@@ -530,7 +542,7 @@ __device__ __forceinline__ void kind1_term(const TrialDev<R>& t, int k, R r1, R 
 // UNROLL: the term loops run to GFK_MAX_TERMS with a uniform early exit, so
 // every parameter index is a compile-time constant (for a trial held in the
 // kernel's parameter bank); otherwise they run to t.nterms (fewer registers).
-template <typename R, bool UNROLL = false>
+template <typename R, bool UNROLL = false, bool PLAIN = false>
 __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
     R s1 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
@@ -572,11 +584,11 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
 #pragma unroll
         for (int k = 0; k < GFK_MAX_TERMS; ++k) {
             if (k >= t.nterms) break;
-            kind1_term<R>(t, k, r1, r2, rr, ir, zz, h1, h2, emax, acc);
+            kind1_term<R, PLAIN>(t, k, r1, r2, rr, ir, zz, h1, h2, emax, acc);
         }
     } else {
         for (int k = 0; k < t.nterms; ++k)
-            kind1_term<R>(t, k, r1, r2, rr, ir, zz, h1, h2, emax, acc);
+            kind1_term<R, PLAIN>(t, k, r1, r2, rr, ir, zz, h1, h2, emax, acc);
     }
     const R Phi = acc.Phi, T = acc.T;
     const R* G1 = acc.G1;
@@ -596,11 +608,14 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
 }
 
 // KIND 0 / 1 select the family at compile time; KIND 2 dispatches on t.kind
-// (used when one launch covers instances of both families).
+// (used when one launch covers instances of both families); KIND 3 is the
+// orbital-pair family whose orbitals all lack the r and z prefactor terms
+// (the mixed walk's launcher picks it when every instance qualifies).
 template <int KIND, typename R, bool UNROLL = false>
 __device__ __forceinline__ void eval_trial(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
     if (KIND == 0) eval_kind0<R>(t, x, o);
     else if (KIND == 1) eval_kind1<R, UNROLL>(t, x, o);
+    else if (KIND == 3) eval_kind1<R, UNROLL, true>(t, x, o);
     else if (t.kind == 0) eval_kind0<R>(t, x, o);
     else eval_kind1<R>(t, x, o);
 }

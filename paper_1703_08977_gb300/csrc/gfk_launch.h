@@ -18,6 +18,8 @@ cudaError_t launch_walk_fp64(int kind, int noise, int threads, int nblk, const I
 cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
                               const BlockMap& bm, const StateMixed& st, PartialRec* part,
                               unsigned long long* counters, cudaStream_t stream);
+// kind: 0 / 1 the trial family, 2 both in one launch, 3 orbital pairs whose
+// orbitals all lack the r and z prefactor terms (mixed_walk_kind).
 // one_trial: when the launch covers a single instance, its trial function (and
 // ee_on); the kernel then takes it as a launch argument.  NULL otherwise.
 cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk,
@@ -25,6 +27,18 @@ cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nbl
                               uint32_t step0, int nsteps, PartialRec* part,
                               unsigned long long* counters, const TrialHost* one_trial,
                               int ee_on, cudaStream_t stream);
+// The mixed walk's kind for these trial functions: 3 when every one is an
+// orbital-pair function whose orbitals have no r or z prefactor terms
+// (c1 = cz = 0 in every used term), else `kind` unchanged.
+inline int mixed_walk_kind(int kind, const TrialHost* trials, int n) {
+    if (kind != GFK_TRIAL_ORBITAL_PAIRS) return kind;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < trials[i].nterms; ++k)
+            for (int e = 0; e < 2; ++e)
+                if (trials[i].c1[k][e] != 0.0 || trials[i].cz[k][e] != 0.0) return kind;
+    return 3;
+}
+
 // Sets what the mixed walk kernel of this launch shape needs before it can be
 // launched (the shared-memory opt-in of 512-thread blocks); called before a
 // stream capture, where it could not happen.

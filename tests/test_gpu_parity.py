@@ -182,6 +182,28 @@ def test_mixed_path_tracks_fp64_oracle(gfk_lib):
     assert np.max(np.abs(g["energy"]["E"] - s["E"])) < 1e-4
 
 
+@pytest.mark.parametrize("name", ["triplet_2s3", "fn3"])
+def test_mixed_orbital_pairs_track_fp64_oracle(gfk_lib, name):
+    """The mixed path's orbital-pair kernels against the oracle: the 2^3S trial (all
+    orbitals without r and z prefactor terms: the specialised evaluation) and trial
+    function 3 ((r0 - r) prefactor: the generic one), 2059 walkers x 100 moves.  Kill
+    decisions agree except for walkers whose FP32 and FP64 paths straddle the node
+    within rounding (at most 0.5 %), positions stay at FP32 distance, and E(t) within
+    2e-4."""
+    gfk = gfk_lib
+    kind, p, et = {"triplet_2s3": (1, wl.triplet_2s3(), -2.1752),
+                   "fn3": (1, wl.fn3(), -2.124)}[name]
+    n, steps = 2048 + 11, 100
+    g = _gpu_run(gfk, kind, p, n, steps, 0.01, et, 3, gfk.GFK_PREC_MIXED, launch=(128, 2))
+    w = _oracle_run(kind, p, n, steps, 0.01, et, 3)
+    same = g["alive"].astype(bool) == w.alive.astype(bool)
+    assert (~same).sum() <= n // 200, (~same).sum()
+    both = same & w.alive.astype(bool)
+    dx = np.abs(g["x"] - w.x).max(axis=1)[both]
+    assert np.median(dx) < 1e-5 and np.quantile(dx, 0.99) < 1e-3, (np.median(dx), dx.max())
+    assert np.max(np.abs(g["energy"]["E"] - w.series()["E"])) < 2e-4
+
+
 def test_mixed_normals_never_degenerate(gfk_lib):
     """The FP32 uniforms stay strictly inside (0, 1): over 2^20 walkers x 48 moves
     (3 x 1.5e8 Box-Muller radii) no ground-state walker is killed for a non-finite
