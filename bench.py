@@ -58,7 +58,22 @@ SEED = 0
 # compares (18); then the move (12), the trial evaluation (105 ops for the
 # ground-state product, kind 0; 220 for a two-term orbital-pair function,
 # kind 1), the weight and the sums (11).  Keyed by (noise, kind).
-OPS_PER_WALKER_STEP = {(0, 0): 290, (0, 1): 405, (1, 0): 146, (1, 1): 261}
+# Orbital pairs whose orbitals have no r or z prefactor terms (the 2^3S trial)
+# do about 12 fewer ops per orbital, 48 per walker-step (key kind 3).
+OPS_PER_WALKER_STEP = {(0, 0): 290, (0, 1): 405, (0, 3): 357,
+                       (1, 0): 146, (1, 1): 261, (1, 3): 213}
+
+
+def _ops_kind(kind, params):
+    """3 for an orbital-pair trial whose orbitals all lack r and z prefactor terms."""
+    if kind != 1:
+        return kind
+    nterms = int(params[6])
+    for t in range(nterms):
+        q = params[7 + 9 * t: 16 + 9 * t]
+        if q[3] != 0 or q[4] != 0 or q[7] != 0 or q[8] != 0:
+            return kind
+    return 3
 # Lanes that can issue an ALU instruction per SM per clock (4 schedulers x 32).
 LANES_PER_SM_CLK = 128
 # DRAM traffic (read + write) of the walk kernel per walker-step, from one ncu
@@ -415,8 +430,8 @@ def run_ours(args):
         ws_per_launch = walk_ws / max(1, walk_launches)
         sm_max = clk.get("sm_max_mhz") or 2070.0
         peak = n_sm * LANES_PER_SM_CLK * sm_max * 1e6 / 1e9      # Gop/s
-        ops = sum(OPS_PER_WALKER_STEP[(d["noise"], d["kind"])] * d["n_walkers"]
-                  for d in insts) / n_walkers
+        ops = sum(OPS_PER_WALKER_STEP[(d["noise"], _ops_kind(d["kind"], d["params"]))]
+                  * d["n_walkers"] for d in insts) / n_walkers
         achieved = ops * ws_per_launch / (avg_launch_ms / 1e3) / 1e9
         traffic = None
         tr = WALK_TRAFFIC.get(args.workload)
