@@ -81,8 +81,8 @@ LANES_PER_SM_CLK = 128
 # threads x 2 walkers, the launch shape the bench autotunes to), valid only for the kernel sources it was taken
 # on (sha256 prefix of csrc/*); scaled by the walker-steps of an average launch.
 WALK_TRAFFIC = {       # workload -> capture
-    "ground": {"src_sha": "ac4ed7b9f1bbc798", "bytes_per_walker_step": 0.19942},
-    "bernoulli": {"src_sha": "ac4ed7b9f1bbc798", "bytes_per_walker_step": 0.20099},
+    "ground": {"src_sha": "9c9bb712f94bee39", "bytes_per_walker_step": 0.19942},
+    "bernoulli": {"src_sha": "9c9bb712f94bee39", "bytes_per_walker_step": 0.20099},
 }
 
 
@@ -365,6 +365,7 @@ def run_ours(args):
     # ---- timed region: K device-resident steps, L2 flushed between them ----
     gfk.gfk_profile(ctx.handle, True)
     gfk.gfk_profile_read(ctx.handle, reset=True)
+    gfk.gfk_kernel_count(ctx.handle, reset=True)
     clocks = Clocks(dev)
     if ws > 1:
         dist.barrier()
@@ -385,6 +386,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     walk_ms, walk_launches, walk_ws = gfk.gfk_profile_read(ctx.handle, reset=True)
+    kernels_timed = gfk.gfk_kernel_count(ctx.handle, reset=True)   # the library's own count
     gfk.gfk_profile(ctx.handle, False)
     if ws > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -437,7 +439,6 @@ def run_ours(args):
         tr = WALK_TRAFFIC.get(args.workload)
         if tr and tr["src_sha"] == _src_sha():
             traffic = tr["bytes_per_walker_step"] * ws_per_launch
-        launches_per_step = 2 * walk_launches / args.steps + 2
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -449,7 +450,7 @@ def run_ours(args):
                                   "chosen_by": "autotune" if launch[2] else "flags"},
                        "l2": "flushed (256 MB write) before every timed step; state "
                              f"{n_walkers * 33 / 2**20:.0f} MB"},
-            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "gpu_launches": int(kernels_timed),
             "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "e2e": {"value": walker_steps_per_step * ws / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

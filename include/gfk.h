@@ -245,6 +245,14 @@ gfk_status gfk_profile(gfk_ctx* ctx, int32_t enable);
 gfk_status gfk_profile_read(gfk_ctx* ctx, double* walk_ms, int64_t* launches,
                             double* walker_steps, int32_t reset);
 
+/* Number of kernels gfk_propagate has queued on the context's stream since
+ * gfk_create or the last reset of the count (reset != 0 clears it after
+ * reading): for each initialisation its kernel and the merge of its sums, for
+ * each chunk of moves the walk kernels (one per run of instances that share a
+ * specialised kernel) and the merge, and for a CUDA-graph replay the kernels
+ * the graph holds.  GFK_EINVAL for a NULL argument. */
+gfk_status gfk_kernel_count(gfk_ctx* ctx, int64_t* count, int32_t reset);
+
 /* Allocation-free variant of the mixed-precision walk (the paper has no
  * counterpart: this is a service to callers that cannot let a library call
  * cudaMalloc -- frameworks that own all device memory through their own

@@ -56,6 +56,7 @@ struct gfk_ctx {
         int64_t step0, n_steps, nblk;
         int init, threads, wpt;
         uint64_t trial_hash;            // single-instance walks take the trial as an argument
+        int64_t kernels;                // kernels the graph launches
         const void* series;
         const void* part;
         cudaGraphExec_t exec;
@@ -70,6 +71,7 @@ struct gfk_ctx {
     std::vector<cudaEvent_t> ev_pool;     // pairs: [2k] start, [2k+1] stop
     int64_t ev_used = 0;                  // pairs recorded since the last read
     int64_t prof_launches = 0;
+    int64_t kernels = 0;                 // kernels queued by gfk_propagate (gfk_kernel_count)
     double prof_ms = 0.0;
     double prof_walker_steps = 0.0;
     // progress
@@ -156,12 +158,6 @@ struct DeviceGuard {
 
 bool finite_d(double v) { return std::isfinite(v); }
 
-// The trial function of a single-instance context (the walk kernels then take it
-// as a launch argument), or NULL when the context holds several instances.
-const TrialHost* one_trial(const gfk_ctx* ctx) {
-    return ctx->n_inst == 1 ? &ctx->trial[0] : nullptr;
-}
-
 gfk_status parse_trial(int kind, const double* p, int np, TrialHost* t) {
     std::memset(t, 0, sizeof(*t));
     if (!p) return GFK_EINVAL;
@@ -230,6 +226,56 @@ int launch_kind(const gfk_ctx* ctx) {
 // The kind the mixed walk kernels are launched with (gfk_launch.h).
 int mixed_kind(const gfk_ctx* ctx) {
     return mixed_walk_kind(launch_kind(ctx), ctx->trial.data(), ctx->n_inst);
+}
+
+// Launches of one chunk of the mixed walk.  A context of several instances is
+// split into runs of consecutive instances that share the specialised kernel
+// kind, one launch each (a run of one instance also takes its trial function as
+// a launch argument), provided every run has at least kMinSegmentBlocks blocks
+// to fill the GPU; otherwise one launch covers all instances.
+struct WalkSegment {
+    int kind, i0, i1;
+};
+constexpr int64_t kMinSegmentBlocks = 1024;
+
+std::vector<WalkSegment> walk_segments(const gfk_ctx* ctx, const BlockMap& bm) {
+    std::vector<WalkSegment> v;
+    if (ctx->n_inst > 1) {
+        for (int i = 0; i < ctx->n_inst; ++i) {
+            const int k = mixed_walk_kind(ctx->trial[i].kind, &ctx->trial[i], 1);
+            if (!v.empty() && v.back().kind == k) v.back().i1 = i + 1;
+            else v.push_back({k, i, i + 1});
+        }
+        bool big = v.size() > 1;
+        for (const WalkSegment& g : v)
+            if (bm.begin[g.i1] - bm.begin[g.i0] < kMinSegmentBlocks) big = false;
+        if (big) return v;
+        v.clear();
+    }
+    v.push_back({mixed_kind(ctx), 0, ctx->n_inst});
+    return v;
+}
+
+cudaError_t launch_mixed_walks(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, uint32_t step0,
+                               int chunk) {
+    for (const WalkSegment& g : walk_segments(ctx, bm)) {
+        const bool one = g.i1 - g.i0 == 1;
+        const cudaError_t e = launch_walk_mixed(
+            g.kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk, bm.begin[g.i0],
+            bm.begin[g.i1] - bm.begin[g.i0], ctx->d_inst, bm, ctx->smx, step0, chunk, ctx->part,
+            ctx->counters, one ? &ctx->trial[g.i0] : nullptr, ctx->desc[g.i0].ee_on, ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t prepare_mixed_walks(const gfk_ctx* ctx, const BlockMap& bm) {
+    for (const WalkSegment& g : walk_segments(ctx, bm)) {
+        const cudaError_t e = prepare_walk_mixed(g.kind, ctx->noise, ctx->wpt, ctx->threads,
+                                                 g.i1 - g.i0 == 1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 gfk_status upload_instances(gfk_ctx* ctx) {
@@ -338,6 +384,7 @@ gfk_status enqueue_init(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk) {
     }
     GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, 1, ctx->series, ctx->series_cap, 0,
                                    ctx->prec == GFK_PREC_FP64, ctx->stream));
+    ctx->kernels += 2;                                  // the init and its merge
     return GFK_OK;
 }
 
@@ -363,15 +410,15 @@ gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t
             GFK_CK(ctx, launch_walk_fp64(kind, ctx->noise, ctx->threads, (int)nblk, ctx->d_inst,
                                          bm, ctx->s64, step0, chunk, ctx->part, ctx->counters, ctx->stream));
         } else {
-            GFK_CK(ctx, launch_walk_mixed(mixed_kind(ctx), ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
-                                          ctx->d_inst, bm, ctx->smx, step0, chunk, ctx->part, ctx->counters,
-                                          one_trial(ctx), ctx->desc[0].ee_on, ctx->stream));
+            GFK_CK(ctx, launch_mixed_walks(ctx, bm, nblk, step0, chunk));
+            ctx->kernels += (int64_t)walk_segments(ctx, bm).size() - 1;   // + 1 below
         }
         if (ev1) {
             GFK_CK(ctx, cudaEventRecord(ev1, ctx->stream));
             ctx->prof_launches += 1;
             ctx->prof_walker_steps += (double)walkers * chunk;
         }
+        ctx->kernels += 2;                              // the walk and the merge
         GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
                                        ctx->series_cap, step_begin + done + 1,
                                        ctx->prec == GFK_PREC_FP64, ctx->stream));
@@ -647,15 +694,16 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
                 break;
             }
         if (!hit) {
-            if (ctx->prec == GFK_PREC_MIXED)
-                GFK_CK(ctx, prepare_walk_mixed(mixed_kind(ctx), ctx->noise, ctx->wpt,
-                                               ctx->threads, one_trial(ctx) != nullptr));
+            if (ctx->prec == GFK_PREC_MIXED) GFK_CK(ctx, prepare_mixed_walks(ctx, bm));
             GFK_CK(ctx, cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeThreadLocal));
             ctx->stream = ctx->graph_stream;          // the enqueue helpers use ctx->stream
+            const int64_t k_before = ctx->kernels;     // captured, not yet run
             gfk_status cs = GFK_OK;
             if (init) cs = enqueue_init(ctx, bm, nblk);
             if (cs == GFK_OK) cs = enqueue_moves(ctx, bm, nblk, rows_fit, step_begin, n_steps, false);
             ctx->stream = user;
+            const int64_t k_graph = ctx->kernels - k_before;
+            ctx->kernels = k_before;
             cudaGraph_t graph = nullptr;
             cudaError_t ce = cudaStreamEndCapture(ctx->graph_stream, &graph);
             if (cs != GFK_OK) {
@@ -672,10 +720,11 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
                 ctx->graphs.erase(ctx->graphs.begin());
             }
             ctx->graphs.push_back({step_begin, n_steps, nblk, init ? 1 : 0, ctx->threads, ctx->wpt,
-                                   th, ctx->series, ctx->part, exec});
+                                   th, k_graph, ctx->series, ctx->part, exec});
             hit = &ctx->graphs.back();
         }
         GFK_CK(ctx, cudaGraphLaunch(hit->exec, ctx->graph_stream));
+        ctx->kernels += hit->kernels;
         GFK_CK(ctx, cudaEventRecord(ctx->graph_join, ctx->graph_stream));
         GFK_CK(ctx, cudaStreamWaitEvent(user, ctx->graph_join, 0));
     } else {
@@ -770,10 +819,7 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
                                          bm, ctx->s64, (uint32_t)ctx->steps, chunk, ctx->part, ctx->counters,
                                          ctx->stream);
                 else
-                    e = launch_walk_mixed(mixed_kind(ctx), ctx->noise, ctx->wpt, ctx->threads, (int)nblk,
-                                          ctx->d_inst, bm, ctx->smx, (uint32_t)ctx->steps, chunk, ctx->part,
-                                          ctx->counters, one_trial(ctx), ctx->desc[0].ee_on,
-                                          ctx->stream);
+                    e = launch_mixed_walks(ctx, bm, nblk, (uint32_t)ctx->steps, chunk);
                 if (e == cudaSuccess)
                     e = launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
                                            ctx->series_cap, ctx->steps + 1,
@@ -1095,7 +1141,8 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
         if (e == cudaSuccess)
             e = f64 ? launch_walk_fp64(kind, ctx->noise, shape.threads, (int)nblk, d_inst, bm, s64,
                                        (uint32_t)(j * K), steps, part, cnt, ctx->stream)
-                    : launch_walk_mixed(kind, ctx->noise, shape.wpt, shape.threads, (int)nblk,
+                    : launch_walk_mixed(kind, ctx->noise, shape.wpt, shape.threads, (int)nblk, 0,
+                                        (int)nblk,
                                         d_inst, bm, smx, (uint32_t)(j * K), steps, part, cnt,
                                         &ctx->trial[inst], ctx->desc[inst].ee_on, ctx->stream);
     }
@@ -1154,6 +1201,13 @@ gfk_status gfk_profile_read(gfk_ctx* ctx, double* walk_ms, int64_t* launches,
         ctx->prof_launches = 0;
         ctx->prof_walker_steps = 0.0;
     }
+    return GFK_OK;
+}
+
+gfk_status gfk_kernel_count(gfk_ctx* ctx, int64_t* count, int32_t reset) {
+    if (!ctx || !count) return GFK_EINVAL;
+    *count = ctx->kernels;
+    if (reset) ctx->kernels = 0;
     return GFK_OK;
 }
 

@@ -22,9 +22,11 @@ cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* in
 // orbitals all lack the r and z prefactor terms (mixed_walk_kind).
 // one_trial: when the launch covers a single instance, its trial function (and
 // ee_on); the kernel then takes it as a launch argument.  NULL otherwise.
-cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk,
-                              const InstDev* insts, const BlockMap& bm, const StateMixed& st,
-                              uint32_t step0, int nsteps, PartialRec* part,
+// nblk: all blocks of the context (the records' stride); the launch runs
+// blocks blk0 .. blk0 + grid - 1 of them.
+cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk, int blk0,
+                              int grid, const InstDev* insts, const BlockMap& bm,
+                              const StateMixed& st, uint32_t step0, int nsteps, PartialRec* part,
                               unsigned long long* counters, const TrialHost* one_trial,
                               int ee_on, cudaStream_t stream);
 // The mixed walk's kind for these trial functions: 3 when every one is an

@@ -9,12 +9,12 @@
 
 namespace gfk {
 
-extern template void launch_walk_mixed_n<1>(int kind, int wpt, int threads, int nblk,
-                                            const InstDev* insts, const BlockMap& bm,
+extern template void launch_walk_mixed_n<1>(int kind, int wpt, int threads, int nblk, int blk0,
+                                            int grid, const InstDev* insts, const BlockMap& bm,
                                             const StateMixed& st, uint32_t step0, int nsteps,
                                             PartialRec* part, unsigned long long* counters,
-                                            const TrialHost* one_trial, int ee_on, cudaStream_t stream,
-                                            bool run);
+                                            const TrialHost* one_trial, int ee_on,
+                                            cudaStream_t stream, bool run);
 
 cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
                               const BlockMap& bm, const StateMixed& st, PartialRec* part,
@@ -28,17 +28,17 @@ cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* in
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk,
-                              const InstDev* insts, const BlockMap& bm, const StateMixed& st,
-                              uint32_t step0, int nsteps, PartialRec* part,
+cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nblk, int blk0,
+                              int grid, const InstDev* insts, const BlockMap& bm,
+                              const StateMixed& st, uint32_t step0, int nsteps, PartialRec* part,
                               unsigned long long* counters, const TrialHost* one_trial,
                               int ee_on, cudaStream_t stream) {
     if (noise == GFK_NOISE_BERNOULLI)
-        launch_walk_mixed_n<1>(kind, wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
-                               counters, one_trial, ee_on, stream, true);
+        launch_walk_mixed_n<1>(kind, wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
+                               part, counters, one_trial, ee_on, stream, true);
     else
-        launch_walk_mixed_n<0>(kind, wpt, threads, nblk, insts, bm, st, step0, nsteps, part,
-                               counters, one_trial, ee_on, stream, true);
+        launch_walk_mixed_n<0>(kind, wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
+                               part, counters, one_trial, ee_on, stream, true);
     return cudaGetLastError();
 }
 
@@ -50,11 +50,11 @@ cudaError_t prepare_walk_mixed(int kind, int noise, int wpt, int threads, bool o
     StateMixed st{};
     const TrialHost* t = one_trial ? &dummy : nullptr;
     if (noise == GFK_NOISE_BERNOULLI)
-        launch_walk_mixed_n<1>(kind, wpt, threads, 0, nullptr, bm, st, 0u, 0, nullptr, nullptr, t,
-                               0, nullptr, false);
+        launch_walk_mixed_n<1>(kind, wpt, threads, 0, 0, 0, nullptr, bm, st, 0u, 0, nullptr,
+                               nullptr, t, 0, nullptr, false);
     else
-        launch_walk_mixed_n<0>(kind, wpt, threads, 0, nullptr, bm, st, 0u, 0, nullptr, nullptr, t,
-                               0, nullptr, false);
+        launch_walk_mixed_n<0>(kind, wpt, threads, 0, 0, 0, nullptr, bm, st, 0u, 0, nullptr,
+                               nullptr, t, 0, nullptr, false);
     return cudaGetLastError();
 }
 

@@ -165,7 +165,7 @@ template <int KIND, int WPT, int NOISE, bool PARAM>
 __global__ void __launch_bounds__(kMaxThreads)
 walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                   uint32_t step0, int nsteps, PartialRec* __restrict__ part, int nblk,
-                  unsigned long long* __restrict__ counters,
+                  unsigned long long* __restrict__ counters, int blk0,
                   const __grid_constant__ TrialDev<float> tk) {
     __shared__ TrialDev<float> s_trial;
     // the per-warp log-weight shift each ring buffer's window used
@@ -175,7 +175,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     //   cnt   [2][kRing][nwarps] unsigned:   per-warp alive counts
     //   stage [nwarps][16][kStageStride] float: each lane's four sums of up to four moves
     extern __shared__ float s_dyn[];
-    const int blk = blockIdx.x;
+    const int blk = blockIdx.x + blk0;       // a launch may cover a range of blocks
     const int inst = block_instance(bm, blk);
     const InstDev& I = insts[inst];
     if (!PARAM && threadIdx.x == 0) load_trial<float>(I.trial, I.ee_on, s_trial);
@@ -413,7 +413,7 @@ static size_t walk_smem_bytes(int threads) {
 // run = false only prepares the kernel (the shared-memory opt-in), so that it
 // can happen before a stream capture rather than inside it.
 template <typename K>
-static void launch_walk(K kernel, int nblk, int threads, cudaStream_t stream,
+static void launch_walk(K kernel, int nblk, int blk0, int grid, int threads, cudaStream_t stream,
                         const InstDev* insts, const BlockMap& bm, const StateMixed& st,
                         uint32_t step0, int nsteps, PartialRec* part,
                         unsigned long long* counters, const TrialDev<float>& tk, bool run) {
@@ -421,33 +421,35 @@ static void launch_walk(K kernel, int nblk, int threads, cudaStream_t stream,
     if (smem > 48 * 1024)       // above the default limit (512-thread blocks): opt in
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (run)
-        kernel<<<nblk, threads, smem, stream>>>(insts, bm, st, step0, nsteps, part, nblk,
-                                                counters, tk);
+        kernel<<<grid, threads, smem, stream>>>(insts, bm, st, step0, nsteps, part, nblk,
+                                                counters, blk0, tk);
 }
 
 template <int KIND, int NOISE, bool PARAM>
-static void launch_walk_mixed_k(int wpt, int threads, int nblk, const InstDev* insts,
+static void launch_walk_mixed_k(int wpt, int threads, int nblk, int blk0, int grid,
+                                const InstDev* insts,
                                 const BlockMap& bm, const StateMixed& st, uint32_t step0,
                                 int nsteps, PartialRec* part, unsigned long long* counters,
                                 const TrialDev<float>& tk, cudaStream_t stream, bool run) {
     switch (wpt) {
         case 1:
-            launch_walk(walk_mixed_kernel<KIND, 1, NOISE, PARAM>, nblk, threads, stream, insts, bm,
-                        st, step0, nsteps, part, counters, tk, run);
+            launch_walk(walk_mixed_kernel<KIND, 1, NOISE, PARAM>, nblk, blk0, grid, threads, stream,
+                        insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
         case 2:
-            launch_walk(walk_mixed_kernel<KIND, 2, NOISE, PARAM>, nblk, threads, stream, insts, bm,
-                        st, step0, nsteps, part, counters, tk, run);
+            launch_walk(walk_mixed_kernel<KIND, 2, NOISE, PARAM>, nblk, blk0, grid, threads, stream,
+                        insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
         default:
-            launch_walk(walk_mixed_kernel<KIND, 4, NOISE, PARAM>, nblk, threads, stream, insts, bm,
-                        st, step0, nsteps, part, counters, tk, run);
+            launch_walk(walk_mixed_kernel<KIND, 4, NOISE, PARAM>, nblk, blk0, grid, threads, stream,
+                        insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
     }
 }
 
 template <int NOISE>
-void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, const InstDev* insts,
+void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, int blk0, int grid,
+                         const InstDev* insts,
                                 const BlockMap& bm, const StateMixed& st, uint32_t step0,
                                 int nsteps, PartialRec* part, unsigned long long* counters,
                                 const TrialHost* one_trial, int ee_on, cudaStream_t stream,
@@ -456,22 +458,22 @@ void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, const InstDev
     std::memset(&tk, 0, sizeof(tk));
     if (one_trial) load_trial<float>(*one_trial, ee_on, tk);
     if (one_trial && kind == 1)
-        launch_walk_mixed_k<1, NOISE, true>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
+        launch_walk_mixed_k<1, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                             part, counters, tk, stream, run);
     else if (one_trial && kind == 3)
-        launch_walk_mixed_k<3, NOISE, true>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
+        launch_walk_mixed_k<3, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                             part, counters, tk, stream, run);
     else if (kind == 3)
-        launch_walk_mixed_k<3, NOISE, false>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
+        launch_walk_mixed_k<3, NOISE, false>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                              part, counters, tk, stream, run);
     else if (kind == 0)
-        launch_walk_mixed_k<0, NOISE, false>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
+        launch_walk_mixed_k<0, NOISE, false>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                              part, counters, tk, stream, run);
     else if (kind == 1)
-        launch_walk_mixed_k<1, NOISE, false>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
+        launch_walk_mixed_k<1, NOISE, false>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                              part, counters, tk, stream, run);
     else
-        launch_walk_mixed_k<2, NOISE, false>(wpt, threads, nblk, insts, bm, st, step0, nsteps,
+        launch_walk_mixed_k<2, NOISE, false>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                              part, counters, tk, stream, run);
 }
 

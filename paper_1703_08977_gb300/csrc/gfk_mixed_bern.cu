@@ -4,8 +4,8 @@
 
 namespace gfk {
 
-template void launch_walk_mixed_n<1>(int kind, int wpt, int threads, int nblk,
-                                     const InstDev* insts, const BlockMap& bm,
+template void launch_walk_mixed_n<1>(int kind, int wpt, int threads, int nblk, int blk0,
+                                     int grid, const InstDev* insts, const BlockMap& bm,
                                      const StateMixed& st, uint32_t step0, int nsteps,
                                      PartialRec* part, unsigned long long* counters,
                                      const TrialHost* one_trial, int ee_on, cudaStream_t stream,

@@ -195,7 +195,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     while (done < n_steps) {
         const int chunk = (int)((n_steps - done) < rows_fit ? (n_steps - done) : rows_fit);
         NA_CK(launch_walk_mixed(mixed_walk_kind(kind, &trial, 1), d.noise, kWpt, kThreads, nblk,
-                                d_inst, bm, sm,
+                                0, nblk, d_inst, bm, sm,
                                 (uint32_t)(step0 + done), chunk, part, dev_counters, &trial,
                                 inst.ee_on, stream));
         NA_CK(launch_reduce_rows(part, nblk, bm, chunk, rows, n_rows, (init ? 1 : 0) + done, false,

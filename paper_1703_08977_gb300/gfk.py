@@ -33,7 +33,7 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
            "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc",
            "gfk_measure_peak", "gfk_set_graph", "gfk_autotune", "gfk_grad",
-           "gfk_normal_moments")
+           "gfk_normal_moments", "gfk_kernel_count")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
             "i2f", "f2f")
 GFK_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -101,6 +101,7 @@ def load(build_if_needed: bool = True):
             "gfk_last_error": ([P], c.c_char_p),
             "gfk_measure_peak": ([c.c_int32, P, dp], c.c_int),
             "gfk_normal_moments": ([c.c_int32, P, dp], c.c_int),
+            "gfk_kernel_count": ([P, c.POINTER(c.c_int64), c.c_int32], c.c_int),
             "gfk_set_graph": ([P, c.c_int32], c.c_int),
             "gfk_grad": ([P, c.c_int32, c.c_int32, c.c_int64, c.c_int32, dp, c.c_int32, dp],
                          c.c_int),
@@ -250,6 +251,13 @@ def gfk_profile_read(ctx, reset=True):
     _check(load().gfk_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(ws),
                                    int(bool(reset))), "gfk_profile_read", ctx)
     return ms.value, n.value, ws.value
+
+
+def gfk_kernel_count(ctx, reset=False) -> int:
+    """Kernels gfk_propagate has queued since creation or the last reset of the count."""
+    v = ctypes.c_int64()
+    _check(load().gfk_kernel_count(ctx, ctypes.byref(v), int(bool(reset))), "gfk_kernel_count")
+    return int(v.value)
 
 
 def gfk_reset(ctx):

@@ -111,6 +111,39 @@ def test_batched_mixed_instances_match_single(gfk_lib):
     ctx.close()
 
 
+def test_kind_segments_match_single_instances_and_count_kernels(gfk_lib):
+    """Three instances of three kernel kinds (ground product; 2^3S, whose orbitals
+    have no prefactor terms; P_z), each above the segmentation threshold: the walk
+    runs one specialised launch per instance run, and every instance's walkers and
+    sums equal those of the instance walked alone, bitwise.  gfk_kernel_count counts
+    the kernels exactly: init and its merge, then per chunk three walks and a merge;
+    a CUDA-graph capture counts when it runs."""
+    gfk = gfk_lib
+    specs = [(0, wl.ground(), -2.9037), (1, wl.triplet_2s3(), -2.1752), (1, wl.pz_state(1.0), -2.1238)]
+    descs = [gfk.InstanceDesc(n_walkers=300000, dt=0.005, e_trial=et, seed=2, rng_stream=i, prec=1)
+             for i, (_, _, et) in enumerate(specs)]
+    trials = [(k, p) for (k, p, _) in specs]
+    ctx = gfk.Context(descs, trials=trials, launch=(128, 2))
+    gfk.gfk_kernel_count(ctx.handle, reset=True)
+    ctx.propagate(64)
+    assert gfk.gfk_kernel_count(ctx.handle) == 2 + 3 + 1
+    for i, (k, p, _) in enumerate(specs):
+        with gfk.Context([descs[i]], trials=[(k, p)], launch=(128, 2)) as one:
+            one.propagate(64)
+            for u, v in zip(ctx.walkers(i), one.walkers(0)):
+                np.testing.assert_array_equal(u, v)
+            np.testing.assert_array_equal(ctx.sums(i), one.sums(0))
+    ctx.close()
+    g = gfk.Context(descs[:1], trials=trials[:1], launch=(128, 2))
+    g.set_graph(True)
+    g.propagate(64)                      # captured and run: init + merge + walk + merge
+    assert gfk.gfk_kernel_count(g.handle, reset=True) == 4
+    g.reset()
+    g.propagate(64)                      # replay
+    assert gfk.gfk_kernel_count(g.handle) == 4
+    g.close()
+
+
 def test_autotune_restores_population(gfk_lib):
     """gfk_autotune times every launch shape on the live population and restores it:
     the walk continued after tuning equals an untuned walk."""
