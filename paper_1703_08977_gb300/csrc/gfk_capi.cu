@@ -230,12 +230,21 @@ int mixed_kind(const gfk_ctx* ctx) {
 
 // Launches of one chunk of the mixed walk.  A context of several instances is
 // split into runs of consecutive instances that share the specialised kernel
-// kind, one launch each (a run of one instance also takes its trial function as
-// a launch argument), provided every run has at least kMinSegmentBlocks blocks
-// to fill the GPU; otherwise one launch covers all instances.
+// kind, one launch each, provided every run has at least kMinSegmentBlocks
+// blocks to fill the GPU; otherwise one launch covers all instances.  A launch
+// whose instances all have the same trial function (and e-e switch) takes that
+// function as a launch argument.
 struct WalkSegment {
     int kind, i0, i1;
 };
+
+bool same_trials(const gfk_ctx* ctx, int i0, int i1) {
+    for (int i = i0 + 1; i < i1; ++i)
+        if (std::memcmp(&ctx->trial[i], &ctx->trial[i0], sizeof(TrialHost)) != 0 ||
+            ctx->desc[i].ee_on != ctx->desc[i0].ee_on)
+            return false;
+    return true;
+}
 constexpr int64_t kMinSegmentBlocks = 1024;
 
 std::vector<WalkSegment> walk_segments(const gfk_ctx* ctx, const BlockMap& bm) {
@@ -259,7 +268,7 @@ std::vector<WalkSegment> walk_segments(const gfk_ctx* ctx, const BlockMap& bm) {
 cudaError_t launch_mixed_walks(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, uint32_t step0,
                                int chunk) {
     for (const WalkSegment& g : walk_segments(ctx, bm)) {
-        const bool one = g.i1 - g.i0 == 1;
+        const bool one = same_trials(ctx, g.i0, g.i1);
         const cudaError_t e = launch_walk_mixed(
             g.kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk, bm.begin[g.i0],
             bm.begin[g.i1] - bm.begin[g.i0], ctx->d_inst, bm, ctx->smx, step0, chunk, ctx->part,
@@ -272,7 +281,7 @@ cudaError_t launch_mixed_walks(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, u
 cudaError_t prepare_mixed_walks(const gfk_ctx* ctx, const BlockMap& bm) {
     for (const WalkSegment& g : walk_segments(ctx, bm)) {
         const cudaError_t e = prepare_walk_mixed(g.kind, ctx->noise, ctx->wpt, ctx->threads,
-                                                 g.i1 - g.i0 == 1);
+                                                 same_trials(ctx, g.i0, g.i1));
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

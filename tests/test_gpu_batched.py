@@ -134,6 +134,22 @@ def test_kind_segments_match_single_instances_and_count_kernels(gfk_lib):
                 np.testing.assert_array_equal(u, v)
             np.testing.assert_array_equal(ctx.sums(i), one.sums(0))
     ctx.close()
+    # runs of two instances that share a trial function (different dt): the run's
+    # launch takes that function as its argument; still equal to single instances
+    descs2, trials2 = [], []
+    for i, (k, p, et) in enumerate(specs):
+        for j, dt in enumerate((0.005, 0.01)):
+            descs2.append(gfk.InstanceDesc(n_walkers=150000, dt=dt, e_trial=et, seed=4,
+                                           rng_stream=10 * i + j, prec=1))
+            trials2.append((k, p))
+    ctx2 = gfk.Context(descs2, trials=trials2, launch=(128, 2)).propagate(64)
+    for i in (1, 2, 5):
+        with gfk.Context([descs2[i]], trials=[trials2[i]], launch=(128, 2)) as one:
+            one.propagate(64)
+            for u, v in zip(ctx2.walkers(i), one.walkers(0)):
+                np.testing.assert_array_equal(u, v)
+            np.testing.assert_array_equal(ctx2.sums(i), one.sums(0))
+    ctx2.close()
     g = gfk.Context(descs[:1], trials=trials[:1], launch=(128, 2))
     g.set_graph(True)
     g.propagate(64)                      # captured and run: init + merge + walk + merge
