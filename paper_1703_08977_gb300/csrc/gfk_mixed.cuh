@@ -155,12 +155,12 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     flush_counters(counters, inst, n_nonfinite, n_node, 0u);
 }
 
-// PARAM: the launch covers one instance and its trial function arrives as the
-// kernel argument tk (constant-bank operands, no shared-memory loads, no
-// registers); otherwise each block loads its instance's trial into shared memory
-// (kind 0 then copies its 16 parameters into registers).  The launcher uses
-// PARAM for the orbital-pair kind only: it speeds that kind up by ~11 % and
-// slows the kind-0 walk by ~2 % against the register copy.
+// PARAM: every instance the launch covers has the same trial function, which
+// arrives as the kernel argument tk (constant-bank operands, no shared-memory
+// loads, no registers); otherwise each block loads its instance's trial into
+// shared memory (kind 0 then copies its 16 parameters into registers).  The
+// launcher uses PARAM for the orbital-pair kinds only: it speeds them up by
+// ~11 % and slows the kind-0 walk by ~2 % against the register copy.
 template <int KIND, int WPT, int NOISE, bool PARAM>
 __global__ void __launch_bounds__(kMaxThreads)
 walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
@@ -208,7 +208,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     bool valid[WPT];
     float x[WPT][6], b[WPT][6];
     double L[WPT];
-    float dsh[WPT], S[WPT], comp[WPT];
+    float dsh[WPT], S[WPT], comp[WPT];   // dsh: (L - c) log2(e), formed at each fold
     int sg[WPT];
 #pragma unroll
     for (int k = 0; k < WPT; ++k) {
@@ -245,7 +245,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     double c = warp_max(lmax);
     c = isfinite(c) ? floor(c) : 0.0;      // integer-valued shift
 #pragma unroll
-    for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) : 0.f;
+    for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) * kLog2e : 0.f;
     int fold_len = 0;
     int buf = 0;
 
@@ -296,7 +296,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             const float tsum = S[k] + y;
             comp[k] = (tsum - S[k]) - y;
             S[k] = tsum;
-            const float w = stay ? ex2_approx(fmaf(-S[k], dt_log2e, dsh[k] * kLog2e)) : 0.f;
+            const float w = stay ? ex2_approx(fmaf(-S[k], dt_log2e, dsh[k])) : 0.f;
             const float we = w * el;
             q0 += w;
             q1 += we;
@@ -358,7 +358,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             c = warp_max(lmax);
             c = isfinite(c) ? floor(c) : 0.0;
 #pragma unroll
-            for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) : 0.f;
+            for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) * kLog2e : 0.f;
             // one barrier per window: the other buffer takes the next window,
             // and nobody writes this one again before the next barrier
             __syncthreads();
