@@ -180,3 +180,26 @@ def test_autotune_restores_population(gfk_lib):
         np.testing.assert_allclose(a.energy(i)["E"], b.energy(i)["E"], rtol=2e-6)
     a.close()
     b.close()
+
+
+def test_maximum_instance_count(gfk_lib):
+    """GFK_MAX_INSTANCES (64) instances of both trial families, uneven sizes (1 to 900
+    walkers, so the launch dispatches per block), 70 moves: every instance equals the
+    same instance walked alone."""
+    gfk = gfk_lib
+    rng = np.random.default_rng(8)
+    sizes = rng.integers(1, 900, 64)
+    fams = [(0, wl.ground(), -2.9), (1, wl.triplet_2s3(), -2.17), (1, wl.pz_state(1.0), -2.12)]
+    descs, trials = [], []
+    for i, n in enumerate(sizes):
+        k, p, et = fams[i % 3]
+        descs.append(gfk.InstanceDesc(n_walkers=int(n), dt=0.01, e_trial=et, seed=3, rng_stream=i,
+                                      prec=1))
+        trials.append((k, p))
+    with gfk.Context(descs, trials=trials) as ctx:
+        ctx.propagate(70)
+        for i in (0, 1, 2, 31, 62, 63):
+            with gfk.Context([descs[i]], trials=[trials[i]]) as one:
+                one.propagate(70)
+                for u, v in zip(ctx.walkers(i), one.walkers(0)):
+                    np.testing.assert_array_equal(u, v)

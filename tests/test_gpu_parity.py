@@ -325,3 +325,28 @@ def test_full_size_sampled_walkers_match_oracle(gfk_lib, noise, dt):
     assert np.median(dx32) < 1e-4 and dx32.max() < 1e-2, (np.median(dx32), dx32.max())
     assert np.abs(e32 - e64).max() < 2e-7, np.abs(e32 - e64).max()
     np.testing.assert_array_equal(n32, n64)
+
+
+def test_large_population_sampled_against_oracle(gfk_lib):
+    """2^24 walkers (65536 blocks of the mixed walk), 16 moves on both paths: walkers
+    sampled across the whole id range (the last one included) match the oracle, the
+    FP64 path to 1e-12 and the mixed path at FP32 distance with the same kills."""
+    gfk = gfk_lib
+    n, moves, dt, et = 1 << 24, 16, 0.005, -2.9037
+    p = wl.triplet_2s3()
+    ids = np.array([0, 255, 256, 1 << 20, (1 << 23) + 7, n - 257, n - 1], dtype=np.uint32)
+    out = {}
+    for prec in (0, 1):
+        d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=et, seed=12, prec=prec)
+        with gfk.Context([d], trials=[(1, p)]) as ctx:
+            ctx.propagate(moves)
+            x, lw, al = ctx.walkers(0)
+            out[prec] = (x[ids].copy(), lw[ids].copy(), al[ids].copy())
+            del x, lw, al
+    w = oracle.Walk(1, p, ids=ids, dt=dt, e_trial=et, seed=12).advance(moves)
+    x64, lw64, al64 = out[0]
+    np.testing.assert_array_equal(al64.astype(bool), w.alive.astype(bool))
+    assert (np.abs(x64 - w.x).max(axis=1) / np.maximum(1.0, np.abs(w.x).max(axis=1))).max() <= REL_WALKER
+    x32, lw32, al32 = out[1]
+    np.testing.assert_array_equal(al32.astype(bool), w.alive.astype(bool))
+    assert np.abs(x32 - w.x).max() < 1e-4
