@@ -228,8 +228,14 @@ static __global__ void adj_terminal_final_kernel(const double* __restrict__ part
 
 // The reverse sweep: one thread per walker, all segments from the last to the
 // first; per block the summed parameter adjoint theta_bar.
+// Blocks per SM the reverse sweep is compiled for: the FP32 sweep runs 4
+// (128 registers, a small spill; +8 % over the 2 blocks its 250 registers
+// allowed), the FP64 one keeps the default.
 template <typename T>
-__global__ void __launch_bounds__(kAdjThreads)
+constexpr int adj_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
+
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
 adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, int J,
                     int loss_kind, const T* __restrict__ ckpt, T* __restrict__ seg,
                     const double* __restrict__ ew, const AdjTerminal* __restrict__ term,
