@@ -206,7 +206,8 @@ class OraclePool:
     """Spawned worker processes (spawn: the parent may already hold a CUDA context)."""
 
     def __init__(self, n=None):
-        self.n = n or max(1, os.cpu_count() or 1)
+        # one process per host core, at most 64 (start-up cost on very large hosts)
+        self.n = n or max(1, min(64, os.cpu_count() or 1))
 
     def __enter__(self):
         import multiprocessing as mp
