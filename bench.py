@@ -81,8 +81,8 @@ LANES_PER_SM_CLK = 128
 # threads x 2 walkers, the launch shape the bench autotunes to), valid only for the kernel sources it was taken
 # on (sha256 prefix of csrc/*); scaled by the walker-steps of an average launch.
 WALK_TRAFFIC = {       # workload -> capture
-    "ground": {"src_sha": "3d7460c2e279c378", "bytes_per_walker_step": 0.19942},
-    "bernoulli": {"src_sha": "3d7460c2e279c378", "bytes_per_walker_step": 0.20099},
+    "ground": {"src_sha": "18ecb83af849efa6", "bytes_per_walker_step": 0.20015},
+    "bernoulli": {"src_sha": "18ecb83af849efa6", "bytes_per_walker_step": 0.19923},
 }
 
 
