@@ -81,16 +81,23 @@ LANES_PER_SM_CLK = 128
 # threads x 2 walkers, the launch shape the bench autotunes to), valid only for the kernel sources it was taken
 # on (sha256 prefix of csrc/*); scaled by the walker-steps of an average launch.
 WALK_TRAFFIC = {       # workload -> capture
-    "ground": {"src_sha": "18ecb83af849efa6", "bytes_per_walker_step": 0.20015},
-    "bernoulli": {"src_sha": "18ecb83af849efa6", "bytes_per_walker_step": 0.19923},
+    "ground": {"src_sha": "4d79c24c4dfe14b8", "bytes_per_walker_step": 0.20015},
+    "bernoulli": {"src_sha": "4d79c24c4dfe14b8", "bytes_per_walker_step": 0.19923},
 }
+
+
+# Sources the mixed walk kernel is compiled from; a captured traffic figure
+# holds only while they are unchanged.
+WALK_SOURCES = ("paper_1703_08977_gb300/csrc/gfk_mixed.cuh", "paper_1703_08977_gb300/csrc/gfk_mixed.cu",
+                "paper_1703_08977_gb300/csrc/gfk_mixed_bern.cu", "paper_1703_08977_gb300/csrc/gfk_device.cuh",
+                "paper_1703_08977_gb300/csrc/gfk_block.cuh", "paper_1703_08977_gb300/csrc/gfk_types.h",
+                "paper_1703_08977_gb300/csrc/gfk_launch.h", "include/gfk.h")
 
 
 def _src_sha() -> str:
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1703_08977_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
+    for f in WALK_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -243,6 +243,9 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
     typedef Dual<kNumTangents, T> D;
     __shared__ TrialDev<T> s_trial;
     __shared__ double s_red[kNumTheta][kAdjThreads / 32];
+    // Per-thread FP64 parameter adjoints, updated once per segment from the
+    // segment's sums in T (kept here rather than in registers).
+    __shared__ double s_theta[kNumTheta][kAdjThreads];
     if (threadIdx.x == 0) load_trial<T>(inst->trial, inst->ee_on, s_trial);
     __syncthreads();
     TrialDev0<D> td;
@@ -252,9 +255,9 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
     adj_steps(inst, dt, sdt);
     const bool bern = inst->noise == GFK_NOISE_BERNOULLI;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double theta[kNumTheta];
+    double* theta = &s_theta[0][threadIdx.x];   // theta[k * kAdjThreads]
 #pragma unroll
-    for (int k = 0; k < kNumTheta; ++k) theta[k] = 0.0;
+    for (int k = 0; k < kNumTheta; ++k) theta[k * kAdjThreads] = 0.0;
 
     if (i < n) {
         const AdjTerminal tr = *term;
@@ -299,6 +302,9 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 }
                 // sweep it backwards
                 const int n_top = (j == J - 1) ? n_hi : n_hi - 1;
+                T tseg[kNumTheta];
+#pragma unroll
+                for (int k = 0; k < kNumTheta; ++k) tseg[k] = T(0);
                 for (int m = n_top; m >= n_lo; --m) {
                     T xv[6];
                     PosIO<T>::load(seg + (int64_t)(m - n_lo) * PosIO<T>::kWords * n, n, i, xv);
@@ -317,14 +323,16 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
 #pragma unroll
                     for (int d = 0; d < 6; ++d) lambda[d] += phi.d[d];
 #pragma unroll
-                    for (int k = 0; k < kNumTheta; ++k) theta[k] += (double)phi.d[6 + k];
+                    for (int k = 0; k < kNumTheta; ++k) tseg[k] += phi.d[6 + k];
                 }
+#pragma unroll
+                for (int k = 0; k < kNumTheta; ++k) theta[k * kAdjThreads] += (double)tseg[k];
             }
         }
     }
 #pragma unroll
     for (int k = 0; k < kNumTheta; ++k) {
-        const double v = warp_sum(theta[k]);
+        const double v = warp_sum(theta[k * kAdjThreads]);
         if ((threadIdx.x & 31) == 0) s_red[k][threadIdx.x >> 5] = v;
     }
     __syncthreads();

@@ -14,7 +14,9 @@
 // is what bounds this kernel here.  Q and R (effective sample size, variance)
 // are plain FP64 sums;
 // n is an integer count, exact in FP64.  The shifts c_b are integer-valued, so
-// a thread recomputes the factor e^{c_b - C} only when the integer changes.
+// the factors e^{c_b - C} for C - c_b < kExpTable come from a table the block
+// fills once with the same exp calls (the FP64 exponential per record was what
+// bounded this kernel); larger or non-integer gaps call exp directly.
 // finalize_kernel turns merged rows into E(t) = P/W, ln z(t) = C + ln W - ln N
 // and ESS = W^2/Q (Eq. 4's z(t) and the space-averaged energy).
 #include <cuda_runtime.h>
@@ -44,6 +46,7 @@ __device__ __forceinline__ DD dd_shfl_xor(DD v, int o) {
 }
 
 constexpr int kReduceThreads = 256;
+constexpr int kExpTable = 64;   // e^{-k}, k = 0 .. kExpTable - 1
 
 template <bool COMP>
 __global__ void __launch_bounds__(kReduceThreads)
@@ -51,6 +54,8 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
                    SeriesRow* __restrict__ series, int64_t series_cap, int64_t row_base) {
     __shared__ double s_max[kReduceThreads / 32];
     __shared__ DD s_acc[5][kReduceThreads / 32];
+    __shared__ double s_exp[kExpTable];
+    if (threadIdx.x < kExpTable) s_exp[threadIdx.x] = exp(-(double)threadIdx.x);
     const int row = blockIdx.x;
     const int inst = blockIdx.y;
     const int b0 = bm.begin[inst], b1 = bm.begin[inst + 1];
@@ -69,15 +74,13 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
 
     // per-thread Neumaier sums for W and P, plain sums for Q, R, n
     double sW = 0.0, cW = 0.0, sP = 0.0, cP = 0.0, sQ = 0.0, sR = 0.0, sN = 0.0;
-    double last_k = -1.0, f = 0.0;
     for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
         const PartialRec r = rp[b];
         if (!(r.n > 0.0)) continue;
         const double k = C - r.c;
-        if (k != last_k) {
-            f = exp(-k);
-            last_k = k;
-        }
+        double f;
+        if (k >= 0.0 && k < (double)kExpTable && (double)(int)k == k) f = s_exp[(int)k];
+        else f = exp(-k);
         const double w = r.W * f, p = r.P * f;
         if (COMP) {
             double t = sW + w;
