@@ -16,8 +16,8 @@
 
 #include "gfk_launch.h"
 #include "gfk_mixed_consts.h"
+#include "gfk_trial_parse.h"
 #include "gfk_types.h"
-
 
 using namespace gfk;
 
@@ -159,41 +159,7 @@ struct DeviceGuard {
 bool finite_d(double v) { return std::isfinite(v); }
 
 gfk_status parse_trial(int kind, const double* p, int np, TrialHost* t) {
-    std::memset(t, 0, sizeof(*t));
-    if (!p) return GFK_EINVAL;
-    for (int i = 0; i < np; ++i)
-        if (!finite_d(p[i])) return GFK_EINVAL;
-    t->kind = kind;
-    if (kind == GFK_TRIAL_JASTROW_PRODUCT) {
-        if (np < 3 || np > 7) return GFK_EINVAL;
-        t->Z = p[0];
-        t->a = p[1];
-        t->beta = p[2];
-        for (int k = 0; k < 4; ++k) t->ck[k] = (3 + k < np) ? p[3 + k] : 0.0;
-        t->nterms = 1;
-        if (!(t->Z > 0.0) || t->beta < 0.0) return GFK_EINVAL;
-        return GFK_OK;
-    }
-    if (kind == GFK_TRIAL_ORBITAL_PAIRS) {
-        if (np < 7) return GFK_EINVAL;
-        t->a = p[0];
-        t->beta = p[1];
-        for (int k = 0; k < 4; ++k) t->ck[k] = p[2 + k];
-        const double ntd = p[6];
-        const int nt = (int)ntd;
-        if ((double)nt != ntd || nt < 1 || nt > GFK_MAX_TERMS || np != 7 + 9 * nt) return GFK_EINVAL;
-        if (t->beta < 0.0) return GFK_EINVAL;
-        t->nterms = nt;
-        for (int i = 0; i < nt; ++i) {
-            const double* q = p + 7 + 9 * i;
-            t->s[i] = q[0];
-            t->alpha[i][0] = q[1]; t->c0[i][0] = q[2]; t->c1[i][0] = q[3]; t->cz[i][0] = q[4];
-            t->alpha[i][1] = q[5]; t->c0[i][1] = q[6]; t->c1[i][1] = q[7]; t->cz[i][1] = q[8];
-            if (t->alpha[i][0] < 0.0 || t->alpha[i][1] < 0.0) return GFK_EINVAL;
-        }
-        return GFK_OK;
-    }
-    return GFK_EINVAL;
+    return parse_trial_params(kind, p, np, t) ? GFK_OK : GFK_EINVAL;
 }
 
 int64_t blocks_for(int64_t n, int threads, int wpt) {

@@ -26,6 +26,7 @@
 
 #include "gfk_launch.h"
 #include "gfk_mixed_consts.h"
+#include "gfk_trial_parse.h"
 #include "gfk_types.h"
 
 
@@ -63,42 +64,6 @@ gfk_status scratch_address(int dev, unsigned char** out) {
     return GFK_OK;
 }
 
-bool parse_trial_noalloc(int kind, const double* p, int np, TrialHost* t) {
-    std::memset(t, 0, sizeof(*t));
-    if (!p) return false;
-    for (int i = 0; i < np; ++i)
-        if (!std::isfinite(p[i])) return false;
-    t->kind = kind;
-    if (kind == GFK_TRIAL_JASTROW_PRODUCT) {
-        if (np < 3 || np > 7) return false;
-        t->Z = p[0];
-        t->a = p[1];
-        t->beta = p[2];
-        for (int k = 0; k < 4; ++k) t->ck[k] = (3 + k < np) ? p[3 + k] : 0.0;
-        t->nterms = 1;
-        return t->Z > 0.0 && t->beta >= 0.0;
-    }
-    if (kind == GFK_TRIAL_ORBITAL_PAIRS) {
-        if (np < 7) return false;
-        t->a = p[0];
-        t->beta = p[1];
-        for (int k = 0; k < 4; ++k) t->ck[k] = p[2 + k];
-        const int nt = (int)p[6];
-        if ((double)nt != p[6] || nt < 1 || nt > GFK_MAX_TERMS || np != 7 + 9 * nt) return false;
-        if (t->beta < 0.0) return false;
-        t->nterms = nt;
-        for (int i = 0; i < nt; ++i) {
-            const double* q = p + 7 + 9 * i;
-            t->s[i] = q[0];
-            t->alpha[i][0] = q[1]; t->c0[i][0] = q[2]; t->c1[i][0] = q[3]; t->cz[i][0] = q[4];
-            t->alpha[i][1] = q[5]; t->c0[i][1] = q[6]; t->c1[i][1] = q[7]; t->cz[i][1] = q[8];
-            if (t->alpha[i][0] < 0.0 || t->alpha[i][1] < 0.0) return false;
-        }
-        return true;
-    }
-    return false;
-}
-
 }  // namespace
 
 extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32_t trial_kind,
@@ -121,7 +86,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     if (step0 + n_steps > 0xffffffffll) return GFK_EINVAL;
     if (((uintptr_t)dev_p0 | (uintptr_t)dev_p1) & 15u) return GFK_EINVAL;
     TrialHost trial;
-    if (!parse_trial_noalloc(trial_kind, params, n_params, &trial)) return GFK_EINVAL;
+    if (!parse_trial_params(trial_kind, params, n_params, &trial)) return GFK_EINVAL;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GFK_ECUDA;
