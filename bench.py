@@ -79,10 +79,10 @@ LANES_PER_SM_CLK = 128
 # DRAM traffic (read + write) of the walk kernel per walker-step, from one ncu
 # capture of a launch of the bench's shape (2^20 walkers x 1024 moves, 128
 # threads x 2 walkers, the launch shape the bench autotunes to), valid only for the kernel sources it was taken
-# on (sha256 prefix of csrc/*); scaled by the walker-steps of an average launch.
+# on (sha256 prefix of WALK_SOURCES); scaled by the walker-steps of an average launch.
 WALK_TRAFFIC = {       # workload -> capture
-    "ground": {"src_sha": "4d79c24c4dfe14b8", "bytes_per_walker_step": 0.20015},
-    "bernoulli": {"src_sha": "4d79c24c4dfe14b8", "bytes_per_walker_step": 0.19923},
+    "ground": {"src_sha": "da2fabf5c8f7aa4c", "bytes_per_walker_step": 0.20028},
+    "bernoulli": {"src_sha": "da2fabf5c8f7aa4c", "bytes_per_walker_step": 0.19995},
 }
 
 

@@ -1116,7 +1116,8 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
         if (e == cudaSuccess)
             e = f64 ? launch_walk_fp64(kind, ctx->noise, shape.threads, (int)nblk, d_inst, bm, s64,
                                        (uint32_t)(j * K), steps, part, cnt, ctx->stream)
-                    : launch_walk_mixed(kind, ctx->noise, shape.wpt, shape.threads, (int)nblk, 0,
+                    : launch_walk_mixed(mixed_walk_kind(kind, &ctx->trial[inst], 1), ctx->noise,
+                                        shape.wpt, shape.threads, (int)nblk, 0,
                                         (int)nblk,
                                         d_inst, bm, smx, (uint32_t)(j * K), steps, part, cnt,
                                         &ctx->trial[inst], ctx->desc[inst].ee_on, ctx->stream);

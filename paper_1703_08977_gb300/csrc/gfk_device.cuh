@@ -407,13 +407,19 @@ struct JastrowOut { R up, upp, jee; };
 
 // Whether the Jastrow polynomial terms are present (a block-uniform branch);
 // the dual-number parameter set always carries them (their derivatives are
-// wanted even where the coefficients are zero).
+// wanted even where the coefficients are zero).  The evaluators below are
+// compiled for POLY = 0 (no polynomial terms) or 1 (with them); POLY = -1
+// selects one of the two at run time with a single branch at the top, so every
+// kernel evaluates a given trial function with the same arithmetic.  The
+// specialised mixed walk kernels pass POLY = 0 (their launcher gives them
+// polynomial-free trial functions only): the branch then disappears from the
+// move loop, which lets the compiler interleave a thread's walkers across it.
 template <typename R>
 __device__ __forceinline__ bool has_poly(const TrialDev<R>& t) { return t.poly != 0; }
 template <typename TD>
 __device__ __forceinline__ bool has_poly(const TD&) { return true; }
 
-template <typename R, typename TD>
+template <typename R, typename TD, int POLY>
 __device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
     R q = R(1) + t.beta * r12;
     R iq = rcp(q);
@@ -422,7 +428,7 @@ __device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
     R d2rho = R(-2) * t.beta * drho * iq;      // d2 rho / dr2
     JastrowOut<R> o;
     const R jee0 = (t.eem2a * i12 + t.eebeta * (R(2) + t.beta * r12)) * drho;
-    if (has_poly(t)) {
+    if (POLY != 0) {
         R h = t.c2 + rho * (t.c3 + rho * (t.c4 + rho * t.c5));   // (du/drho - a) / rho
         R du = t.a + rho * h;                                   // du / drho
         R d2u = t.d2 + rho * (t.d6 + rho * (t.d12 + rho * t.d20));
@@ -442,8 +448,13 @@ __device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
 //   E_L = (Z - 2)(1/r1 + 1/r2) - Z^2 + (ee - 2u')/r12 - u'' - u'^2
 //         + Z u' (r1_hat - r2_hat) . e12
 // (the nuclear 1/r terms cancel exactly for Z = 2).
-template <typename R, typename TD>
+template <typename R, typename TD, int POLY = -1>
 __device__ __forceinline__ void eval_kind0(const TD& t, const R x[6], EvalOut<R>& o) {
+    if constexpr (POLY < 0) {
+        if (has_poly(t)) eval_kind0<R, TD, 1>(t, x, o);
+        else eval_kind0<R, TD, 0>(t, x, o);
+        return;
+    }
     R s1 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
     R dx = x[0] - x[3], dy = x[1] - x[4], dz = x[2] - x[5];
@@ -453,7 +464,7 @@ __device__ __forceinline__ void eval_kind0(const TD& t, const R x[6], EvalOut<R>
     radius(s2, r2, i2);
     radius(s12, r12, i12);
     R ex = dx * i12, ey = dy * i12, ez = dz * i12;
-    JastrowOut<R> j = jastrow<R>(t, r12, i12);
+    JastrowOut<R> j = jastrow<R, TD, POLY>(t, r12, i12);
     R h1x = x[0] * i1, h1y = x[1] * i1, h1z = x[2] * i1;
     R h2x = x[3] * i2, h2y = x[4] * i2, h2z = x[5] * i2;
     o.b[0] = -t.Z * h1x + j.up * ex;
@@ -542,8 +553,13 @@ __device__ __forceinline__ void kind1_term(const TrialDev<R>& t, int k, R r1, R 
 // UNROLL: the term loops run to GFK_MAX_TERMS with a uniform early exit, so
 // every parameter index is a compile-time constant (for a trial held in the
 // kernel's parameter bank); otherwise they run to t.nterms (fewer registers).
-template <typename R, bool UNROLL = false, bool PLAIN = false>
+template <typename R, bool UNROLL = false, bool PLAIN = false, int POLY = -1>
 __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
+    if constexpr (POLY < 0) {
+        if (has_poly(t)) eval_kind1<R, UNROLL, PLAIN, 1>(t, x, o);
+        else eval_kind1<R, UNROLL, PLAIN, 0>(t, x, o);
+        return;
+    }
     R s1 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     R s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
     R dx = x[0] - x[3], dy = x[1] - x[4], dz = x[2] - x[5];
@@ -593,7 +609,7 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
     const R Phi = acc.Phi, T = acc.T;
     const R* G1 = acc.G1;
     const R* G2 = acc.G2;
-    JastrowOut<R> j = jastrow<R>(t, r12, i12);
+    JastrowOut<R> j = jastrow<R, TrialDev<R>, POLY>(t, r12, i12);
     R iP = rcp(Phi);
     o.b[0] = G1[0] * iP + j.up * ex;
     o.b[1] = G1[1] * iP + j.up * ey;
@@ -610,12 +626,13 @@ __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], E
 // KIND 0 / 1 select the family at compile time; KIND 2 dispatches on t.kind
 // (used when one launch covers instances of both families); KIND 3 is the
 // orbital-pair family whose orbitals all lack the r and z prefactor terms
-// (the mixed walk's launcher picks it when every instance qualifies).
-template <int KIND, typename R, bool UNROLL = false>
+// (the mixed walk's launcher picks it when every instance qualifies).  POLY as
+// for jastrow (KIND 2 always decides at run time).
+template <int KIND, typename R, bool UNROLL = false, int POLY = -1>
 __device__ __forceinline__ void eval_trial(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
-    if (KIND == 0) eval_kind0<R>(t, x, o);
-    else if (KIND == 1) eval_kind1<R, UNROLL>(t, x, o);
-    else if (KIND == 3) eval_kind1<R, UNROLL, true>(t, x, o);
+    if (KIND == 0) eval_kind0<R, TrialDev<R>, POLY>(t, x, o);
+    else if (KIND == 1) eval_kind1<R, UNROLL, false, POLY>(t, x, o);
+    else if (KIND == 3) eval_kind1<R, UNROLL, true, POLY>(t, x, o);
     else if (t.kind == 0) eval_kind0<R>(t, x, o);
     else eval_kind1<R>(t, x, o);
 }

@@ -18,8 +18,9 @@ cudaError_t launch_walk_fp64(int kind, int noise, int threads, int nblk, const I
 cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
                               const BlockMap& bm, const StateMixed& st, PartialRec* part,
                               unsigned long long* counters, cudaStream_t stream);
-// kind: 0 / 1 the trial family, 2 both in one launch, 3 orbital pairs whose
-// orbitals all lack the r and z prefactor terms (mixed_walk_kind).
+// kind: 0 / 1 the trial family, 2 both in one launch (or any trial function
+// with Jastrow polynomial terms), 3 orbital pairs whose orbitals all lack the
+// r and z prefactor terms (mixed_walk_kind).
 // one_trial: when the launch covers a single instance, its trial function (and
 // ee_on); the kernel then takes it as a launch argument.  NULL otherwise.
 // nblk: all blocks of the context (the records' stride); the launch runs
@@ -29,10 +30,15 @@ cudaError_t launch_walk_mixed(int kind, int noise, int wpt, int threads, int nbl
                               const StateMixed& st, uint32_t step0, int nsteps, PartialRec* part,
                               unsigned long long* counters, const TrialHost* one_trial,
                               int ee_on, cudaStream_t stream);
-// The mixed walk's kind for these trial functions: 3 when every one is an
-// orbital-pair function whose orbitals have no r or z prefactor terms
-// (c1 = cz = 0 in every used term), else `kind` unchanged.
+// The mixed walk's kind for these trial functions.  The specialised kinds 0,
+// 1 and 3 are compiled for trial functions without Jastrow polynomial terms,
+// so a set with any c_k != 0 takes the per-block dispatch (2).  Otherwise 3
+// when every one is an orbital-pair function whose orbitals have no r or z
+// prefactor terms (c1 = cz = 0 in every used term), else `kind` unchanged.
 inline int mixed_walk_kind(int kind, const TrialHost* trials, int n) {
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 4; ++k)
+            if (trials[i].ck[k] != 0.0) return 2;
     if (kind != GFK_TRIAL_ORBITAL_PAIRS) return kind;
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < trials[i].nterms; ++k)

@@ -183,6 +183,9 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     TrialDev<float> t_local;
     if (!PARAM && KIND == 0) t_local = s_trial;
     const TrialDev<float>& t = PARAM ? tk : ((KIND == 0) ? t_local : s_trial);
+    // the specialised kinds run trial functions without Jastrow polynomial
+    // terms only (mixed_walk_kind); the per-block dispatch handles the rest
+    constexpr int kPoly = KIND == 2 ? -1 : 0;
 
     // FP32 time step, noise scale and radius constant chosen on the host so the
     // diffusion matches the drift, and the other derived constants, all formed
@@ -229,7 +232,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         if (valid[k]) load_mixed(st, slot[k], x[k], L[k], sg[k]);
         if (sg[k] != 0) {
             EvalOut<float> ev;
-            eval_trial<KIND, float, PARAM>(t, x[k], ev);
+            eval_trial<KIND, float, PARAM, kPoly>(t, x[k], ev);
 #pragma unroll
             for (int d = 0; d < 6; ++d) b[k][d] = ev.b[d];
         }
@@ -272,7 +275,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                 xn[d] = NOISE == 1 ? move_bern_f32(x[k][d], b[k][d], xi[d], xlo[d], dt)
                                    : move_gauss_f32(x[k][d], b[k][d], xi[d], dt, sdt);
             EvalOut<float> ev;
-            eval_trial<KIND, float, PARAM>(t, xn, ev);
+            eval_trial<KIND, float, PARAM, kPoly>(t, xn, ev);
             // a non-finite position is a non-finite kill, then a sign change a
             // node kill, then a non-finite drift or local energy (a position that
             // is not finite makes E_L not finite, so the position itself is only
