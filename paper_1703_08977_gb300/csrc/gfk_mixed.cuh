@@ -63,29 +63,44 @@ __device__ __forceinline__ void load_mixed(const StateMixed& st, int64_t slot, f
     sg = st.sgn[slot];
 }
 
-// Philox words of one move.  The even move of a pair runs the blocks of tags
-// 0 and 1 and keeps tag 1's last two words (carry) for the odd move, which
-// runs tag 2 (and tag 1 again when the launch starts on an odd move).
-__device__ __forceinline__ void pair_move_words(const PhiloxPre& pre, uint32_t carry[2],
-                                                uint32_t step, bool first, uint32_t k0,
-                                                uint32_t k1, uint32_t words[6]) {
+// The Philox words of one move for all WPT walkers of a thread.  The even
+// move of a pair runs the blocks of tags 0 and 1 and keeps tag 1's last two
+// words (carry) for the odd move, which runs tag 2 (and tag 1 again when the
+// launch starts on an odd move).  The even / odd branch is taken once for all
+// walkers, so the walkers' moves that follow are one branch-free stretch the
+// compiler can interleave.
+template <int WPT>
+__device__ __forceinline__ void pair_move_words_all(const PhiloxPre (&pre)[WPT],
+                                                    uint32_t (&carry)[WPT][2], uint32_t step,
+                                                    bool first, uint32_t k0, uint32_t k1,
+                                                    uint32_t (&words)[WPT][6]) {
     const uint32_t m = step >> 1;
     if ((step & 1u) == 0u) {
-        Words4 wa, wb;
-        philox10_pair(pre, m, k0, k1, wa, wb);
-        words[0] = wa.w[0]; words[1] = wa.w[1]; words[2] = wa.w[2]; words[3] = wa.w[3];
-        words[4] = wb.w[0]; words[5] = wb.w[1];
-        carry[0] = wb.w[2];
-        carry[1] = wb.w[3];
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            Words4 wa, wb;
+            philox10_pair(pre[k], m, k0, k1, wa, wb);
+            words[k][0] = wa.w[0]; words[k][1] = wa.w[1]; words[k][2] = wa.w[2];
+            words[k][3] = wa.w[3]; words[k][4] = wb.w[0]; words[k][5] = wb.w[1];
+            carry[k][0] = wb.w[2];
+            carry[k][1] = wb.w[3];
+        }
     } else {
         if (first) {
-            const Words4 wb = philox10_tag(pre, m, 1u, k0, k1);
-            carry[0] = wb.w[2];
-            carry[1] = wb.w[3];
+#pragma unroll
+            for (int k = 0; k < WPT; ++k) {
+                const Words4 wb = philox10_tag(pre[k], m, 1u, k0, k1);
+                carry[k][0] = wb.w[2];
+                carry[k][1] = wb.w[3];
+            }
         }
-        const Words4 wc = philox10_tag(pre, m, 2u, k0, k1);
-        words[0] = carry[0]; words[1] = carry[1];
-        words[2] = wc.w[0]; words[3] = wc.w[1]; words[4] = wc.w[2]; words[5] = wc.w[3];
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            const Words4 wc = philox10_tag(pre[k], m, 2u, k0, k1);
+            words[k][0] = carry[k][0]; words[k][1] = carry[k][1];
+            words[k][2] = wc.w[0]; words[k][3] = wc.w[1]; words[k][4] = wc.w[2];
+            words[k][5] = wc.w[3];
+        }
     }
 }
 
@@ -256,24 +271,31 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         const uint32_t step = step0 + (uint32_t)s;
         float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
         unsigned na = 0;
-        // every walker slot runs the same instructions (dead or past the end
-        // included) so the compiler can interleave the WPT walkers; only the
-        // commit of the new state is predicated
+        // Gaussian noise: the normals of all WPT walkers first (the Philox
+        // words under one even / odd branch), so the moves that follow are one
+        // branch-free stretch (+2.4 % against drawing each walker's words in
+        // its own iteration); the Bernoulli steps, branch-free already, are
+        // drawn per walker (0.6 % faster there).  Every walker slot runs the
+        // same instructions (dead or past the end included) so the compiler
+        // can interleave the WPT walkers; only the commit of the new state is
+        // predicated.
+        float xi[WPT][6], xlo[WPT][6];
+        if (NOISE == 0) {
+            uint32_t words[WPT][6];
+            pair_move_words_all<WPT>(pre, carry, step, s == 0, k0, k1, words);
+#pragma unroll
+            for (int k = 0; k < WPT; ++k) normals6_f32(words[k], xi[k], r2_fix);
+        }
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
             const bool alive = sg[k] != 0;
-            float xi[6], xlo[6], xn[6];
-            if (NOISE == 1) {
-                bernoulli6_steps(lcg[k], sdt, sdt_lo, xi, xlo);   // +-sdt, +-sdt_lo
-            } else {
-                uint32_t words[6];
-                pair_move_words(pre[k], carry[k], step, s == 0, k0, k1, words);
-                normals6_f32(words, xi, r2_fix);
-            }
+            float xn[6];
+            if (NOISE == 1)
+                bernoulli6_steps(lcg[k], sdt, sdt_lo, xi[k], xlo[k]);   // +-sdt, +-sdt_lo
 #pragma unroll
             for (int d = 0; d < 6; ++d)
-                xn[d] = NOISE == 1 ? move_bern_f32(x[k][d], b[k][d], xi[d], xlo[d], dt)
-                                   : move_gauss_f32(x[k][d], b[k][d], xi[d], dt, sdt);
+                xn[d] = NOISE == 1 ? move_bern_f32(x[k][d], b[k][d], xi[k][d], xlo[k][d], dt)
+                                   : move_gauss_f32(x[k][d], b[k][d], xi[k][d], dt, sdt);
             EvalOut<float> ev;
             eval_trial<KIND, float, PARAM, kPoly>(t, xn, ev);
             // a non-finite position is a non-finite kill, then a sign change a
