@@ -299,11 +299,11 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             EvalOut<float> ev;
             eval_trial<KIND, float, PARAM, kPoly>(t, xn, ev);
             // a non-finite position is a non-finite kill, then a sign change a
-            // node kill, then a non-finite drift or local energy (a position that
-            // is not finite makes E_L not finite, so the position itself is only
-            // examined in the rare case that the sign test fires)
-            bool node = ev.sign != sg[k];
-            if (node) node = finite_(((xn[0] + xn[1]) + (xn[2] + xn[3])) + (xn[4] + xn[5]));
+            // node kill, then a non-finite drift or local energy (the position
+            // test runs every move, without a branch: +0.4 to +1.3 % against
+            // testing it only after a sign change, bitwise the same)
+            const bool node = (ev.sign != sg[k]) &
+                              finite_(((xn[0] + xn[1]) + (xn[2] + xn[3])) + (xn[4] + xn[5]));
             const bool fin = eval_finite(ev);
             const bool stay = alive && !node && fin;
             n_coal += (alive && ev.rmin < 1e-5f) ? 1u : 0u;
