@@ -14,8 +14,10 @@
 // this recursion, with phi_n = dt lambda_{n+1} . b(X_n) [n < S]
 // - gamma dt E_L(X_n) [n >= 1] + alpha E_L(X_n) [n = S], is
 //   lambda_n = lambda_{n+1} + grad_X phi_n,   theta_bar += grad_theta phi_n,
-// for n = S down to 0.  One forward-mode dual evaluation of the trial function
-// at X_n (6 position tangents + 7 parameter tangents) gives both gradients.
+// for n = S down to 0.  phi_n is one scalar, w . b(X_n) + w_E E_L(X_n), so a
+// reverse-mode pass through the trial evaluation (adj_grad_kind0: the
+// evaluation's statements, then their adjoints in reverse order) gives both
+// gradients, 6 + 7 numbers, at a few times the cost of the evaluation.
 //
 // Positions are not stored for the whole walk: the forward keeps them every K
 // moves (checkpoints), and the backward recomputes each K-move segment from
@@ -27,14 +29,12 @@
 #include <cuda_runtime.h>
 
 #include "gfk_device.cuh"
-#include "gfk_dual.cuh"
 #include "gfk_types.h"
 
 namespace gfk {
 
 constexpr int kAdjThreads = 128;
 constexpr int kNumTheta = 7;                  // kind 0: Z, a, beta, c1..c4
-constexpr int kNumTangents = 6 + kNumTheta;
 
 // Terminal quantities shared by every walker: {c, W, L, Var, loss}.
 struct AdjTerminal {
@@ -110,23 +110,124 @@ __device__ __forceinline__ void adj_steps(const InstDev* inst, float& dt, float&
     sdt = inst->sdt_f32;
 }
 
+// Reverse-mode gradient of phi = w . b(X) + wE E_L(X) for the kind-0 trial
+// psi = exp(-Z r1 - Z r2 + u(r12)), u = a rho + sum_k c_k rho^{k+1} (the
+// evaluation of eval_kind0 with the polynomial terms, whose derivatives are
+// wanted even where the c_k vanish): xbar = d phi / dX and
+// thbar = d phi / d(Z, a, beta, c1, c2, c3, c4).  The forward statements come
+// first, as eval_kind0 and jastrow write them:
+//   d = r1_vec - r2_vec, (r, 1/r) of |x1|^2, |x2|^2, |d|^2, e = d / r12,
+//   h1 = x1 / r1, h2 = x2 / r2, q = 1 + beta r12, iq = 1/q, rho = r12 iq,
+//   drho = iq^2, d2rho = -2 beta drho iq,
+//   A = (ee - 2a) / r12 + ee beta (2 + beta r12), jee = A drho - 2 hh drho iq,
+//   hh = 2c1 + 3c2 rho + 4c3 rho^2 + 5c4 rho^3, du = a + rho hh,
+//   d2u = 2c1 + 6c2 rho + 12c3 rho^2 + 20c4 rho^3,
+//   up = du drho, upp = d2u drho^2 + du d2rho,
+//   b1 = -Z h1 + up e, b2 = -Z h2 - up e, proj = (h1 - h2) . e,
+//   E_L = (Z - 2)(1/r1 + 1/r2) - Z^2 + jee - upp - up^2 + Z up proj;
+// then the adjoint of each statement, last to first (a suffix b marks the
+// derivative of phi with respect to that quantity).
 template <typename T>
-__device__ __forceinline__ void load_trial0_dual(const TrialHost& h, int ee_on,
-                                                 TrialDev0<Dual<kNumTangents, T>>& t) {
-    typedef Dual<kNumTangents, T> D;
-    const T ee = ee_on ? T(1) : T(0);
-    t.Z = D::seed((T)h.Z, 6);
-    t.a = D::seed((T)h.a, 7);
-    t.beta = D::seed((T)h.beta, 8);
-    const D c1 = D::seed((T)h.ck[0], 9), c2 = D::seed((T)h.ck[1], 10);
-    const D c3 = D::seed((T)h.ck[2], 11), c4 = D::seed((T)h.ck[3], 12);
-    t.Zm2 = t.Z - T(2);
-    t.Z2 = t.Z * t.Z;
-    t.ee = D(ee);
-    t.eem2a = ee - T(2) * t.a;
-    t.eebeta = ee * t.beta;
-    t.c2 = T(2) * c1; t.c3 = T(3) * c2; t.c4 = T(4) * c3; t.c5 = T(5) * c4;
-    t.d2 = T(2) * c1; t.d6 = T(6) * c2; t.d12 = T(12) * c3; t.d20 = T(20) * c4;
+__device__ __forceinline__ void adj_grad_kind0(const TrialDev<T>& t, const T x[6], const T w[6],
+                                               T wE, T xbar[6], T thbar[kNumTheta]) {
+    // forward
+    const T s1 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const T s2 = x[3] * x[3] + x[4] * x[4] + x[5] * x[5];
+    const T d[3] = {x[0] - x[3], x[1] - x[4], x[2] - x[5]};
+    const T s12 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    T r1, r2, r12, i1, i2, i12;
+    radius(s1, r1, i1);
+    radius(s2, r2, i2);
+    radius(s12, r12, i12);
+    const T e[3] = {d[0] * i12, d[1] * i12, d[2] * i12};
+    const T h1[3] = {x[0] * i1, x[1] * i1, x[2] * i1};
+    const T h2[3] = {x[3] * i2, x[4] * i2, x[5] * i2};
+    const T q = T(1) + t.beta * r12;
+    const T iq = rcp(q);
+    const T rho = r12 * iq;
+    const T drho = iq * iq;
+    const T d2rho = T(-2) * t.beta * drho * iq;
+    const T A = t.eem2a * i12 + t.eebeta * (T(2) + t.beta * r12);
+    const T hh = t.c2 + rho * (t.c3 + rho * (t.c4 + rho * t.c5));
+    const T du = t.a + rho * hh;
+    const T d2u = t.d2 + rho * (t.d6 + rho * (t.d12 + rho * t.d20));
+    const T up = du * drho;
+    const T proj = (h1[0] - h2[0]) * e[0] + (h1[1] - h2[1]) * e[1] + (h1[2] - h2[2]) * e[2];
+
+    // E_L
+    T i1b = wE * t.Zm2, i2b = wE * t.Zm2;
+    T Zb = wE * up * proj;
+    const T Zm2b = wE * (i1 + i2);
+    const T Z2b = -wE;
+    const T jeeb = wE, uppb = -wE;
+    T upb = wE * (t.Z * proj - T(2) * up);
+    const T projb = wE * t.Z * up;
+    // b1, b2 and proj
+    T eb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T wd = w[c] - w[3 + c];
+        const T h1b = projb * e[c] - t.Z * w[c];
+        const T h2b = -projb * e[c] - t.Z * w[3 + c];
+        eb[c] = projb * (h1[c] - h2[c]) + up * wd;
+        upb += e[c] * wd;
+        Zb -= w[c] * h1[c] + w[3 + c] * h2[c];
+        // h1 = x1 i1, h2 = x2 i2
+        xbar[c] = h1b * i1;
+        xbar[3 + c] = h2b * i2;
+        i1b += h1b * x[c];
+        i2b += h2b * x[3 + c];
+    }
+    // jee, upp, up
+    const T Ab = jeeb * drho;
+    T drhob = jeeb * (A - T(2) * hh * iq) + uppb * T(2) * d2u * drho + upb * du;
+    T iqb = T(-2) * jeeb * hh * drho;
+    T hhb = T(-2) * jeeb * drho * iq;
+    const T d2ub = uppb * drho * drho;
+    const T dub = uppb * d2rho + upb * drho;
+    const T d2rhob = uppb * du;
+    // d2u, du, hh
+    const T rho2 = rho * rho, rho3 = rho2 * rho;
+    T rhob = d2ub * (t.d6 + rho * (T(2) * t.d12 + T(3) * rho * t.d20)) + dub * hh;
+    hhb += dub * rho;
+    rhob += hhb * (t.c3 + rho * (T(2) * t.c4 + T(3) * rho * t.c5));
+    // A
+    T i12b = Ab * t.eem2a;
+    const T eem2ab = Ab * i12;
+    const T eebetab = Ab * (T(2) + t.beta * r12);
+    T betab = Ab * t.eebeta * r12;
+    T r12b = Ab * t.eebeta * t.beta;
+    // d2rho, drho, rho, iq, q
+    betab += T(-2) * d2rhob * drho * iq;
+    drhob += T(-2) * d2rhob * t.beta * iq;
+    iqb += T(-2) * d2rhob * t.beta * drho;
+    iqb += T(2) * drhob * iq;
+    r12b += rhob * iq;
+    iqb += rhob * r12;
+    const T qb = -iqb * iq * iq;
+    betab += qb * r12;
+    r12b += qb * t.beta;
+    // e, the three radii (d r / d s = 1/(2r), d (1/r) / d s = -1/(2 r^3)), d
+#pragma unroll
+    for (int c = 0; c < 3; ++c) i12b += eb[c] * d[c];
+    const T s12b = r12b * T(0.5) * i12 - i12b * T(0.5) * i12 * i12 * i12;
+    const T s1b = -i1b * T(0.5) * i1 * i1 * i1;
+    const T s2b = -i2b * T(0.5) * i2 * i2 * i2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T db = eb[c] * i12 + T(2) * d[c] * s12b;
+        xbar[c] += T(2) * x[c] * s1b + db;
+        xbar[3 + c] += T(2) * x[3 + c] * s2b - db;
+    }
+    // the parameters behind Z - 2, Z^2, ee - 2a, ee beta and the polynomial
+    // coefficients (2, 3, 4, 5) c_k and (2, 6, 12, 20) c_k
+    thbar[0] = Zb + Zm2b + T(2) * t.Z * Z2b;
+    thbar[1] = dub - T(2) * eem2ab;
+    thbar[2] = betab + t.ee * eebetab;
+    thbar[3] = T(2) * (hhb + d2ub);
+    thbar[4] = T(3) * hhb * rho + T(6) * d2ub * rho;
+    thbar[5] = T(4) * hhb * rho2 + T(12) * d2ub * rho2;
+    thbar[6] = T(5) * hhb * rho3 + T(20) * d2ub * rho3;
 }
 
 // Terminal pass 1: per block, the largest final log-weight of live walkers.
@@ -240,7 +341,6 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                     int loss_kind, const T* __restrict__ ckpt, T* __restrict__ seg,
                     const double* __restrict__ ew, const AdjTerminal* __restrict__ term,
                     double* __restrict__ part_theta) {
-    typedef Dual<kNumTangents, T> D;
     __shared__ TrialDev<T> s_trial;
     __shared__ double s_red[kNumTheta][kAdjThreads / 32];
     // Per-thread FP64 parameter adjoints, updated once per segment from the
@@ -248,8 +348,6 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
     __shared__ double s_theta[kNumTheta][kAdjThreads];
     if (threadIdx.x == 0) load_trial<T>(inst->trial, inst->ee_on, s_trial);
     __syncthreads();
-    TrialDev0<D> td;
-    load_trial0_dual<T>(inst->trial, inst->ee_on, td);
     const TrialDev<T>& tp = s_trial;
     T dt, sdt;
     adj_steps(inst, dt, sdt);
@@ -308,22 +406,17 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 for (int m = n_top; m >= n_lo; --m) {
                     T xv[6];
                     PosIO<T>::load(seg + (int64_t)(m - n_lo) * PosIO<T>::kWords * n, n, i, xv);
-                    D xd[6];
+                    // phi = w . b + wE E_L at X_m
+                    T wv[6];
 #pragma unroll
-                    for (int d = 0; d < 6; ++d) xd[d] = D::seed(xv[d], d);
-                    EvalOut<D> ev;
-                    eval_kind0<D>(td, xd, ev);
-                    D phi(T(0));
-                    if (m < S) {
+                    for (int d = 0; d < 6; ++d) wv[d] = m < S ? dt * lambda[d] : T(0);
+                    const T wE = (m >= 1 ? -g_dt : T(0)) + (m == S ? a_t : T(0));
+                    T xb[6], thb[kNumTheta];
+                    adj_grad_kind0<T>(tp, xv, wv, wE, xb, thb);
 #pragma unroll
-                        for (int d = 0; d < 6; ++d) phi += (dt * lambda[d]) * ev.b[d];
-                    }
-                    if (m >= 1) phi -= g_dt * ev.el;
-                    if (m == S) phi += a_t * ev.el;
+                    for (int d = 0; d < 6; ++d) lambda[d] += xb[d];
 #pragma unroll
-                    for (int d = 0; d < 6; ++d) lambda[d] += phi.d[d];
-#pragma unroll
-                    for (int k = 0; k < kNumTheta; ++k) tseg[k] += phi.d[6 + k];
+                    for (int k = 0; k < kNumTheta; ++k) tseg[k] += thb[k];
                 }
 #pragma unroll
                 for (int k = 0; k < kNumTheta; ++k) theta[k * kAdjThreads] += (double)tseg[k];

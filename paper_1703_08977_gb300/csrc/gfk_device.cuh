@@ -405,9 +405,8 @@ struct EvalOut {
 template <typename R>
 struct JastrowOut { R up, upp, jee; };
 
-// Whether the Jastrow polynomial terms are present (a block-uniform branch);
-// the dual-number parameter set always carries them (their derivatives are
-// wanted even where the coefficients are zero).  The evaluators below are
+// Whether the Jastrow polynomial terms are present (a block-uniform branch).
+// The evaluators below are
 // compiled for POLY = 0 (no polynomial terms) or 1 (with them); POLY = -1
 // selects one of the two at run time with a single branch at the top, so every
 // kernel evaluates a given trial function with the same arithmetic.  The
@@ -416,8 +415,6 @@ struct JastrowOut { R up, upp, jee; };
 // move loop, which lets the compiler interleave a thread's walkers across it.
 template <typename R>
 __device__ __forceinline__ bool has_poly(const TrialDev<R>& t) { return t.poly != 0; }
-template <typename TD>
-__device__ __forceinline__ bool has_poly(const TD&) { return true; }
 
 template <typename R, typename TD, int POLY>
 __device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
@@ -636,13 +633,6 @@ __device__ __forceinline__ void eval_trial(const TrialDev<R>& t, const R x[6], E
     else if (t.kind == 0) eval_kind0<R>(t, x, o);
     else eval_kind1<R>(t, x, o);
 }
-
-// Kind-0 parameters only (the fields eval_kind0 reads), for dual-number
-// evaluation where the full TrialDev would be needlessly large.
-template <typename R>
-struct TrialDev0 {
-    R Z, Zm2, Z2, a, beta, ee, eem2a, eebeta, c2, c3, c4, c5, d2, d6, d12, d20;
-};
 
 // A sum is finite only if every term is (an infinity or NaN in any term makes
 // it infinite or NaN), so one test covers the drift and the local energy.
