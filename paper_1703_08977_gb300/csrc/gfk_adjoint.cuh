@@ -110,6 +110,38 @@ __device__ __forceinline__ void adj_steps(const InstDev* inst, float& dt, float&
     sdt = inst->sdt_f32;
 }
 
+// Recomputes the positions of moves n_lo + 1 .. n_hi of walker i from its
+// position x at move n_lo and stores them (with x itself) in the segment
+// planes: the forward walk's noise (the same paired Philox words, or the
+// walker's Superduper generator skipped ahead to move n_lo) and arithmetic.
+// NOISE and POLY are fixed for the whole segment, so the loop has no branch.
+template <int NOISE, int POLY, typename T>
+__device__ __forceinline__ void adj_recompute(const TrialDev<T>& tp, const InstDev* inst,
+                                              int64_t n, int64_t i, int n_lo, int n_hi, T dt,
+                                              T sdt, T x[6], T* seg) {
+    PosIO<T>::store(seg, n, i, x);
+    const uint32_t id = inst->id0 + (uint32_t)i;
+    uint32_t lcg = 0u;
+    PhiloxPre pre[1];
+    uint32_t carry[1][2] = {{0u, 0u}};
+    if (NOISE == 1) lcg = superduper_at(id, inst->stream, inst->k0, inst->k1, (uint32_t)n_lo);
+    else pre[0] = philox_pre(id, inst->stream, inst->k0, inst->k1);
+    for (int m = n_lo; m < n_hi; ++m) {
+        T xi[6], xlo[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        if (NOISE == 1) {
+            adj_bernoulli(lcg, sdt, inst, xi, xlo);
+        } else {
+            uint32_t words[1][6];
+            pair_move_words_all<1>(pre, carry, (uint32_t)m, m == n_lo, inst->k0, inst->k1, words);
+            adj_normals(words[0], xi, inst);
+        }
+        EvalOut<T> ev;
+        eval_kind0<T, TrialDev<T>, POLY>(tp, x, ev);
+        adj_move(x, ev.b, xi, xlo, dt, sdt, NOISE == 1);
+        PosIO<T>::store(seg + (int64_t)(m - n_lo + 1) * PosIO<T>::kWords * n, n, i, x);
+    }
+}
+
 // Reverse-mode gradient of phi = w . b(X) + wE E_L(X) for the kind-0 trial
 // psi = exp(-Z r1 - Z r2 + u(r12)), u = a rho + sum_k c_k rho^{k+1} (the
 // evaluation of eval_kind0 with the polynomial terms, whose derivatives are
@@ -352,6 +384,7 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
     T dt, sdt;
     adj_steps(inst, dt, sdt);
     const bool bern = inst->noise == GFK_NOISE_BERNOULLI;
+    const bool poly = has_poly(tp);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double* theta = &s_theta[0][threadIdx.x];   // theta[k * kAdjThreads]
 #pragma unroll
@@ -378,25 +411,12 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 // recompute the segment's positions n_lo .. n_hi
                 T x[6];
                 PosIO<T>::load(ckpt + (int64_t)j * PosIO<T>::kWords * n, n, i, x);
-                PosIO<T>::store(seg, n, i, x);
-                uint32_t lcg = 0u;
-                if (inst->noise == GFK_NOISE_BERNOULLI)
-                    lcg = superduper_at(inst->id0 + (uint32_t)i, inst->stream, inst->k0, inst->k1,
-                                        (uint32_t)n_lo);
-                for (int m = n_lo; m < n_hi; ++m) {
-                    EvalOut<T> ev;
-                    eval_kind0<T>(tp, x, ev);
-                    T xi[6], xlo[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-                    if (inst->noise == GFK_NOISE_BERNOULLI) {
-                        adj_bernoulli(lcg, sdt, inst, xi, xlo);
-                    } else {
-                        uint32_t words[6];
-                        move_words(inst->id0 + (uint32_t)i, (uint32_t)m, inst->stream, inst->k0,
-                                   inst->k1, words);
-                        adj_normals(words, xi, inst);
-                    }
-                    adj_move(x, ev.b, xi, xlo, dt, sdt, bern);
-                    PosIO<T>::store(seg + (int64_t)(m - n_lo + 1) * PosIO<T>::kWords * n, n, i, x);
+                if (bern) {
+                    if (poly) adj_recompute<1, 1, T>(tp, inst, n, i, n_lo, n_hi, dt, sdt, x, seg);
+                    else adj_recompute<1, 0, T>(tp, inst, n, i, n_lo, n_hi, dt, sdt, x, seg);
+                } else {
+                    if (poly) adj_recompute<0, 1, T>(tp, inst, n, i, n_lo, n_hi, dt, sdt, x, seg);
+                    else adj_recompute<0, 0, T>(tp, inst, n, i, n_lo, n_hi, dt, sdt, x, seg);
                 }
                 // sweep it backwards
                 const int n_top = (j == J - 1) ? n_hi : n_hi - 1;

@@ -167,6 +167,47 @@ __device__ __forceinline__ void philox10_pair(const PhiloxPre& p, uint32_t m, ui
     b.w[0] = bc0; b.w[1] = bc1; b.w[2] = bc2; b.w[3] = bc3;
 }
 
+// The Philox words of one move for all WPT walkers of a thread.  The even
+// move of a pair runs the blocks of tags 0 and 1 and keeps tag 1's last two
+// words (carry) for the odd move, which runs tag 2 (and tag 1 again when the
+// launch starts on an odd move).  The even / odd branch is taken once for all
+// walkers, so the walkers' moves that follow are one branch-free stretch the
+// compiler can interleave.
+template <int WPT>
+__device__ __forceinline__ void pair_move_words_all(const PhiloxPre (&pre)[WPT],
+                                                    uint32_t (&carry)[WPT][2], uint32_t step,
+                                                    bool first, uint32_t k0, uint32_t k1,
+                                                    uint32_t (&words)[WPT][6]) {
+    const uint32_t m = step >> 1;
+    if ((step & 1u) == 0u) {
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            Words4 wa, wb;
+            philox10_pair(pre[k], m, k0, k1, wa, wb);
+            words[k][0] = wa.w[0]; words[k][1] = wa.w[1]; words[k][2] = wa.w[2];
+            words[k][3] = wa.w[3]; words[k][4] = wb.w[0]; words[k][5] = wb.w[1];
+            carry[k][0] = wb.w[2];
+            carry[k][1] = wb.w[3];
+        }
+    } else {
+        if (first) {
+#pragma unroll
+            for (int k = 0; k < WPT; ++k) {
+                const Words4 wb = philox10_tag(pre[k], m, 1u, k0, k1);
+                carry[k][0] = wb.w[2];
+                carry[k][1] = wb.w[3];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            const Words4 wc = philox10_tag(pre[k], m, 2u, k0, k1);
+            words[k][0] = carry[k][0]; words[k][1] = carry[k][1];
+            words[k][2] = wc.w[0]; words[k][3] = wc.w[1]; words[k][4] = wc.w[2];
+            words[k][5] = wc.w[3];
+        }
+    }
+}
+
 // FP32: the same words.  The radius uniform keeps the full 32-bit resolution,
 // u_a = fl(fl(w) 2^-32 + 2^-33) (exact for w < 2^23, where the Gaussian tail
 // lives; elsewhere within an FP32 ulp of (w + 1/2) 2^-32).  A coarser grid
