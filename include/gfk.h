@@ -231,8 +231,10 @@ gfk_status gfk_restore(gfk_ctx* ctx, const void* host_blob, int64_t bytes);
  * (GFK_EINVAL otherwise); grad receives the derivatives with respect to all
  * seven parameters [Z, a, beta, c1, c2, c3, c4] (n_params must be 7), *loss
  * the loss (may be NULL).  Does not touch the context's population.
- * Synchronises the stream; allocates working memory of about
- * n_walkers x (n_steps / ckpt_every + ckpt_every) x 48 bytes (FP64). */
+ * Synchronises the stream.  Needs working memory of about
+ * n_walkers x (n_steps / ckpt_every + ckpt_every) x 48 bytes (FP64), which the
+ * context allocates on the first call, keeps for later calls (growing it when
+ * one needs more) and frees in gfk_destroy. */
 gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_steps,
                     int32_t ckpt_every, double* grad, int32_t n_params, double* loss);
 

@@ -290,13 +290,21 @@ adj_terminal_sums_kernel(const InstDev* __restrict__ inst, const T* __restrict__
     __shared__ TrialDev<T> s_trial;
     __shared__ double s_c;
     __shared__ double s_red[3][kAdjThreads / 32];
-    if (threadIdx.x == 0) {
-        load_trial<T>(inst->trial, inst->ee_on, s_trial);
+    if (threadIdx.x == 0) load_trial<T>(inst->trial, inst->ee_on, s_trial);
+    // the shift c: the largest block maximum, scanned by the whole block
+    {
         double c = -INFINITY;
-        for (int b = 0; b < nblk; ++b) c = fmax(c, part_max[b]);
-        s_c = isfinite(c) ? floor(c) : 0.0;
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) c = fmax(c, part_max[b]);
+        c = warp_max(c);
+        if ((threadIdx.x & 31) == 0) s_red[0][threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = s_red[0][0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[0][w]);
+            s_c = isfinite(m) ? floor(m) : 0.0;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double q[3] = {0.0, 0.0, 0.0};
     if (i < n) {
@@ -328,30 +336,70 @@ adj_terminal_sums_kernel(const InstDev* __restrict__ inst, const T* __restrict__
     }
 }
 
-// Terminal pass 3 (one thread): W, L, Var and the loss, summed in block order.
-static __global__ void adj_terminal_final_kernel(const double* __restrict__ part_max,
-                                          const double* __restrict__ part_sums, int nblk,
-                                          int loss_kind, AdjTerminal* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double c = -INFINITY;
-    for (int b = 0; b < nblk; ++b) c = fmax(c, part_max[b]);
-    c = isfinite(c) ? floor(c) : 0.0;
-    double W = 0, P = 0, R = 0, cW = 0, cP = 0, cR = 0;
-    for (int b = 0; b < nblk; ++b) {
-        const double v[3] = {part_sums[3 * b], part_sums[3 * b + 1], part_sums[3 * b + 2]};
-        double* s[3] = {&W, &P, &R};
-        double* cc[3] = {&cW, &cP, &cR};
-        for (int k = 0; k < 3; ++k) {   // Neumaier
-            const double t = *s[k] + v[k];
-            *cc[k] += fabs(*s[k]) >= fabs(v[k]) ? (*s[k] - t) + v[k] : (v[k] - t) + *s[k];
-            *s[k] = t;
+// Threads of the final-sum kernels, and a Neumaier-compensated running sum.
+constexpr int kFinalThreads = 256;
+struct NeumaierSum {
+    double s = 0.0, c = 0.0;
+    __device__ __forceinline__ void add(double v) {
+        const double t = s + v;
+        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+};
+
+// Adds the compensated sums (s[u], c[u]) of the kFinalThreads threads in a
+// fixed pairwise tree (u + stride into u, stride 128, 64, ..., 1), each step
+// error-free (TwoSum) on the sums; the total is s[0] + c[0].  All threads of
+// the block call it.
+__device__ __forceinline__ void tree_sum(double* s, double* c) {
+    const int u = threadIdx.x;
+#pragma unroll
+    for (int stride = kFinalThreads / 2; stride > 0; stride >>= 1) {
+        __syncthreads();
+        if (u < stride) {
+            double t, e;
+            two_sum(s[u], s[u + stride], t, e);
+            c[u] = c[u] + c[u + stride] + e;
+            s[u] = t;
         }
     }
-    W += cW;
-    P += cP;
-    R += cR;
+    __syncthreads();
+}
+
+// Terminal pass 3 (one block): W, L, Var and the loss.  Thread u sums blocks
+// u, u + 256, ... (Neumaier); the threads' sums are then added in a fixed
+// tree (tree_sum), so the result does not change from run to run.
+static __global__ void __launch_bounds__(kFinalThreads)
+adj_terminal_final_kernel(const double* __restrict__ part_max,
+                          const double* __restrict__ part_sums, int nblk, int loss_kind,
+                          AdjTerminal* __restrict__ out) {
+    __shared__ double s_max[kFinalThreads / 32];
+    __shared__ double s_part[3][2][kFinalThreads];
+    const int u = threadIdx.x;
+    double c = -INFINITY;
+    NeumaierSum acc[3];
+    for (int b = u; b < nblk; b += kFinalThreads) {
+        c = fmax(c, part_max[b]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[k].add(part_sums[3 * b + k]);
+    }
+    c = warp_max(c);
+    if ((u & 31) == 0) s_max[u >> 5] = c;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s_part[k][0][u] = acc[k].s;
+        s_part[k][1][u] = acc[k].c;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tree_sum(s_part[k][0], s_part[k][1]);
+    if (u != 0) return;
+    double cm = s_max[0];
+    for (int v = 1; v < kFinalThreads / 32; ++v) cm = fmax(cm, s_max[v]);
+    const double W = s_part[0][0][0] + s_part[0][1][0];
+    const double P = s_part[1][0][0] + s_part[1][1][0];
+    const double R = s_part[2][0][0] + s_part[2][1][0];
     AdjTerminal r;
-    r.c = c;
+    r.c = isfinite(cm) ? floor(cm) : 0.0;
     r.W = W;
     r.L = P / W;
     r.Var = R / W - r.L * r.L;
@@ -463,19 +511,26 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
     }
 }
 
-// Sum of the blocks' theta_bar (one thread per parameter, block order, Neumaier).
-static __global__ void adj_grad_final_kernel(const double* __restrict__ part_theta, int nblk,
-                                      double* __restrict__ grad) {
-    const int k = threadIdx.x;
-    if (k >= kNumTheta) return;
-    double s = 0.0, c = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-        const double v = part_theta[(int64_t)kNumTheta * b + k];
-        const double t = s + v;
-        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-        s = t;
+// Sum of the blocks' theta_bar (one block): thread u sums blocks u, u + 256,
+// ... per parameter (Neumaier); the threads' sums are then added in a fixed
+// tree (tree_sum).
+static __global__ void __launch_bounds__(kFinalThreads)
+adj_grad_final_kernel(const double* __restrict__ part_theta, int nblk, double* __restrict__ grad) {
+    __shared__ double s_part[kNumTheta][2][kFinalThreads];
+    const int u = threadIdx.x;
+    NeumaierSum acc[kNumTheta];
+    for (int b = u; b < nblk; b += kFinalThreads) {
+#pragma unroll
+        for (int k = 0; k < kNumTheta; ++k) acc[k].add(part_theta[(int64_t)kNumTheta * b + k]);
     }
-    grad[k] = s + c;
+#pragma unroll
+    for (int k = 0; k < kNumTheta; ++k) {
+        s_part[k][0][u] = acc[k].s;
+        s_part[k][1][u] = acc[k].c;
+    }
+#pragma unroll
+    for (int k = 0; k < kNumTheta; ++k) tree_sum(s_part[k][0], s_part[k][1]);
+    if (u < kNumTheta) grad[u] = s_part[u][0][0] + s_part[u][1][0];
 }
 
 // Host side of one precision: terminal passes, reverse sweep, final sum.
@@ -489,10 +544,11 @@ cudaError_t adj_run(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
     adj_terminal_max_kernel<T><<<nblk, kAdjThreads, 0, stream>>>(logw_final, n, part_max);
     adj_terminal_sums_kernel<T><<<nblk, kAdjThreads, 0, stream>>>(inst, pos_final, logw_final, n,
                                                                    part_max, nblk, ew, part_sums);
-    adj_terminal_final_kernel<<<1, 32, 0, stream>>>(part_max, part_sums, nblk, loss_kind, term);
+    adj_terminal_final_kernel<<<1, kFinalThreads, 0, stream>>>(part_max, part_sums, nblk, loss_kind,
+                                                            term);
     adj_backward_kernel<T><<<nblk, kAdjThreads, 0, stream>>>(inst, n, S, K, J, loss_kind, ckpt, seg,
                                                               ew, term, part_theta);
-    adj_grad_final_kernel<<<1, 32, 0, stream>>>(part_theta, nblk, grad);
+    adj_grad_final_kernel<<<1, kFinalThreads, 0, stream>>>(part_theta, nblk, grad);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,10 @@ struct gfk_ctx {
     // output staging for gfk_energy / gfk_get_walkers, grown on demand
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // gfk_grad's working memory (checkpoints, segment, state copy), kept
+    // between calls and grown on demand
+    void* grad_ws = nullptr;
+    size_t grad_ws_bytes = 0;
     // launch shape
     int threads = 128;
     int wpt = 1;
@@ -130,16 +134,23 @@ void dev_free(void* p) {
     if (p) cudaFree(p);
 }
 
-gfk_status ensure_scratch(gfk_ctx* ctx, size_t bytes) {
-    if (bytes <= ctx->scratch_bytes) return GFK_OK;
+// Grows a device buffer of the context to at least `bytes` (its contents are
+// not kept); the stream is synchronised first, as work queued on it may still
+// use the old buffer.
+gfk_status ensure_buffer(gfk_ctx* ctx, void** buf, size_t* cap, size_t bytes) {
+    if (bytes <= *cap) return GFK_OK;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
-    dev_free(ctx->scratch);
-    ctx->scratch = nullptr;
-    ctx->scratch_bytes = 0;
-    gfk_status st = dev_alloc(ctx, &ctx->scratch, bytes);
-    if (st == GFK_OK) ctx->scratch_bytes = bytes;
+    dev_free(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    gfk_status st = dev_alloc(ctx, buf, bytes);
+    if (st == GFK_OK) *cap = bytes;
     return st;
+}
+
+gfk_status ensure_scratch(gfk_ctx* ctx, size_t bytes) {
+    return ensure_buffer(ctx, &ctx->scratch, &ctx->scratch_bytes, bytes);
 }
 
 // Makes the context's device current for the duration of a call.
@@ -418,6 +429,7 @@ void free_all(gfk_ctx* ctx) {
     dev_free(ctx->smx.sgn);
     dev_free(ctx->part);
     dev_free(ctx->scratch);
+    dev_free(ctx->grad_ws);
     dev_free(ctx->series);
     dev_free(ctx->counters);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -1074,10 +1086,9 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
     const size_t o_pth = take(sizeof(double) * 7 * nblk_adj);
     const size_t o_term = take(64);
     const size_t o_grad = take(sizeof(double) * 8);
-    void* mem = nullptr;
-    st = dev_alloc(ctx, &mem, off);
+    st = ensure_buffer(ctx, &ctx->grad_ws, &ctx->grad_ws_bytes, off);
     if (st != GFK_OK) return st;
-    char* base = (char*)mem;
+    char* base = (char*)ctx->grad_ws;
     InstDev* d_inst = (InstDev*)(base + o_inst);
     cudaError_t e = cudaMemcpyAsync(d_inst, ctx->d_inst + inst, sizeof(InstDev),
                                     cudaMemcpyDeviceToDevice, ctx->stream);
@@ -1150,7 +1161,6 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
     if (e == cudaSuccess) e = cudaMemcpyAsync(hg, grad_d, sizeof(hg), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hterm, term, sizeof(hterm), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    dev_free(mem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gfk_grad");
     for (int k = 0; k < 7; ++k) grad[k] = hg[k];
     if (loss) *loss = hterm[4];
