@@ -1075,7 +1075,12 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
     const size_t o_inst = take(sizeof(InstDev));
     const size_t o_state = take(f64 ? n * (7 * sizeof(double)) : n * 2 * sizeof(float4));
     const size_t o_sgn = take((size_t)n);
-    const size_t o_part = take(sizeof(PartialRec) * (size_t)K * nblk);
+    // the mixed walk writes the checkpoints itself when they fall on its 64-move
+    // folds, and then runs in launches of up to kGradChunk moves
+    constexpr int kGradChunk = 1024;
+    const bool ckpt_in_kernel = !f64 && K % kRing == 0;
+    const int part_rows = ckpt_in_kernel ? std::min(S, kGradChunk) : K;
+    const size_t o_part = take(sizeof(PartialRec) * (size_t)part_rows * nblk);
     const size_t o_cnt = take(sizeof(unsigned long long) * kNumCounters);
     const size_t o_ckpt = take(tsz * words * (size_t)n * J);
     const size_t o_seg = take(std::max(tsz * words * (size_t)n * (K + 1), sizeof(double) * 7 * (size_t)n));
@@ -1119,7 +1124,25 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
     if (e == cudaSuccess)
         e = f64 ? launch_init_fp64(kind, shape.threads, (int)nblk, d_inst, bm, s64, part, cnt, ctx->stream)
                 : launch_init_mixed(kind, shape.threads, (int)nblk, d_inst, bm, smx, part, cnt, ctx->stream);
-    for (int j = 0; j < J && e == cudaSuccess; ++j) {
+    if (ckpt_in_kernel) {
+        // checkpoint 0 is the initial state; the walk kernel writes 1 .. J - 1
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ckpt, base + o_state, tsz * words * (size_t)n,
+                                cudaMemcpyDeviceToDevice, ctx->stream);
+        smx.ckpt = (float4*)ckpt;
+        smx.ckpt_slots = n;
+        smx.ckpt_every = K;
+        smx.ckpt_count = J;
+        for (int done = 0; done < S && e == cudaSuccess; done += kGradChunk) {
+            const int steps = std::min(kGradChunk, S - done);
+            e = launch_walk_mixed(mixed_walk_kind(kind, &ctx->trial[inst], 1), ctx->noise,
+                                  shape.wpt, shape.threads, (int)nblk, 0, (int)nblk, d_inst, bm,
+                                  smx, (uint32_t)done, steps, part, cnt, &ctx->trial[inst],
+                                  ctx->desc[inst].ee_on, ctx->stream);
+        }
+        smx.ckpt = nullptr;
+    }
+    for (int j = 0; j < J && !ckpt_in_kernel && e == cudaSuccess; ++j) {
         const size_t plane_bytes = tsz * words * (size_t)n;
         e = cudaMemcpyAsync(ckpt + plane_bytes * j, base + o_state, plane_bytes,
                             cudaMemcpyDeviceToDevice, ctx->stream);

@@ -135,7 +135,7 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 // shared memory (kind 0 then copies its 16 parameters into registers).  The
 // launcher uses PARAM for the orbital-pair kinds only: it speeds them up by
 // ~11 % and slows the kind-0 walk by ~2 % against the register copy.
-template <int KIND, int WPT, int NOISE, bool PARAM>
+template <int KIND, int WPT, int NOISE, bool PARAM, bool CKPT = false>
 __global__ void __launch_bounds__(kMaxThreads)
 walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                   uint32_t step0, int nsteps, PartialRec* __restrict__ part, int nblk,
@@ -343,6 +343,22 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             c = isfinite(c) ? floor(c) : 0.0;
 #pragma unroll
             for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) * kLog2e : 0.f;
+            // position checkpoint (StateMixed::ckpt) after move step; compiled
+            // into the gradient's forward kernels only (CKPT), since the extra
+            // code at the fold slowed the other walks by up to 1.7 %
+            if (CKPT) {
+                const uint32_t done = step + 1u;
+                const uint32_t j = done / (uint32_t)st.ckpt_every;
+                if (done % (uint32_t)st.ckpt_every == 0u && j >= 1u && j < (uint32_t)st.ckpt_count) {
+                    float4* base = st.ckpt + (int64_t)j * 2 * st.ckpt_slots;
+#pragma unroll
+                    for (int k = 0; k < WPT; ++k) {
+                        if (!valid[k]) continue;
+                        base[slot[k]] = make_float4(x[k][0], x[k][1], x[k][2], x[k][3]);
+                        base[st.ckpt_slots + slot[k]] = make_float4(x[k][4], x[k][5], 0.f, 0.f);
+                    }
+                }
+            }
             // one barrier per window: the other buffer takes the next window,
             // and nobody writes this one again before the next barrier
             __syncthreads();
@@ -409,7 +425,7 @@ static void launch_walk(K kernel, int nblk, int blk0, int grid, int threads, cud
                                                 counters, blk0, tk);
 }
 
-template <int KIND, int NOISE, bool PARAM>
+template <int KIND, int NOISE, bool PARAM, bool CKPT = false>
 static void launch_walk_mixed_k(int wpt, int threads, int nblk, int blk0, int grid,
                                 const InstDev* insts,
                                 const BlockMap& bm, const StateMixed& st, uint32_t step0,
@@ -417,15 +433,15 @@ static void launch_walk_mixed_k(int wpt, int threads, int nblk, int blk0, int gr
                                 const TrialDev<float>& tk, cudaStream_t stream, bool run) {
     switch (wpt) {
         case 1:
-            launch_walk(walk_mixed_kernel<KIND, 1, NOISE, PARAM>, nblk, blk0, grid, threads, stream,
+            launch_walk(walk_mixed_kernel<KIND, 1, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
                         insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
         case 2:
-            launch_walk(walk_mixed_kernel<KIND, 2, NOISE, PARAM>, nblk, blk0, grid, threads, stream,
+            launch_walk(walk_mixed_kernel<KIND, 2, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
                         insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
         default:
-            launch_walk(walk_mixed_kernel<KIND, 4, NOISE, PARAM>, nblk, blk0, grid, threads, stream,
+            launch_walk(walk_mixed_kernel<KIND, 4, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
                         insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
     }
@@ -441,6 +457,17 @@ void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, int blk0, int
     TrialDev<float> tk;
     std::memset(&tk, 0, sizeof(tk));
     if (one_trial) load_trial<float>(*one_trial, ee_on, tk);
+    if (st.ckpt != nullptr) {
+        // gfk_grad's forward: kind 0, or the per-block dispatch for a trial
+        // function with Jastrow polynomial terms
+        if (kind == 0)
+            launch_walk_mixed_k<0, NOISE, false, true>(wpt, threads, nblk, blk0, grid, insts, bm, st,
+                                                       step0, nsteps, part, counters, tk, stream, run);
+        else
+            launch_walk_mixed_k<2, NOISE, false, true>(wpt, threads, nblk, blk0, grid, insts, bm, st,
+                                                       step0, nsteps, part, counters, tk, stream, run);
+        return;
+    }
     if (one_trial && kind == 1)
         launch_walk_mixed_k<1, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                             part, counters, tk, stream, run);

@@ -135,7 +135,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     rows_fit = rows_fit > 1024 ? 1024 : (rows_fit / 16) * 16;
     if (rows_fit < 16) return GFK_EINVAL;      // cannot happen below GFK_NOALLOC_MAX_WALKERS
 
-    StateMixed sm;
+    StateMixed sm{};
     sm.p0 = (float4*)dev_p0;
     sm.p1 = (float4*)dev_p1;
     sm.sgn = dev_sgn;

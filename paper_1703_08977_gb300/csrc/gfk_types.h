@@ -72,6 +72,16 @@ struct StateMixed {
     float4* p0;
     float4* p1;
     int8_t* sgn;
+    // Optional position checkpoints written by the walk kernel (gfk_grad's
+    // forward): after a move that completes global move j * ckpt_every, for
+    // 1 <= j < ckpt_count, each slot's positions go to the planes at
+    // ckpt + j * 2 * ckpt_slots: (x1, y1, z1, x2) at [slot], (y2, z2, 0, 0) at
+    // [ckpt_slots + slot].  Written at the kernel's 64-move folds, so
+    // ckpt_every must be a multiple of kRing and launches must start on a
+    // multiple of it.  NULL: none.
+    float4* ckpt;
+    int64_t ckpt_slots;
+    int32_t ckpt_every, ckpt_count;
 };
 
 // Steps between flushes of the per-step block sums; also the mixed path's
