@@ -409,11 +409,12 @@ adj_terminal_final_kernel(const double* __restrict__ part_max,
 
 // The reverse sweep: one thread per walker, all segments from the last to the
 // first; per block the summed parameter adjoint theta_bar.
-// Blocks per SM the reverse sweep is compiled for: the FP32 sweep runs 4
-// (128 registers, a small spill; +8 % over the 2 blocks its 250 registers
-// allowed), the FP64 one keeps the default.
+// Blocks per SM the reverse sweep is compiled for: the FP32 sweep runs 6
+// (80 registers, no spills; against 4 blocks at 120 registers +0.4 %, 5 blocks
+// -0.8 %, 8 blocks with spills -2.5 %: more resident walkers also widen the
+// segment positions' working set in L2), the FP64 one keeps the default.
 template <typename T>
-constexpr int adj_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
+constexpr int adj_min_blocks() { return sizeof(T) == 4 ? 6 : 1; }
 
 template <typename T>
 __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
