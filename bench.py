@@ -81,8 +81,8 @@ LANES_PER_SM_CLK = 128
 # threads x 2 walkers, the launch shape the bench autotunes to), valid only for the kernel sources it was taken
 # on (sha256 prefix of WALK_SOURCES); scaled by the walker-steps of an average launch.
 WALK_TRAFFIC = {       # workload -> capture
-    "ground": {"src_sha": "4144ddd768f15fbd", "bytes_per_walker_step": 0.19922},
-    "bernoulli": {"src_sha": "4144ddd768f15fbd", "bytes_per_walker_step": 0.20071},
+    "ground": {"src_sha": "50abc19209121823", "bytes_per_walker_step": 0.19995},
+    "bernoulli": {"src_sha": "50abc19209121823", "bytes_per_walker_step": 0.19977},
 }
 
 
