@@ -69,6 +69,26 @@ template <> struct PosIO<float> {
     static constexpr int kWords = 8;          // floats per walker per plane set
 };
 
+// The recomputed positions of one segment, with a plane stride ns (walkers,
+// even).  FP64: six planes of ns doubles per move (PosIO).  FP32: per move a
+// float4 plane (x1, y1, z1, x2) and a float2 plane (y2, z2), 24 bytes a walker
+// (two loads, like the state's two float4 planes, but a quarter less
+// traffic); with ns even every float4 plane starts a multiple of 48 bytes
+// from the (256-byte aligned) segment buffer, as 16-byte vector loads need.
+template <typename T> struct SegIO : PosIO<T> {};
+template <> struct SegIO<float> {
+    __device__ __forceinline__ static void load(const float* base, int64_t ns, int64_t i, float x[6]) {
+        const float4 a = reinterpret_cast<const float4*>(base)[i];
+        const float2 b = reinterpret_cast<const float2*>(base + 4 * ns)[i];
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y;
+    }
+    __device__ __forceinline__ static void store(float* base, int64_t ns, int64_t i, const float x[6]) {
+        reinterpret_cast<float4*>(base)[i] = make_float4(x[0], x[1], x[2], x[3]);
+        reinterpret_cast<float2*>(base + 4 * ns)[i] = make_float2(x[4], x[5]);
+    }
+    static constexpr int kWords = 6;          // floats per walker per move
+};
+
 // The forward move of the precision, written exactly as the walk kernel of
 // that precision writes it (so the recomputed positions are the forward's).
 // FP64: X + b dt + sdt xi for both noise modes (xi = +-1 for Bernoulli).
@@ -117,9 +137,9 @@ __device__ __forceinline__ void adj_steps(const InstDev* inst, float& dt, float&
 // NOISE and POLY are fixed for the whole segment, so the loop has no branch.
 template <int NOISE, int POLY, typename T>
 __device__ __forceinline__ void adj_recompute(const TrialDev<T>& tp, const InstDev* inst,
-                                              int64_t n, int64_t i, int n_lo, int n_hi, T dt,
+                                              int64_t ns, int64_t i, int n_lo, int n_hi, T dt,
                                               T sdt, T x[6], T* seg) {
-    PosIO<T>::store(seg, n, i, x);
+    SegIO<T>::store(seg, ns, i, x);
     const uint32_t id = inst->id0 + (uint32_t)i;
     uint32_t lcg = 0u;
     PhiloxPre pre[1];
@@ -138,7 +158,7 @@ __device__ __forceinline__ void adj_recompute(const TrialDev<T>& tp, const InstD
         EvalOut<T> ev;
         eval_kind0<T, TrialDev<T>, POLY>(tp, x, ev);
         adj_move(x, ev.b, xi, xlo, dt, sdt, NOISE == 1);
-        PosIO<T>::store(seg + (int64_t)(m - n_lo + 1) * PosIO<T>::kWords * n, n, i, x);
+        SegIO<T>::store(seg + (int64_t)(m - n_lo + 1) * SegIO<T>::kWords * ns, ns, i, x);
     }
 }
 
@@ -434,6 +454,7 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
     adj_steps(inst, dt, sdt);
     const bool bern = inst->noise == GFK_NOISE_BERNOULLI;
     const bool poly = has_poly(tp);
+    const int64_t ns = (n + 1) & ~(int64_t)1;   // segment plane stride (SegIO): even
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double* theta = &s_theta[0][threadIdx.x];   // theta[k * kAdjThreads]
 #pragma unroll
@@ -461,11 +482,11 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 T x[6];
                 PosIO<T>::load(ckpt + (int64_t)j * PosIO<T>::kWords * n, n, i, x);
                 if (bern) {
-                    if (poly) adj_recompute<1, 1, T>(tp, inst, n, i, n_lo, n_hi, dt, sdt, x, seg);
-                    else adj_recompute<1, 0, T>(tp, inst, n, i, n_lo, n_hi, dt, sdt, x, seg);
+                    if (poly) adj_recompute<1, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                    else adj_recompute<1, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
                 } else {
-                    if (poly) adj_recompute<0, 1, T>(tp, inst, n, i, n_lo, n_hi, dt, sdt, x, seg);
-                    else adj_recompute<0, 0, T>(tp, inst, n, i, n_lo, n_hi, dt, sdt, x, seg);
+                    if (poly) adj_recompute<0, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                    else adj_recompute<0, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
                 }
                 // sweep it backwards
                 const int n_top = (j == J - 1) ? n_hi : n_hi - 1;
@@ -475,11 +496,11 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 // each move loads the position of the next (earlier) one, so the
                 // load's latency hides behind a gradient evaluation (+2.2 %)
                 T xv[6];
-                PosIO<T>::load(seg + (int64_t)(n_top - n_lo) * PosIO<T>::kWords * n, n, i, xv);
+                SegIO<T>::load(seg + (int64_t)(n_top - n_lo) * SegIO<T>::kWords * ns, ns, i, xv);
                 for (int m = n_top; m >= n_lo; --m) {
                     T xnext[6];
                     const int mp = m > n_lo ? m - 1 : m;
-                    PosIO<T>::load(seg + (int64_t)(mp - n_lo) * PosIO<T>::kWords * n, n, i, xnext);
+                    SegIO<T>::load(seg + (int64_t)(mp - n_lo) * SegIO<T>::kWords * ns, ns, i, xnext);
                     // phi = w . b + wE E_L at X_m
                     T wv[6];
 #pragma unroll

@@ -1083,7 +1083,9 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
     const size_t o_part = take(sizeof(PartialRec) * (size_t)part_rows * nblk);
     const size_t o_cnt = take(sizeof(unsigned long long) * kNumCounters);
     const size_t o_ckpt = take(tsz * words * (size_t)n * J);
-    const size_t o_seg = take(std::max(tsz * words * (size_t)n * (K + 1), sizeof(double) * 7 * (size_t)n));
+    // the reverse sweep's segment planes use an even walker stride (SegIO)
+    const size_t n_even = (size_t)((n + 1) & ~(int64_t)1);
+    const size_t o_seg = take(std::max(tsz * words * n_even * (K + 1), sizeof(double) * 7 * (size_t)n));
     const size_t o_logw = take(sizeof(double) * (size_t)n);
     const size_t o_ew = take(sizeof(double) * 2 * (size_t)n);
     const size_t o_pmax = take(sizeof(double) * nblk_adj);

@@ -15,13 +15,14 @@ def _ctx(gfk, n, dt, prec, theta=THETA, seed=7, stream=1):
 
 @pytest.mark.parametrize("loss_kind", [0, 1])
 @pytest.mark.parametrize("S,K", [(24, 8), (30, 8), (17, 64)])
-def test_fp64_grad_matches_autograd_oracle(gfk_lib, loss_kind, S, K):
-    """FP64 adjoint (checkpointed every K moves, ragged last segment) = autograd through
-    the oracle's walk with the same Philox noise."""
+@pytest.mark.parametrize("n", [40, 41])
+def test_fp64_grad_matches_autograd_oracle(gfk_lib, loss_kind, S, K, n):
+    """FP64 adjoint (checkpointed every K moves, ragged last segment; an odd walker count
+    pads the segment planes' stride) = autograd through the oracle's walk with the same
+    Philox noise."""
     torch = pytest.importorskip("torch")
     from oracle import grad as og
     gfk = gfk_lib
-    n = 40
     with _ctx(gfk, n, 0.01, gfk.GFK_PREC_FP64) as c:
         loss, g = gfk.gfk_grad(c.handle, 0, loss_kind, S, K)
     ref_loss, ref_g = og.gradient(THETA, n_walkers=n, n_steps=S, dt=0.01, e_trial=-2.9, seed=7,
@@ -66,11 +67,13 @@ def test_fp64_grad_matches_central_differences(gfk_lib, loss_kind):
     assert err_plain <= 3e-5, (err_plain, g, d1)
 
 
-def test_mixed_grad_close_to_fp64(gfk_lib):
+@pytest.mark.parametrize("n", [8192, 8191])
+def test_mixed_grad_close_to_fp64(gfk_lib, n):
     """The mixed path's gradient (FP32 positions and trial arithmetic, FP64 weights and
-    adjoint sums) stays within 1e-3 of the FP64 gradient on the same seeds."""
+    adjoint sums) stays within 1e-3 of the FP64 gradient on the same seeds; also for an
+    odd walker count (the segment planes' padded stride)."""
     gfk = gfk_lib
-    n, S = 8192, 200
+    S = 200
     with _ctx(gfk, n, 0.005, gfk.GFK_PREC_FP64) as c:
         l64, g64 = gfk.gfk_grad(c.handle, 0, 0, S, 64)
     with _ctx(gfk, n, 0.005, gfk.GFK_PREC_MIXED) as c:
@@ -115,3 +118,25 @@ def test_autograd_function_and_adam_reduce_variance(gfk_lib):
         np.testing.assert_allclose(th.grad.numpy(), g, rtol=1e-12)
         hist, theta = tuning.tune(c.handle, 0, theta0, steps=12, lr=0.03, loss_kind=1, n_steps=200)
     assert hist[-1][0] < 0.9 * hist[0][0], [h[0] for h in hist]
+
+
+def test_mixed_grad_does_not_depend_on_checkpoint_interval(gfk_lib):
+    """Checkpoints every 64 moves are written by the walk kernel at its folds; other
+    intervals are copied between launches.  The recomputed trajectories are the
+    forward's either way, so the gradient agrees across intervals (to the rounding of
+    the per-segment FP32 partial sums), on an odd walker count and a ragged last
+    segment."""
+    gfk = gfk_lib
+    n, S = 4099, 300
+    out = {}
+    for K in (64, 128, 32, 100):
+        with _ctx(gfk, n, 0.005, gfk.GFK_PREC_MIXED) as c:
+            out[K] = gfk.gfk_grad(c.handle, 0, 1, S, K)
+    l64, g64 = out[64]
+    for K, (l, g) in out.items():
+        # intervals that are not multiples of 64 fold the FP32 log-weight sums at
+        # other moves (launch ends), so the loss agrees to rounding, not bitwise
+        if K % 64 == 0:
+            assert l == l64, (K, l, l64)
+        assert abs(l - l64) <= 1e-7 * abs(l64), (K, l, l64)
+        np.testing.assert_allclose(g, g64, rtol=2e-5, atol=2e-5 * np.abs(g64).max())
