@@ -36,9 +36,14 @@ struct gfk_ctx {
     // state
     StateF64 s64{};
     StateMixed smx{};
-    // per-step block records for one chunk
+    // per-step block records for one chunk, double-buffered: chunk c writes
+    // part_buf[c % 2] while the merge of chunk c - 1 reads the other buffer on
+    // merge_stream (part == part_buf[0], one allocation)
     PartialRec* part = nullptr;
-    int64_t part_records = 0;     // capacity in records
+    PartialRec* part_buf[2] = {nullptr, nullptr};
+    int64_t part_records = 0;     // capacity in records of each buffer
+    cudaStream_t merge_stream = nullptr;          // low priority: fills the walks' idle tails
+    cudaEvent_t ev_walked[2] = {nullptr, nullptr}, ev_merged[2] = {nullptr, nullptr};
     // merged per-step sums, [inst][series_cap]
     SeriesRow* series = nullptr;
     int64_t series_cap = 0;
@@ -243,12 +248,12 @@ std::vector<WalkSegment> walk_segments(const gfk_ctx* ctx, const BlockMap& bm) {
 }
 
 cudaError_t launch_mixed_walks(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, uint32_t step0,
-                               int chunk) {
+                               int chunk, PartialRec* part) {
     for (const WalkSegment& g : walk_segments(ctx, bm)) {
         const bool one = same_trials(ctx, g.i0, g.i1);
         const cudaError_t e = launch_walk_mixed(
             g.kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk, bm.begin[g.i0],
-            bm.begin[g.i1] - bm.begin[g.i0], ctx->d_inst, bm, ctx->smx, step0, chunk, ctx->part,
+            bm.begin[g.i1] - bm.begin[g.i0], ctx->d_inst, bm, ctx->smx, step0, chunk, part,
             ctx->counters, one ? &ctx->trial[g.i0] : nullptr, ctx->desc[g.i0].ee_on, ctx->stream);
         if (e != cudaSuccess) return e;
     }
@@ -300,23 +305,35 @@ gfk_status upload_instances(gfk_ctx* ctx) {
     return GFK_OK;
 }
 
-// Ensures room for `rows` chunk rows of block records; returns the rows that fit.
+// Ensures room for `rows` chunk rows of block records in each of the two
+// buffers, and the merge stream and its events; returns the rows that fit.
 gfk_status ensure_partials(gfk_ctx* ctx, int64_t nblk, int64_t* rows_fit) {
     int64_t rows = ctx->part_budget_bytes / (int64_t)(nblk * sizeof(PartialRec));
     rows = std::max<int64_t>(kRing, std::min<int64_t>(rows, 1024));
     rows = (rows / kRing) * kRing;
     const int64_t need = rows * nblk;
     if (need > ctx->part_records) {
-        // the old buffer may still be read by queued kernels
+        // the old buffers may still be read by queued kernels (the caller's
+        // stream waits for every merge it queued)
         GFK_CK(ctx, cudaStreamSynchronize(ctx->stream));
         dev_free(ctx->part);
-        ctx->part = nullptr;
+        ctx->part = ctx->part_buf[0] = ctx->part_buf[1] = nullptr;
         ctx->part_records = 0;
         void* p = nullptr;
-        gfk_status st = dev_alloc(ctx, &p, sizeof(PartialRec) * (size_t)need);
+        gfk_status st = dev_alloc(ctx, &p, 2 * sizeof(PartialRec) * (size_t)need);
         if (st != GFK_OK) return st;
-        ctx->part = (PartialRec*)p;
+        ctx->part = ctx->part_buf[0] = (PartialRec*)p;
+        ctx->part_buf[1] = ctx->part + need;
         ctx->part_records = need;
+    }
+    if (!ctx->merge_stream) {
+        int least = 0, greatest = 0;
+        GFK_CK(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        GFK_CK(ctx, cudaStreamCreateWithPriority(&ctx->merge_stream, cudaStreamNonBlocking, least));
+        for (int b = 0; b < 2; ++b) {
+            GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_walked[b], cudaEventDisableTiming));
+            GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_merged[b], cudaEventDisableTiming));
+        }
     }
     *rows_fit = rows;
     return GFK_OK;
@@ -377,15 +394,25 @@ gfk_status enqueue_init(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk) {
 gfk_status profile_pair(gfk_ctx* ctx, cudaEvent_t* a, cudaEvent_t* b);
 
 // Queues n_steps moves from global step step_begin in chunks of rows_fit.
+// Chunk c's walk writes records buffer c % 2 on the context's stream; its
+// merge runs on the low-priority merge stream, so that its blocks take the
+// slots the next walk leaves idle in its last partial wave.  The walk of
+// chunk c waits for the merge of chunk c - 2 (the same buffer), and the
+// context's stream waits for every merge before this returns (in a graph
+// capture these waits join the merge stream into the graph).
 gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t rows_fit,
                          int64_t step_begin, int64_t n_steps, bool events) {
     const int kind = launch_kind(ctx);
     int64_t walkers = 0;
     for (int i = 0; i < ctx->n_inst; ++i) walkers += ctx->desc[i].n_walkers;
     int64_t done = 0;
+    int64_t c = 0;                                      // chunk index
     while (done < n_steps) {
         const int chunk = (int)std::min<int64_t>(n_steps - done, rows_fit);
         const uint32_t step0 = (uint32_t)(step_begin + done);
+        const int b = (int)(c & 1);
+        PartialRec* const part = ctx->part_buf[b];
+        if (c >= 2) GFK_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_merged[b], 0));
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (events) {
             gfk_status st = profile_pair(ctx, &ev0, &ev1);
@@ -394,9 +421,9 @@ gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t
         if (ev0) GFK_CK(ctx, cudaEventRecord(ev0, ctx->stream));
         if (ctx->prec == GFK_PREC_FP64) {
             GFK_CK(ctx, launch_walk_fp64(kind, ctx->noise, ctx->threads, (int)nblk, ctx->d_inst,
-                                         bm, ctx->s64, step0, chunk, ctx->part, ctx->counters, ctx->stream));
+                                         bm, ctx->s64, step0, chunk, part, ctx->counters, ctx->stream));
         } else {
-            GFK_CK(ctx, launch_mixed_walks(ctx, bm, nblk, step0, chunk));
+            GFK_CK(ctx, launch_mixed_walks(ctx, bm, nblk, step0, chunk, part));
             ctx->kernels += (int64_t)walk_segments(ctx, bm).size() - 1;   // + 1 below
         }
         if (ev1) {
@@ -405,11 +432,17 @@ gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t
             ctx->prof_walker_steps += (double)walkers * chunk;
         }
         ctx->kernels += 2;                              // the walk and the merge
-        GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
+        GFK_CK(ctx, cudaEventRecord(ctx->ev_walked[b], ctx->stream));
+        GFK_CK(ctx, cudaStreamWaitEvent(ctx->merge_stream, ctx->ev_walked[b], 0));
+        GFK_CK(ctx, launch_reduce_rows(part, (int)nblk, bm, chunk, ctx->series,
                                        ctx->series_cap, step_begin + done + 1,
-                                       ctx->prec == GFK_PREC_FP64, ctx->stream));
+                                       ctx->prec == GFK_PREC_FP64, ctx->merge_stream));
+        GFK_CK(ctx, cudaEventRecord(ctx->ev_merged[b], ctx->merge_stream));
         done += chunk;
+        ++c;
     }
+    for (int64_t b = 0; b < std::min<int64_t>(c, 2); ++b)
+        GFK_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_merged[b], 0));
     return GFK_OK;
 }
 
@@ -436,6 +469,13 @@ void free_all(gfk_ctx* ctx) {
     ctx->ev_pool.clear();
     for (auto& gph : ctx->graphs) cudaGraphExecDestroy(gph.exec);
     ctx->graphs.clear();
+    for (int b = 0; b < 2; ++b) {
+        if (ctx->ev_walked[b]) cudaEventDestroy(ctx->ev_walked[b]);
+        if (ctx->ev_merged[b]) cudaEventDestroy(ctx->ev_merged[b]);
+        ctx->ev_walked[b] = ctx->ev_merged[b] = nullptr;
+    }
+    if (ctx->merge_stream) cudaStreamDestroy(ctx->merge_stream);
+    ctx->merge_stream = nullptr;
     if (ctx->graph_fork) cudaEventDestroy(ctx->graph_fork);
     if (ctx->graph_join) cudaEventDestroy(ctx->graph_join);
     if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
@@ -664,7 +704,13 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
         // replay a captured graph of this exact launch sequence, or capture one,
         // on the private stream, after everything queued so far on the caller's
         if (!ctx->graph_stream) {
-            GFK_CK(ctx, cudaStreamCreateWithFlags(&ctx->graph_stream, cudaStreamNonBlocking));
+            // the highest priority: the walks captured on it run ahead of the
+            // merges captured on merge_stream (lowest), which take the slots a
+            // walk leaves idle (the graph is instantiated with node priorities)
+            int least = 0, greatest = 0;
+            GFK_CK(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            GFK_CK(ctx, cudaStreamCreateWithPriority(&ctx->graph_stream, cudaStreamNonBlocking,
+                                                     greatest));
             GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->graph_fork, cudaEventDisableTiming));
             GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->graph_join, cudaEventDisableTiming));
         }
@@ -699,7 +745,7 @@ gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
             }
             if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
             cudaGraphExec_t exec = nullptr;
-            ce = cudaGraphInstantiate(&exec, graph, 0);
+            ce = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
             cudaGraphDestroy(graph);
             if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
             if (ctx->graphs.size() >= 8) {
@@ -806,7 +852,7 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
                                          bm, ctx->s64, (uint32_t)ctx->steps, chunk, ctx->part, ctx->counters,
                                          ctx->stream);
                 else
-                    e = launch_mixed_walks(ctx, bm, nblk, (uint32_t)ctx->steps, chunk);
+                    e = launch_mixed_walks(ctx, bm, nblk, (uint32_t)ctx->steps, chunk, ctx->part);
                 if (e == cudaSuccess)
                     e = launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
                                            ctx->series_cap, ctx->steps + 1,
