@@ -44,6 +44,12 @@ struct gfk_ctx {
     int64_t part_records = 0;     // capacity in records of each buffer
     cudaStream_t merge_stream = nullptr;          // low priority: fills the walks' idle tails
     cudaEvent_t ev_walked[2] = {nullptr, nullptr}, ev_merged[2] = {nullptr, nullptr};
+    // the specialised launches of one chunk (launch_mixed_walks) after the first
+    // run concurrently on these, forked from and joined to the context's stream
+    static constexpr int kAuxStreams = 3;
+    cudaStream_t aux_stream[kAuxStreams] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_aux[kAuxStreams] = {nullptr, nullptr, nullptr};
     // merged per-step sums, [inst][series_cap]
     SeriesRow* series = nullptr;
     int64_t series_cap = 0;
@@ -247,17 +253,37 @@ std::vector<WalkSegment> walk_segments(const gfk_ctx* ctx, const BlockMap& bm) {
     return v;
 }
 
+// The launches of one chunk touch disjoint blocks, walker slots and record
+// columns, so launches 2, 3, ... run on the auxiliary streams, concurrently
+// with the first (no launch then waits for another's last partial wave).
 cudaError_t launch_mixed_walks(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, uint32_t step0,
                                int chunk, PartialRec* part) {
-    for (const WalkSegment& g : walk_segments(ctx, bm)) {
-        const bool one = same_trials(ctx, g.i0, g.i1);
-        const cudaError_t e = launch_walk_mixed(
-            g.kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk, bm.begin[g.i0],
-            bm.begin[g.i1] - bm.begin[g.i0], ctx->d_inst, bm, ctx->smx, step0, chunk, part,
-            ctx->counters, one ? &ctx->trial[g.i0] : nullptr, ctx->desc[g.i0].ee_on, ctx->stream);
+    const std::vector<WalkSegment> segs = walk_segments(ctx, bm);
+    const bool fork = segs.size() > 1 && ctx->aux_stream[0] != nullptr;
+    const int n_aux = fork ? (int)std::min<size_t>(segs.size() - 1, gfk_ctx::kAuxStreams) : 0;
+    cudaError_t e = cudaSuccess;
+    if (fork) {
+        e = cudaEventRecord(ctx->ev_fork, ctx->stream);
+        for (int j = 0; j < n_aux && e == cudaSuccess; ++j)
+            e = cudaStreamWaitEvent(ctx->aux_stream[j], ctx->ev_fork, 0);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    for (size_t k = 0; k < segs.size(); ++k) {
+        const WalkSegment& g = segs[k];
+        const bool one = same_trials(ctx, g.i0, g.i1);
+        cudaStream_t s = (fork && k > 0) ? ctx->aux_stream[(k - 1) % gfk_ctx::kAuxStreams]
+                                         : ctx->stream;
+        e = launch_walk_mixed(
+            g.kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk, bm.begin[g.i0],
+            bm.begin[g.i1] - bm.begin[g.i0], ctx->d_inst, bm, ctx->smx, step0, chunk, part,
+            ctx->counters, one ? &ctx->trial[g.i0] : nullptr, ctx->desc[g.i0].ee_on, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (int j = 0; j < n_aux && e == cudaSuccess; ++j) {
+        e = cudaEventRecord(ctx->ev_aux[j], ctx->aux_stream[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_aux[j], 0);
+    }
+    return e;
 }
 
 cudaError_t prepare_mixed_walks(const gfk_ctx* ctx, const BlockMap& bm) {
@@ -333,6 +359,12 @@ gfk_status ensure_partials(gfk_ctx* ctx, int64_t nblk, int64_t* rows_fit) {
         for (int b = 0; b < 2; ++b) {
             GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_walked[b], cudaEventDisableTiming));
             GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_merged[b], cudaEventDisableTiming));
+        }
+        GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        for (int j = 0; j < gfk_ctx::kAuxStreams; ++j) {
+            GFK_CK(ctx, cudaStreamCreateWithPriority(&ctx->aux_stream[j], cudaStreamNonBlocking,
+                                                     greatest));
+            GFK_CK(ctx, cudaEventCreateWithFlags(&ctx->ev_aux[j], cudaEventDisableTiming));
         }
     }
     *rows_fit = rows;
@@ -476,6 +508,14 @@ void free_all(gfk_ctx* ctx) {
     }
     if (ctx->merge_stream) cudaStreamDestroy(ctx->merge_stream);
     ctx->merge_stream = nullptr;
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    ctx->ev_fork = nullptr;
+    for (int j = 0; j < gfk_ctx::kAuxStreams; ++j) {
+        if (ctx->aux_stream[j]) cudaStreamDestroy(ctx->aux_stream[j]);
+        if (ctx->ev_aux[j]) cudaEventDestroy(ctx->ev_aux[j]);
+        ctx->aux_stream[j] = nullptr;
+        ctx->ev_aux[j] = nullptr;
+    }
     if (ctx->graph_fork) cudaEventDestroy(ctx->graph_fork);
     if (ctx->graph_join) cudaEventDestroy(ctx->graph_join);
     if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
