@@ -162,7 +162,11 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
                         int32_t* best_walkers_per_thread, double* best_walker_steps_per_s);
 
 /* Advance every instance by n_steps moves (asynchronous on the context's
- * stream).  The first call after gfk_create / gfk_reset initialises the
+ * stream: part of the work runs on the context's own internal streams -- the
+ * merges of the block sums, concurrent launches of several instance groups,
+ * CUDA-graph replays -- ordered after the work already queued on the
+ * context's stream, which in turn waits for all of it before any later work
+ * queued there).  The first call after gfk_create / gfk_reset initialises the
  * population (X0 = init_sigma * xi from the Philox blocks (id, 0, stream, 3/4),
  * log-weight 0) and records the step-0 population sums.  Each move is
  *   X <- X + b(X) dt + sqrt(dt) xi,   b = grad ln|psi|       (the SDE under Eq. 4)
