@@ -6,6 +6,12 @@ initialise 2^20 walkers of the He 1^1S trial function
 exp(-2 r1 - 2 r2) exp(r12 / (2 (1 + 0.5 r12))) and advance them 20000 moves at
 dt = 0.005 on the mixed-precision path (FP32 drift / local energy / normals,
 FP64 log-weights and population sums), with the population sums of every move.
+The same line carries the FP64 path on the same seeds (speed and the mixed
+path's energy error), the rooflines of the walk kernel (FP32 flops counted on
+the oracle's procedure against the measured FFMA rate; special-function unit;
+issue slots), and, under "workloads", the 2^3S, twelve-instance batched and
++-1 Bernoulli walks and the adjoint gradient with 50 Adam steps, each measured
+on its own.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,48 +56,58 @@ WORKLOADS = {
 }
 SEED = 0
 
-# Algorithmic ALU work of one walker-step of the mixed path, counted from the
-# method's definition (one op per multiply, add, compare, reciprocal, square
-# root, log, exp, sine, cosine; a 32x32->64 multiply is one op): with Gaussian
-# noise, Philox4x32-10 at 1.5 blocks per move (120) and Box-Muller x3 (42); with
-# Bernoulli noise, six generator steps (multiply, add) and six threshold
-# compares (18); then the move (12), the trial evaluation (105 ops for the
-# ground-state product, kind 0; 220 for a two-term orbital-pair function,
-# kind 1), the weight and the sums (11).  Keyed by (noise, kind).
-# Orbital pairs whose orbitals have no r or z prefactor terms (the 2^3S trial)
-# do about 12 fewer ops per orbital, 48 per walker-step (key kind 3).
-OPS_PER_WALKER_STEP = {(0, 0): 290, (0, 1): 405, (0, 3): 357,
-                       (1, 0): 146, (1, 1): 261, (1, 3): 213}
-
-
-def _ops_kind(kind, params):
-    """3 for an orbital-pair trial whose orbitals all lack r and z prefactor terms."""
-    if kind != 1:
-        return kind
-    nterms = int(params[6])
-    for t in range(nterms):
-        q = params[7 + 9 * t: 16 + 9 * t]
-        if q[3] != 0 or q[4] != 0 or q[7] != 0 or q[8] != 0:
-            return kind
-    return 3
-# Lanes that can issue an ALU instruction per SM per clock (4 schedulers x 32).
+# Algorithmic work of one walker-step, counted on the oracle's own procedure by
+# oracle/opcount.py (tests/test_op_counts.py checks that these literals equal its
+# output): "flops" = floating-point additions, multiplications and divisions (a
+# fused multiply-add is two), "special" = square roots, exponentials,
+# logarithms, sines and cosines, "int" = the integer operations of the noise.
+# Keyed by (noise, trial case); the cases are the workloads' trial functions
+# per state (0: the 1^1S product, 1: the 2^3S pair, 2: the P_z pair).
+OP_COUNTS = {
+    (0, "ground"): {"flops": 168.0, "special": 18.0, "int": 90.5, "fp_add": 56.0,
+                    "fp_mul": 87.0, "fp_div": 25.0, "fp_sqrt": 6.0, "fp_exp": 3.0,
+                    "fp_log": 3.0, "fp_sin": 3.0, "fp_cos": 3.0},
+    (0, "triplet_2s3"): {"flops": 212.0, "special": 20.0, "int": 90.5, "fp_add": 67.0,
+                         "fp_mul": 112.0, "fp_div": 33.0, "fp_sqrt": 6.0, "fp_exp": 5.0,
+                         "fp_log": 3.0, "fp_sin": 3.0, "fp_cos": 3.0},
+    (0, "pz"): {"flops": 224.0, "special": 20.0, "int": 90.5, "fp_add": 71.0, "fp_mul": 118.0,
+                "fp_div": 35.0, "fp_sqrt": 6.0, "fp_exp": 5.0, "fp_log": 3.0, "fp_sin": 3.0,
+                "fp_cos": 3.0},
+    (1, "ground"): {"flops": 138.0, "special": 6.0, "int": 12.0, "fp_add": 50.0,
+                    "fp_mul": 63.0, "fp_div": 25.0, "fp_sqrt": 3.0, "fp_exp": 3.0,
+                    "fp_log": 0.0, "fp_sin": 0.0, "fp_cos": 0.0},
+    (1, "triplet_2s3"): {"flops": 182.0, "special": 8.0, "int": 12.0, "fp_add": 61.0,
+                         "fp_mul": 88.0, "fp_div": 33.0, "fp_sqrt": 3.0, "fp_exp": 5.0,
+                         "fp_log": 0.0, "fp_sin": 0.0, "fp_cos": 0.0},
+    (1, "pz"): {"flops": 194.0, "special": 8.0, "int": 12.0, "fp_add": 65.0, "fp_mul": 94.0,
+                "fp_div": 35.0, "fp_sqrt": 3.0, "fp_exp": 5.0, "fp_log": 0.0, "fp_sin": 0.0,
+                "fp_cos": 0.0},
+}
+STATE_CASE = {0: "ground", 1: "triplet_2s3", 2: "pz"}
+# Each special operation of the count runs as one special-function-unit
+# instruction on the GPU; the measured rate of that instruction class
+# (gfk_measure_peak) prices it: square root -> rsqrt, exponential -> ex2,
+# logarithm -> lg2, sine and cosine -> sin.
+SPECIAL_UNIT = {"fp_sqrt": "rsq", "fp_exp": "ex2", "fp_log": "lg2", "fp_sin": "sin",
+                "fp_cos": "sin"}
+# Issue slots: 4 schedulers x 32 lanes per SM and clock.
 LANES_PER_SM_CLK = 128
-# DRAM traffic (read + write) of the walk kernel per walker-step, from one ncu
-# capture of a launch of the bench's shape (2^20 walkers x 1024 moves, 128
-# threads x 2 walkers, the launch shape the bench autotunes to), valid only for the kernel sources it was taken
-# on (sha256 prefix of WALK_SOURCES); scaled by the walker-steps of an average launch.
-WALK_TRAFFIC = {       # workload -> capture
-    "ground": {"src_sha": "50abc19209121823", "bytes_per_walker_step": 0.19995},
-    "bernoulli": {"src_sha": "50abc19209121823", "bytes_per_walker_step": 0.19977},
+# ncu figures of the mixed walk kernel at the bench's launch shape (2^20 walkers x
+# 1024 moves, 128 threads x 2 walkers), valid only for the kernel sources they
+# were taken on (sha256 prefix of WALK_SOURCES): DRAM bytes (read + write) and
+# executed thread instructions per walker-step, and the issue-active fraction.
+WALK_PROFILE = {       # workload -> capture
+    "ground": {"src_sha": "50abc19209121823", "bytes_per_walker_step": 0.19995,
+               "inst_per_walker_step": None, "issue_active": None},
+    "bernoulli": {"src_sha": "50abc19209121823", "bytes_per_walker_step": 0.19977,
+                  "inst_per_walker_step": None, "issue_active": None},
 }
 
-
-# Sources the mixed walk kernel is compiled from; a captured traffic figure
-# holds only while they are unchanged.
+# Sources the mixed walk kernel is compiled from (the kernels and the device
+# code they include); a captured figure holds only while they are unchanged.
 WALK_SOURCES = ("paper_1703_08977_gb300/csrc/gfk_mixed.cuh", "paper_1703_08977_gb300/csrc/gfk_mixed.cu",
                 "paper_1703_08977_gb300/csrc/gfk_mixed_bern.cu", "paper_1703_08977_gb300/csrc/gfk_device.cuh",
-                "paper_1703_08977_gb300/csrc/gfk_block.cuh", "paper_1703_08977_gb300/csrc/gfk_types.h",
-                "paper_1703_08977_gb300/csrc/gfk_launch.h", "include/gfk.h")
+                "paper_1703_08977_gb300/csrc/gfk_block.cuh", "paper_1703_08977_gb300/csrc/gfk_types.h")
 
 
 def _src_sha() -> str:
@@ -100,6 +116,25 @@ def _src_sha() -> str:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def _op_counts(insts):
+    """Walker-count-weighted op counts per walker-step of a workload's instances."""
+    n = sum(d["n_walkers"] for d in insts)
+    out = {}
+    for d in insts:
+        c = OP_COUNTS[(d["noise"], STATE_CASE[d["state"]])]
+        for k, v in c.items():
+            out[k] = out.get(k, 0.0) + v * d["n_walkers"] / n
+    return out
+
+
+def bench_config(name, rank=0):
+    """The `config` object of a workload (the same for both arms of the bench)."""
+    insts, moves = _workload(name, rank)
+    n = sum(d["n_walkers"] for d in insts)
+    return {"workload": WORKLOADS[name], "name": name, "walkers_per_gpu": n, "moves": moves,
+            "l2": f"flushed (256 MB write) before every timed step; state {n * 33 / 2**20:.0f} MB"}
 
 
 # ----------------------------------------------------------------------------
@@ -181,14 +216,13 @@ def run_reference(args):
         cores = pool.n
     dt_s = sum(t)
     value = n_sample * moves * args.steps / dt_s
-    sample = (f"{n_sample} walkers x {moves} moves per step (a slice of the 2^20 x 20000 "
-              f"workload), {cores} processes over disjoint walker ids")
+    sample = (f"{n_sample} walkers x {moves} moves per step (a slice of the workload), "
+              f"{cores} processes over disjoint walker ids")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOADS[name], "name": name,
-                                        "sample": sample},
+        "data": "synthetic", "config": bench_config(name),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -279,24 +313,66 @@ def _workload(name, rank):
     return insts, moves
 
 
-def run_adjoint(args):
-    """Workload 5: walker-steps/s of gfk_grad (each walker-step counted once although it
-    is walked forward, recomputed and swept backwards), mixed and FP64, and optionally
-    the 50-step Adam variance minimisation."""
+def measure_peaks():
+    """Measured lane-operation rates (per second, whole GPU) of the instruction classes
+    the rooflines use: FP32 and FP64 fused multiply-add and the special-function unit's
+    ex2, rsqrt, lg2 and sin (gfk_measure_peak, about 10 ms each)."""
+    from paper_1703_08977_gb300 import gfk
+    return {op: gfk.gfk_measure_peak(op) for op in ("ffma", "dfma", "ex2", "rsq", "lg2", "sin")}
+
+
+def walk_rooflines(name, insts, avg_launch_ms, ws_per_launch, peaks, n_sm, sm_max, sm_mhz):
+    """The walk kernel's rooflines from its own launch time: FP32 flops against the
+    measured FFMA rate (the primary figure), the special-function unit against its
+    measured rates, and issue slots from the ncu instruction count."""
+    counts = _op_counts(insts)
+    rate = ws_per_launch / (avg_launch_ms / 1e3)          # walker-steps/s in the walk kernel
+    achieved = counts["flops"] * rate / 1e12
+    peak = 2.0 * peaks["ffma"] / 1e12
+    derived = n_sm * LANES_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    prof = WALK_PROFILE.get(name)
+    valid = bool(prof) and prof["src_sha"] == _src_sha()
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": prof["bytes_per_walker_step"] * ws_per_launch if valid else None,
+            "kernel": "walk_mixed_kernel",
+            "peak_basis": "of measured: FFMA lane rate (gfk_measure_peak, this run) x 2 flops",
+            "peak_derived": derived, "frac_of_derived": achieved / derived,
+            "derived_basis": f"{n_sm} SMs x {LANES_PER_SM_CLK} FP32 lanes x 2 flops x "
+                             f"{sm_max:.0f} MHz",
+            "flops_per_walker_step": counts["flops"],
+            "counts": "oracle/opcount.py (the oracle's walker-step on a counting scalar)",
+            "avg_launch_ms": avg_launch_ms, "walker_steps_per_launch": ws_per_launch}
+    busy = sum(counts[k] / peaks[u] for k, u in SPECIAL_UNIT.items())   # s per walker-step
+    mufu = {"frac": busy * rate, "special_per_walker_step": counts["special"],
+            "basis": "sum over sqrt, exp, log, sin, cos of count / measured rate of "
+                     "rsq, ex2, lg2, sin"}
+    clk = (sm_mhz or sm_max) * 1e6
+    inst = prof.get("inst_per_walker_step") if valid else None
+    issue = {"frac": inst * rate / (n_sm * LANES_PER_SM_CLK * clk) if inst else None,
+             "inst_per_walker_step": inst, "ncu_issue_active": prof.get("issue_active") if valid else None,
+             "basis": f"executed thread instructions (ncu) / ({n_sm} SMs x {LANES_PER_SM_CLK} "
+                      "issue lanes x sampled SM clock)"}
+    return roof, mufu, issue
+
+
+def measure_adjoint(steps, warmup, adam=True):
+    """Workload 5: walker-steps/s of gfk_grad (each walker-step counted once although it is
+    walked forward, recomputed and swept backwards), mixed and FP64, the mixed
+    gradient's error against the FP64 one, and the 50-step Adam variance minimisation."""
     import numpy as np
     import torch
-    ws, rank, local = _dist_env()
-    if rank != 0:
-        return
     from paper_1703_08977_gb300 import gfk, tuning
     n, S, K, dt = 1 << 18, 2000, 64, 0.005
     theta = [2.0, 0.5, 0.5, 0.0, 0.0, 0.0, 0.0]
     res = {}
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     for prec, name in ((gfk.GFK_PREC_MIXED, "mixed"), (gfk.GFK_PREC_FP64, "fp64")):
         d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=-2.9037, seed=SEED, prec=prec)
         with gfk.Context([d], trials=[(0, theta)]) as ctx:
-            reps = args.steps if prec == gfk.GFK_PREC_MIXED else 1
-            for _ in range(1 if prec == gfk.GFK_PREC_FP64 else args.warmup):
+            reps = steps if prec == gfk.GFK_PREC_MIXED else 1
+            for _ in range(warmup if prec == gfk.GFK_PREC_MIXED else 1):
                 gfk.gfk_grad(ctx.handle, 0, 0, S, K)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -304,18 +380,24 @@ def run_adjoint(args):
                 loss, g = gfk.gfk_grad(ctx.handle, 0, 0, S, K)
             el = (time.perf_counter() - t0) / reps
             res[name] = {"value": n * S / el, "seconds": el, "loss": loss, "grad": g.tolist()}
+    clk = clocks.stop()
     gerr = np.abs(np.array(res["mixed"]["grad"]) - np.array(res["fp64"]["grad"])).max() / \
         np.abs(np.array(res["fp64"]["grad"])).max()
     out = {"metric": "gradient walker-steps/sec on 1 GB300 (adjoint through the walk)",
-           "value": res["mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * res["mixed"]["seconds"],
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-           "data": "synthetic", "config": {"workload": WORKLOADS["adjoint"], "name": "adjoint"},
+           "value": res["mixed"]["value"], "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": 1e3 * res["mixed"]["seconds"], "dtype": "f32+f64",
+           "config": {"workload": WORKLOADS["adjoint"], "name": "adjoint"},
            "fp64_path": {"value": res["fp64"]["value"], "unit": UNIT,
                          "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"]},
            "gradient_mixed_vs_fp64_rel": float(gerr),
-           "gpu_launches": 5 + 2 * ((S + K - 1) // K) + 1}
-    if args.adam:
+           "gradient_mixed": res["mixed"]["grad"], "gradient_fp64": res["fp64"]["grad"],
+           "gpu_launches": 5 + 2 * ((S + K - 1) // K) + 1,
+           "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+           "roofline": None,
+           "roofline_note": "the reverse sweep has no algorithmic op count (the counter covers "
+                            "the forward walker-step); ncu figures of its kernel are under "
+                            "profiles/"}
+    if adam:
         d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=-2.9037, seed=SEED,
                              prec=gfk.GFK_PREC_MIXED)
         with gfk.Context([d], trials=[(0, theta)]) as ctx:
@@ -324,25 +406,32 @@ def run_adjoint(args):
                                    n_steps=S, ckpt_every=K)
             out["adam"] = {"steps": 50, "lr": 1e-2, "loss": "weighted variance of E_L",
                            "variance_first": hist[0][0], "variance_last": hist[-1][0],
+                           "variance_min": min(h[0] for h in hist),
                            "theta_final": th.tolist(), "seconds": time.perf_counter() - t0}
+    return out
+
+
+def run_adjoint(args):
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    out = measure_adjoint(args.steps, args.warmup, adam=args.adam)
+    out.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "data": "synthetic"})
     print(json.dumps(out), flush=True)
 
 
-def run_ours(args):
+def measure_walk(name, steps, warmup, *, rank, ws, peaks, n_sm, threads=0, wpt=0,
+                 e2e=False, fp64_moves=0):
+    """One workload on the walk kernels: `steps` device-timed runs after `warmup`, L2
+    flushed before each, clocks sampled.  Returns the fields of its JSON object (and the
+    mixed E(t) of instance 0 for the FP64 comparison)."""
     import numpy as np
     import torch
     import torch.distributed as dist
-
-    ws, rank, local = _dist_env()
-    if ws > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.cuda.current_device()
     from paper_1703_08977_gb300 import gfk
 
-    props = torch.cuda.get_device_properties(dev)
-    n_sm = props.multi_processor_count
-    insts, n_moves = _workload(args.workload, rank)
+    insts, n_moves = _workload(name, rank)
     n_walkers = sum(d["n_walkers"] for d in insts)
     trials = [(d["kind"], d["params"]) for d in insts]
 
@@ -354,9 +443,9 @@ def run_ours(args):
                 for d in insts]
 
     ctx = gfk.Context(descs(gfk.GFK_PREC_MIXED), trials=trials)
-    if args.threads and args.wpt:
-        ctx.set_launch(args.threads, args.wpt)
-        launch = (args.threads, args.wpt, None)
+    if threads and wpt:
+        ctx.set_launch(threads, wpt)
+        launch = (threads, wpt, None)
     else:
         launch = gfk.autotune_cached(ctx.handle, ctx.descs, trials, probe_steps=256)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
@@ -366,21 +455,21 @@ def run_ours(args):
         ctx.reset()
         ctx.propagate(n_moves)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         device_step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K device-resident steps, L2 flushed between them ----
+    # ---- timed region: `steps` device-resident runs, L2 flushed between them ----
     gfk.gfk_profile(ctx.handle, True)
     gfk.gfk_profile_read(ctx.handle, reset=True)
     gfk.gfk_kernel_count(ctx.handle, reset=True)
-    clocks = Clocks(dev)
+    clocks = Clocks(torch.cuda.current_device())
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     evs = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -400,111 +489,136 @@ def run_ours(args):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    ms_per_step = ms / args.steps
     walker_steps_per_step = n_walkers * n_moves
-    value = walker_steps_per_step * ws * args.steps / (ms / 1e3)
+    out = {"value": walker_steps_per_step * ws * steps / (ms / 1e3), "unit": UNIT,
+           "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+           "config": bench_config(name, rank),
+           "launch": {"threads": launch[0], "walkers_per_thread": launch[1],
+                      "chosen_by": "autotune" if launch[2] else "flags"},
+           "gpu_launches": int(kernels_timed),
+           "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    avg_launch_ms = walk_ms / max(1, walk_launches)
+    ws_per_launch = walk_ws / max(1, walk_launches)
+    out["roofline"], out["mufu"], out["issue"] = walk_rooflines(
+        name, insts, avg_launch_ms, ws_per_launch, peaks, n_sm, sm_max, clk.get("sm_mhz"))
 
-    # ---- end to end through the C ABI with host buffers (graph replay) ----
-    cap = n_moves + 1
-    e_host = [np.empty(cap) for _ in insts]
-    lz_host = [np.empty(cap) for _ in insts]
-    ess_host = [np.empty(cap) for _ in insts]
-    h2d = sum(8 * len(p) for _, p in trials) + 1024 * len(insts)   # trial vectors + instance table
-    d2h = len(insts) * (3 * 8 * cap + 8)
-    ctx.set_graph(True)
-    ctx.reset()
-    ctx.propagate(n_moves)              # capture once (outside the timing)
-    torch.cuda.synchronize()
-    n_e2e = max(1, args.steps // 2)
-    t0 = time.perf_counter()
-    for _ in range(n_e2e):
-        gfk.gfk_reset(ctx.handle)
-        for i, (k, p) in enumerate(trials):
-            gfk.gfk_set_trial(ctx.handle, i, k, p)
-        gfk.gfk_propagate(ctx.handle, n_moves)
-        for i in range(len(insts)):
-            gfk.gfk_energy(ctx.handle, i, cap=cap, out=(e_host[i], lz_host[i], ess_host[i]))
-    e2e_s = (time.perf_counter() - t0) / n_e2e
-    e_mixed = e_host[0].copy()
-    merged_e_final = None
-    if ws > 1:
-        # the one exchange step: merge the ranks' per-step sums of instance 0
-        from paper_1703_08977_gb300 import distributed as gd
-        merged = gd.merge_sums(ctx.sums(0))
-        merged_e_final = float(gd.estimators(merged, insts[0]["n_walkers"] * ws)["E"][-1])
+    e_mixed = None
+    if e2e:
+        # ---- end to end through the C ABI with host buffers (graph replay) ----
+        cap = n_moves + 1
+        e_host = [np.empty(cap) for _ in insts]
+        lz_host = [np.empty(cap) for _ in insts]
+        ess_host = [np.empty(cap) for _ in insts]
+        h2d = sum(8 * len(p) for _, p in trials) + 1024 * len(insts)   # trials + instance table
+        d2h = len(insts) * (3 * 8 * cap + 8)
+        ctx.set_graph(True)
+        ctx.reset()
+        ctx.propagate(n_moves)              # capture once (outside the timing)
+        torch.cuda.synchronize()
+        n_e2e = max(1, steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            gfk.gfk_reset(ctx.handle)
+            for i, (k, p) in enumerate(trials):
+                gfk.gfk_set_trial(ctx.handle, i, k, p)
+            gfk.gfk_propagate(ctx.handle, n_moves)
+            for i in range(len(insts)):
+                gfk.gfk_energy(ctx.handle, i, cap=cap, out=(e_host[i], lz_host[i], ess_host[i]))
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+        out["e2e"] = {"value": walker_steps_per_step * ws / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "path": "gfk_set_trial + gfk_propagate (CUDA-graph replay) + gfk_energy "
+                              "into host arrays, wall clock"}
+        e_mixed = e_host[0].copy()
+        if ws > 1:
+            # the one exchange step: merge the ranks' per-step sums of instance 0
+            from paper_1703_08977_gb300 import distributed as gd
+            merged = gd.merge_sums(ctx.sums(0))
+            out["merged_E_final_all_ranks"] = float(
+                gd.estimators(merged, insts[0]["n_walkers"] * ws)["E"][-1])
     ctx.close()
 
+    if fp64_moves and rank == 0:
+        # ---- the FP64 path on the same seeds, and the mixed path's energy error ----
+        if e_mixed is None:
+            with gfk.Context(descs(gfk.GFK_PREC_MIXED), trials=trials) as cm:
+                cm.propagate(fp64_moves)
+                e_mixed = cm.energy(0)["E"]
+        c64 = gfk.Context(descs(gfk.GFK_PREC_FP64), trials=trials)
+        c64.propagate(32)
+        torch.cuda.synchronize()
+        c64.reset()
+        gfk.gfk_profile(c64.handle, True)
+        gfk.gfk_profile_read(c64.handle, reset=True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c64.propagate(fp64_moves)
+        b.record(stream)
+        torch.cuda.synchronize()
+        w64_ms, w64_l, w64_ws = gfk.gfk_profile_read(c64.handle, reset=True)
+        fp64_ms = a.elapsed_time(b)
+        fp64_value = n_walkers * fp64_moves / (fp64_ms / 1e3)
+        e64 = c64.energy(0)["E"]
+        c64.close()
+        counts = _op_counts(insts)
+        r64 = w64_ws / (w64_ms / 1e3)
+        diff = e_mixed[: fp64_moves + 1] - e64
+        tail = diff[len(diff) // 2:]
+        out["fp64_path"] = {
+            "value": fp64_value, "unit": UNIT, "moves": fp64_moves,
+            "mixed_over_fp64": out["value"] / ws / fp64_value,
+            "roofline": {"bound": "alu", "achieved": counts["flops"] * r64 / 1e12,
+                         "peak": 2.0 * peaks["dfma"] / 1e12, "unit": "TFLOP/s",
+                         "frac": counts["flops"] * r64 / (2.0 * peaks["dfma"]),
+                         "kernel": "walk_fp64_kernel",
+                         "peak_basis": "of measured: DFMA lane rate (gfk_measure_peak) x 2 flops",
+                         "note": "FP64 library exp/log/sqrt/sin/cos run as instruction sequences "
+                                 "on the FP64 pipe, beyond the algorithmic flops counted here"}}
+        out["energy_error_vs_fp64"] = {
+            "moves": fp64_moves, "max_abs_E_t": float(np.max(np.abs(diff))),
+            "mean_E_t_second_half": float(np.mean(tail)), "final": float(diff[-1]),
+            "note": "mixed minus FP64 path, same seeds and walkers; the FP64 path "
+                    "matches the FP64 oracle to 1e-13 (tests)"}
+    return out
+
+
+EXTRA_WALKS = ("triplet", "batched", "bernoulli")
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measure_peaks()
+    main_line = measure_walk(args.workload, args.steps, args.warmup, rank=rank, ws=ws,
+                             peaks=peaks, n_sm=n_sm, threads=args.threads, wpt=args.wpt,
+                             e2e=True,
+                             fp64_moves=args.fp64_moves if args.workload in ("ground", "bernoulli")
+                             else 0)
     out = None
     if rank == 0:
-        avg_launch_ms = walk_ms / max(1, walk_launches)
-        ws_per_launch = walk_ws / max(1, walk_launches)
-        sm_max = clk.get("sm_max_mhz") or 2070.0
-        peak = n_sm * LANES_PER_SM_CLK * sm_max * 1e6 / 1e9      # Gop/s
-        ops = sum(OPS_PER_WALKER_STEP[(d["noise"], _ops_kind(d["kind"], d["params"]))]
-                  * d["n_walkers"] for d in insts) / n_walkers
-        achieved = ops * ws_per_launch / (avg_launch_ms / 1e3) / 1e9
-        traffic = None
-        tr = WALK_TRAFFIC.get(args.workload)
-        if tr and tr["src_sha"] == _src_sha():
-            traffic = tr["bytes_per_walker_step"] * ws_per_launch
-        out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
-                       "walkers_per_gpu": n_walkers, "moves": n_moves,
-                       "launch": {"threads": launch[0], "walkers_per_thread": launch[1],
-                                  "chosen_by": "autotune" if launch[2] else "flags"},
-                       "l2": "flushed (256 MB write) before every timed step; state "
-                             f"{n_walkers * 33 / 2**20:.0f} MB"},
-            "gpu_launches": int(kernels_timed),
-            "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-            "e2e": {"value": walker_steps_per_step * ws / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "path": "gfk_set_trial + gfk_propagate (CUDA-graph replay) + gfk_energy "
-                            "into host arrays, wall clock"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "walk_mixed_kernel",
-                         "peak_basis": f"{n_sm} SMs x {LANES_PER_SM_CLK} lanes x {sm_max:.0f} MHz "
-                                       "(instruction-issue limit, derived from unit counts and "
-                                       "clock)",
-                         "ops_per_walker_step": ops,
-                         "avg_launch_ms": avg_launch_ms, "walker_steps_per_launch": ws_per_launch},
-        }
-        try:
-            out["roofline"]["measured_ffma_lane_ops_per_s"] = gfk.gfk_measure_peak("ffma")
-        except Exception:
-            pass
-        if args.workload in ("ground", "bernoulli"):
-            # ---- the FP64 path on the same seeds, and the mixed path's energy error ----
-            n_cmp = args.fp64_moves
-            c64 = gfk.Context(descs(gfk.GFK_PREC_FP64), trials=trials)
-            c64.propagate(32)
-            torch.cuda.synchronize()
-            c64.reset()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            c64.propagate(n_cmp)
-            b.record(stream)
-            torch.cuda.synchronize()
-            fp64_ms = a.elapsed_time(b)
-            fp64_value = n_walkers * n_cmp / (fp64_ms / 1e3)
-            e64 = c64.energy(0)["E"]
-            c64.close()
-            diff = e_mixed[: n_cmp + 1] - e64
-            tail = diff[len(diff) // 2:]
-            out["fp64_path"] = {"value": fp64_value, "unit": UNIT, "moves": n_cmp,
-                                "mixed_over_fp64": value / ws / fp64_value}
-            out["energy_error_vs_fp64"] = {
-                "moves": n_cmp, "max_abs_E_t": float(np.max(np.abs(diff))),
-                "mean_E_t_second_half": float(np.mean(tail)), "final": float(diff[-1]),
-                "note": "mixed minus FP64 path, same seeds and walkers; the FP64 path "
-                        "matches the FP64 oracle to 1e-13 (tests)"}
-        if merged_e_final is not None:
-            out["merged_E_final_all_ranks"] = merged_e_final
+        out = {"metric": METRIC, "n_gpus": ws, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic"}
+        out.update(main_line)
+        out["measured_peaks_lane_ops_per_s"] = peaks
+    extras = {}
+    if ws == 1 and args.workload == "ground" and not args.no_extras:
+        # the other workloads of the scope, each its own measurement (3 warm-up runs,
+        # 3 timed runs, L2 flushed before each, clocks sampled)
+        for name in EXTRA_WALKS:
+            extras[name] = measure_walk(name, 3, 3, rank=rank, ws=ws, peaks=peaks, n_sm=n_sm)
+        extras["adjoint"] = measure_adjoint(3, 3, adam=True)
+    if rank == 0:
+        if extras:
+            out["workloads"] = extras
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(out), flush=True)
@@ -548,6 +662,9 @@ def main():
     ap.add_argument("--wpt", type=int, default=0, help="walkers per thread (0: autotune)")
     ap.add_argument("--fp64-moves", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline workload only (skip the triplet, batched, Bernoulli and "
+                         "adjoint measurements)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small ncu capture case instead of the benchmark")
     ap.add_argument("--prec", type=int, default=1, help="profile case: 1 mixed, 0 FP64")

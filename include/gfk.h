@@ -54,7 +54,10 @@ typedef enum { GFK_1S = 0, GFK_2S3 = 1, GFK_PZ = 2 } gfk_state;
  *                 each walker's log-weight is an FP64 base plus an FP32
  *                 Kahan-compensated sum of increments folded into the base
  *                 every 64 steps; population sums go FP32 within a warp,
- *                 FP64 above it, compensated (TwoSum) across blocks. */
+ *                 FP64 above it; across blocks the sums of weights W and of
+ *                 weighted local energies P are double-doubles (Neumaier
+ *                 sums per thread, TwoSum between threads), as on the FP64
+ *                 path. */
 typedef enum { GFK_PREC_FP64 = 0, GFK_PREC_MIXED = 1 } gfk_prec;
 
 /* Increments of the walk, X <- X + b dt + sqrt(dt) xi.
@@ -281,15 +284,20 @@ gfk_status gfk_kernel_count(gfk_ctx* ctx, int64_t* count, int32_t reset);
  *                   the call when init != 0, accumulated otherwise
  * step0 is the global step of the first move (0 when init != 0).  The call is
  * asynchronous on cuda_stream (NULL = legacy default stream).
+ * The moves are walked in chunks of a multiple of 64 moves (64 at
+ * GFK_NOALLOC_MAX_WALKERS, up to 1024 for smaller populations), so the FP32
+ * log-weight increments are folded into the FP64 base after the same moves
+ * as in gfk_propagate: walkers, per-step sums and counters equal those of a
+ * context with launch shape (256, 2) given the same sequence of calls.
  * It allocates nothing.  Its only other device memory is a file-scope array of
  * GFK_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits; the first call on each device looks up that array's
  * address (make this first call before any stream capture).  All calls share
  * the array, so calls that overlap on the GPU race; each call rewrites what it
  * reads.  Returns GFK_EINVAL for n_walkers above GFK_NOALLOC_MAX_WALKERS (the
- * most whose per-move records fit the array, 16 moves at a time) or any other
- * bad argument, GFK_ECUDA if a launch or copy fails. */
-#define GFK_NOALLOC_SCRATCH_BYTES (16u << 20)
+ * most whose per-move records fit the array, 64 moves at a time) or any other
+ * bad argument, GFK_ECUDA if a launch fails. */
+#define GFK_NOALLOC_SCRATCH_BYTES (32u << 20)
 #define GFK_NOALLOC_MAX_WALKERS (1ll << 22)
 gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32_t trial_kind,
                                  const double* params, int32_t n_params,

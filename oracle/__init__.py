@@ -28,6 +28,12 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                     threshold at 2^31, balance and independence of the +-1 steps.
   run (noise 1)     pinned: a hand-computed Bernoulli step, exact weights for an
                     exact eigenfunction, and the stationary <E_L> closed form.
+  trial_eval_many   pinned: equal to trial_eval point by point (a loop over it).
+  node_distance     pinned: the closed forms 1/(Z sqrt 2) (nodeless product),
+                    |r1 - r2|/sqrt 2 (2^3S pair), |z1 + z2|/sqrt 2 (function 7), 0 on
+                    a node.
+  opcount (module)  pinned: its restatement of a walker-step equals the C walk bit
+                    for bit; its counts follow hand counts of the noise.
 """
 from __future__ import annotations
 
@@ -83,6 +89,9 @@ def _load():
         lib.orc_trial_eval.argtypes = [c.c_int, dp, c.c_int, c.c_int, dp,
                                        c.POINTER(c.c_int), dp, dp, dp]
         lib.orc_trial_eval.restype = c.c_int
+        lib.orc_trial_eval_many.argtypes = [c.c_int, dp, c.c_int, c.c_int, c.c_int64, dp,
+                                            c.POINTER(c.c_int), dp, dp, dp]
+        lib.orc_trial_eval_many.restype = c.c_int
         lib.orc_neumaier_sum.argtypes = [dp, c.c_int64]
         lib.orc_neumaier_sum.restype = c.c_double
         lib.orc_run.argtypes = [c.c_int, dp, c.c_int, c.c_int,
@@ -181,6 +190,50 @@ def trial_eval(kind: int, params, x, ee_on: bool = True):
     if rc != 0:
         raise ValueError("oracle: malformed trial parameter vector")
     return s.value, b, el.value, lp.value
+
+
+def trial_eval_many(kind: int, params, x, ee_on: bool = True):
+    """trial_eval at every row of x (n, 6): (sign (n,), b (n, 6), E_L (n,), ln|psi| (n,))."""
+    lib = _load()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xv = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 6)
+    n = xv.shape[0]
+    s = np.zeros(n, dtype=np.intc)
+    b = np.zeros((n, 6))
+    el = np.zeros(n)
+    lp = np.zeros(n)
+    rc = lib.orc_trial_eval_many(int(kind), _ptr(p, ctypes.c_double), len(p), int(bool(ee_on)),
+                                 n, _ptr(xv, ctypes.c_double), _ptr(s, ctypes.c_int),
+                                 _ptr(b, ctypes.c_double), _ptr(el, ctypes.c_double),
+                                 _ptr(lp, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle: malformed trial parameter vector")
+    return s, b, el, lp
+
+
+def without_jastrow(kind: int, params):
+    """The parameter vector with the Jastrow factor removed (a = 0, c_k = 0), so that
+    psi = Phi: the orbital part alone, which carries every node."""
+    p = [float(v) for v in params]
+    if int(kind) == KIND_JASTROW_PRODUCT:
+        p = p[:1] + [0.0] + p[2:3] + [0.0] * max(0, len(p) - 3)
+    else:
+        p[0] = 0.0
+        p[2:6] = [0.0, 0.0, 0.0, 0.0]
+    return p
+
+
+def node_distance(kind: int, params, x) -> np.ndarray:
+    """First-order distance (bohr, in R^6) from each row of x (n, 6) to the nodal
+    surface Phi = 0 of the trial function: |Phi| / |grad Phi| = 1 / |grad ln|Phi||,
+    from the oracle's drift of the trial function without its Jastrow factor (which
+    has no zeros).  Exact for a planar node; 0 on the node; for a nodeless Phi it is
+    the inverse of the orbital drift, e.g. 1 / (Z sqrt 2) for exp(-Z r1 - Z r2)."""
+    s, b, _, _ = trial_eval_many(kind, without_jastrow(kind, params), x, ee_on=True)
+    g = np.sqrt((b * b).sum(axis=1))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d = np.where(s == 0, 0.0, 1.0 / g)
+    return d
 
 
 def neumaier_sum(v) -> float:

@@ -387,6 +387,27 @@ int orc_trial_eval(int kind, const double* params, int n_params, int ee_on,
     return 0;
 }
 
+/* The same evaluation at n points x[6 i .. 6 i + 5] (a loop over orc_eval,
+ * for tests that evaluate whole populations).  Any output may be NULL.
+ * Returns 0, or -1 on bad params. */
+int orc_trial_eval_many(int kind, const double* params, int n_params, int ee_on,
+                        int64_t n, const double* x, int* sign, double* b, double* el,
+                        double* lnpsi)
+{
+    orc_trial t;
+    if (orc_trial_parse(kind, params, n_params, &t) != 0) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int s;
+        double bi[6], e, lp;
+        orc_eval(&t, ee_on, x + 6 * i, &s, bi, &e, &lp);
+        if (sign) sign[i] = s;
+        if (b) for (int d = 0; d < 6; ++d) b[6 * i + d] = bi[d];
+        if (el) el[i] = e;
+        if (lnpsi) lnpsi[i] = lp;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Compensated summation (Neumaier 1974)                                    */
 /* ------------------------------------------------------------------------ */

@@ -42,7 +42,12 @@ struct gfk_ctx {
     PartialRec* part = nullptr;
     PartialRec* part_buf[2] = {nullptr, nullptr};
     int64_t part_records = 0;     // capacity in records of each buffer
-    cudaStream_t merge_stream = nullptr;          // low priority: fills the walks' idle tails
+    // low priority: fills the walks' idle tails.  The ordering by priority
+    // holds fully under graph replay (graph_stream and the auxiliary streams
+    // have the highest priority); without graphs the first launch of a chunk
+    // runs on the caller's stream, whose priority is usually the default
+    // (lowest) one, so a merge then competes with it on equal terms
+    cudaStream_t merge_stream = nullptr;
     cudaEvent_t ev_walked[2] = {nullptr, nullptr}, ev_merged[2] = {nullptr, nullptr};
     // the specialised launches of one chunk (launch_mixed_walks) after the first
     // run concurrently on these, forked from and joined to the context's stream
@@ -256,19 +261,24 @@ std::vector<WalkSegment> walk_segments(const gfk_ctx* ctx, const BlockMap& bm) {
 // The launches of one chunk touch disjoint blocks, walker slots and record
 // columns, so launches 2, 3, ... run on the auxiliary streams, concurrently
 // with the first (no launch then waits for another's last partial wave).
+// Every auxiliary stream that was forked is joined back to the context's
+// stream before this returns, also when a launch fails (a capture would
+// otherwise end with unjoined work); the first error is returned.
 cudaError_t launch_mixed_walks(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, uint32_t step0,
                                int chunk, PartialRec* part) {
     const std::vector<WalkSegment> segs = walk_segments(ctx, bm);
     const bool fork = segs.size() > 1 && ctx->aux_stream[0] != nullptr;
     const int n_aux = fork ? (int)std::min<size_t>(segs.size() - 1, gfk_ctx::kAuxStreams) : 0;
     cudaError_t e = cudaSuccess;
+    int n_forked = 0;
     if (fork) {
         e = cudaEventRecord(ctx->ev_fork, ctx->stream);
-        for (int j = 0; j < n_aux && e == cudaSuccess; ++j)
+        for (int j = 0; j < n_aux && e == cudaSuccess; ++j) {
             e = cudaStreamWaitEvent(ctx->aux_stream[j], ctx->ev_fork, 0);
-        if (e != cudaSuccess) return e;
+            if (e == cudaSuccess) ++n_forked;
+        }
     }
-    for (size_t k = 0; k < segs.size(); ++k) {
+    for (size_t k = 0; k < segs.size() && e == cudaSuccess; ++k) {
         const WalkSegment& g = segs[k];
         const bool one = same_trials(ctx, g.i0, g.i1);
         cudaStream_t s = (fork && k > 0) ? ctx->aux_stream[(k - 1) % gfk_ctx::kAuxStreams]
@@ -277,11 +287,11 @@ cudaError_t launch_mixed_walks(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, u
             g.kind, ctx->noise, ctx->wpt, ctx->threads, (int)nblk, bm.begin[g.i0],
             bm.begin[g.i1] - bm.begin[g.i0], ctx->d_inst, bm, ctx->smx, step0, chunk, part,
             ctx->counters, one ? &ctx->trial[g.i0] : nullptr, ctx->desc[g.i0].ee_on, s);
-        if (e != cudaSuccess) return e;
     }
-    for (int j = 0; j < n_aux && e == cudaSuccess; ++j) {
-        e = cudaEventRecord(ctx->ev_aux[j], ctx->aux_stream[j]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_aux[j], 0);
+    for (int j = 0; j < n_forked; ++j) {
+        cudaError_t ej = cudaEventRecord(ctx->ev_aux[j], ctx->aux_stream[j]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(ctx->stream, ctx->ev_aux[j], 0);
+        if (e == cudaSuccess) e = ej;
     }
     return e;
 }
@@ -418,7 +428,7 @@ gfk_status enqueue_init(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk) {
                                       ctx->part, ctx->counters, ctx->stream));
     }
     GFK_CK(ctx, launch_reduce_rows(ctx->part, (int)nblk, bm, 1, ctx->series, ctx->series_cap, 0,
-                                   ctx->prec == GFK_PREC_FP64, ctx->stream));
+                                   ctx->stream));
     ctx->kernels += 2;                                  // the init and its merge
     return GFK_OK;
 }
@@ -430,8 +440,9 @@ gfk_status profile_pair(gfk_ctx* ctx, cudaEvent_t* a, cudaEvent_t* b);
 // merge runs on the low-priority merge stream, so that its blocks take the
 // slots the next walk leaves idle in its last partial wave.  The walk of
 // chunk c waits for the merge of chunk c - 2 (the same buffer), and the
-// context's stream waits for every merge before this returns (in a graph
-// capture these waits join the merge stream into the graph).
+// context's stream waits for every merge queued before this returns, on
+// success and on failure alike (in a graph capture these waits join the merge
+// stream into the graph).
 gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t rows_fit,
                          int64_t step_begin, int64_t n_steps, bool events) {
     const int kind = launch_kind(ctx);
@@ -439,43 +450,59 @@ gfk_status enqueue_moves(gfk_ctx* ctx, const BlockMap& bm, int64_t nblk, int64_t
     for (int i = 0; i < ctx->n_inst; ++i) walkers += ctx->desc[i].n_walkers;
     int64_t done = 0;
     int64_t c = 0;                                      // chunk index
+    bool merged_any[2] = {false, false};
+    gfk_status st = GFK_OK;
+#define EM_CK(call)                                                    \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) { st = cuda_fail(ctx, e_, #call); goto join; } \
+    } while (0)
     while (done < n_steps) {
         const int chunk = (int)std::min<int64_t>(n_steps - done, rows_fit);
         const uint32_t step0 = (uint32_t)(step_begin + done);
         const int b = (int)(c & 1);
         PartialRec* const part = ctx->part_buf[b];
-        if (c >= 2) GFK_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_merged[b], 0));
+        if (c >= 2) EM_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_merged[b], 0));
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (events) {
-            gfk_status st = profile_pair(ctx, &ev0, &ev1);
-            if (st != GFK_OK) return st;
+            st = profile_pair(ctx, &ev0, &ev1);
+            if (st != GFK_OK) goto join;
         }
-        if (ev0) GFK_CK(ctx, cudaEventRecord(ev0, ctx->stream));
+        if (ev0) EM_CK(cudaEventRecord(ev0, ctx->stream));
         if (ctx->prec == GFK_PREC_FP64) {
-            GFK_CK(ctx, launch_walk_fp64(kind, ctx->noise, ctx->threads, (int)nblk, ctx->d_inst,
-                                         bm, ctx->s64, step0, chunk, part, ctx->counters, ctx->stream));
+            EM_CK(launch_walk_fp64(kind, ctx->noise, ctx->threads, (int)nblk, ctx->d_inst,
+                                   bm, ctx->s64, step0, chunk, part, ctx->counters, ctx->stream));
         } else {
-            GFK_CK(ctx, launch_mixed_walks(ctx, bm, nblk, step0, chunk, part));
+            EM_CK(launch_mixed_walks(ctx, bm, nblk, step0, chunk, part));
             ctx->kernels += (int64_t)walk_segments(ctx, bm).size() - 1;   // + 1 below
         }
         if (ev1) {
-            GFK_CK(ctx, cudaEventRecord(ev1, ctx->stream));
+            EM_CK(cudaEventRecord(ev1, ctx->stream));
             ctx->prof_launches += 1;
             ctx->prof_walker_steps += (double)walkers * chunk;
         }
         ctx->kernels += 2;                              // the walk and the merge
-        GFK_CK(ctx, cudaEventRecord(ctx->ev_walked[b], ctx->stream));
-        GFK_CK(ctx, cudaStreamWaitEvent(ctx->merge_stream, ctx->ev_walked[b], 0));
-        GFK_CK(ctx, launch_reduce_rows(part, (int)nblk, bm, chunk, ctx->series,
-                                       ctx->series_cap, step_begin + done + 1,
-                                       ctx->prec == GFK_PREC_FP64, ctx->merge_stream));
-        GFK_CK(ctx, cudaEventRecord(ctx->ev_merged[b], ctx->merge_stream));
+        EM_CK(cudaEventRecord(ctx->ev_walked[b], ctx->stream));
+        EM_CK(cudaStreamWaitEvent(ctx->merge_stream, ctx->ev_walked[b], 0));
+        merged_any[b] = true;
+        EM_CK(launch_reduce_rows(part, (int)nblk, bm, chunk, ctx->series,
+                                 ctx->series_cap, step_begin + done + 1,
+                                 ctx->merge_stream));
+        EM_CK(cudaEventRecord(ctx->ev_merged[b], ctx->merge_stream));
         done += chunk;
         ++c;
     }
-    for (int64_t b = 0; b < std::min<int64_t>(c, 2); ++b)
-        GFK_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_merged[b], 0));
-    return GFK_OK;
+#undef EM_CK
+join:
+    // the merge stream's work (including whatever a failed step left queued on
+    // it) is ordered before anything later on the context's stream
+    for (int b = 0; b < 2; ++b) {
+        if (!merged_any[b]) continue;
+        cudaError_t e = cudaEventRecord(ctx->ev_merged[b], ctx->merge_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_merged[b], 0);
+        if (e != cudaSuccess && st == GFK_OK) st = cuda_fail(ctx, e, "join of the merge stream");
+    }
+    return st;
 }
 
 gfk_status check_inst(gfk_ctx* ctx, int32_t inst) {
@@ -895,8 +922,7 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
                     e = launch_mixed_walks(ctx, bm, nblk, (uint32_t)ctx->steps, chunk, ctx->part);
                 if (e == cudaSuccess)
                     e = launch_reduce_rows(ctx->part, (int)nblk, bm, chunk, ctx->series,
-                                           ctx->series_cap, ctx->steps + 1,
-                                           ctx->prec == GFK_PREC_FP64, ctx->stream);
+                                           ctx->series_cap, ctx->steps + 1, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(b);
                 float ms = 0.f;

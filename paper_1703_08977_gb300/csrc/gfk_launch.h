@@ -51,10 +51,10 @@ inline int mixed_walk_kind(int kind, const TrialHost* trials, int n) {
 // launched (the shared-memory opt-in of 512-thread blocks); called before a
 // stream capture, where it could not happen.
 cudaError_t prepare_walk_mixed(int kind, int noise, int wpt, int threads, bool one_trial);
-// compensated: double-double W and P (the FP64 path); plain FP64 sums otherwise
+// W and P are merged as double-doubles (compensated) on both paths
 cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
                                SeriesRow* series, int64_t series_cap, int64_t row_base,
-                               bool compensated, cudaStream_t stream);
+                               cudaStream_t stream);
 cudaError_t launch_finalize(const SeriesRow* rows, int64_t n, double n0, double* e, double* lnz,
                             double* ess, cudaStream_t stream);
 cudaError_t launch_export(bool mixed, const StateF64& s64, const StateMixed& smx, int64_t off,

@@ -12,12 +12,18 @@
 // The array holds the instance record and the per-(move, block) population
 // records of one chunk of moves (the scratch the walk kernel writes and the
 // merge kernel reads).  Every call shares it, and it keeps the last call's
-// contents: each call rewrites the instance record and every record it later
-// reads, so nothing in it has to start at zero.  Calls whose work overlaps on
-// the GPU (two streams, or two host threads) race on it.
+// contents: each call rewrites the instance record (with a one-thread kernel
+// that receives it as a launch argument, so no host buffer has to outlive the
+// call) and every record it later reads, so nothing in it has to start at
+// zero.  Calls whose work overlaps on the GPU (two streams, or two host
+// threads) race on it.
 //
 // The kernels launched are the library's own mixed init / walk / merge
-// kernels; only the memory they are given differs from gfk_propagate.
+// kernels; only the memory they are given differs from gfk_propagate.  The
+// moves of a call are walked in chunks whose lengths are multiples of the
+// walk's 64-move fold window (except the last), so the FP32 log-weight
+// increments are folded after the same moves as in gfk_propagate and the
+// results equal gfk_propagate's bit for bit for the same sequence of calls.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -42,6 +48,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GFK_NOALLOC_SCR
 
 constexpr int kThreads = 256;   // launch shape of this entry point
 constexpr int kWpt = 2;
+// GFK_NOALLOC_MAX_WALKERS walkers need one fold window of records per chunk
+static_assert((GFK_NOALLOC_SCRATCH_BYTES - kHeaderBytes) / sizeof(PartialRec) >=
+                  (size_t)kRing * (GFK_NOALLOC_MAX_WALKERS / (kThreads * kWpt)),
+              "the scratch must hold 64 moves of block records at the largest population");
+
+// Writes the instance record into the scratch (one thread; the record arrives
+// as a launch argument).
+__global__ void put_instance_kernel(InstDev rec, InstDev* dst) { *dst = rec; }
 
 // Device address of the scratch, looked up once per device with that device
 // current (in host code the symbol itself is only a host-side stand-in).
@@ -95,7 +109,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     if (st != GFK_OK) return st;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
-    // instance record (host copy staged by the runtime before the call returns)
+    // instance record
     InstDev inst;
     std::memset(&inst, 0, sizeof(inst));
     inst.n = d.n_walkers;
@@ -130,10 +144,12 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     const int nblk = (int)((d.n_walkers + per_block - 1) / per_block);
     bm.begin[0] = 0;
     bm.begin[1] = nblk;
+    // chunk length: as many moves as the records fit, up to 1024, rounded down
+    // to a multiple of the fold window (at GFK_NOALLOC_MAX_WALKERS: 64 moves)
     const int64_t rec_cap = (int64_t)((GFK_NOALLOC_SCRATCH_BYTES - kHeaderBytes) / sizeof(PartialRec));
     int64_t rows_fit = rec_cap / nblk;
-    rows_fit = rows_fit > 1024 ? 1024 : (rows_fit / 16) * 16;
-    if (rows_fit < 16) return GFK_EINVAL;      // cannot happen below GFK_NOALLOC_MAX_WALKERS
+    rows_fit = rows_fit > 1024 ? 1024 : (rows_fit / kRing) * kRing;
+    if (rows_fit < kRing) return GFK_EINVAL;   // cannot happen up to GFK_NOALLOC_MAX_WALKERS
 
     StateMixed sm{};
     sm.p0 = (float4*)dev_p0;
@@ -150,11 +166,12 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
             return GFK_ECUDA;                        \
         }                                            \
     } while (0)
-    NA_CK(cudaMemcpyAsync(d_inst, &inst, sizeof(inst), cudaMemcpyHostToDevice, stream));
+    put_instance_kernel<<<1, 1, 0, stream>>>(inst, d_inst);
+    NA_CK(cudaGetLastError());
     if (init) {
         NA_CK(cudaMemsetAsync(dev_counters, 0, sizeof(unsigned long long) * kNumCounters, stream));
         NA_CK(launch_init_mixed(kind, kThreads, nblk, d_inst, bm, sm, part, dev_counters, stream));
-        NA_CK(launch_reduce_rows(part, nblk, bm, 1, rows, n_rows, 0, false, stream));
+        NA_CK(launch_reduce_rows(part, nblk, bm, 1, rows, n_rows, 0, stream));
     }
     int64_t done = 0;
     while (done < n_steps) {
@@ -163,7 +180,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
                                 0, nblk, d_inst, bm, sm,
                                 (uint32_t)(step0 + done), chunk, part, dev_counters, &trial,
                                 inst.ee_on, stream));
-        NA_CK(launch_reduce_rows(part, nblk, bm, chunk, rows, n_rows, (init ? 1 : 0) + done, false,
+        NA_CK(launch_reduce_rows(part, nblk, bm, chunk, rows, n_rows, (init ? 1 : 0) + done,
                                  stream));
         done += chunk;
     }

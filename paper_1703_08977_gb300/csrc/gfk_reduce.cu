@@ -5,14 +5,12 @@
 // block records {c_b, W_b, P_b, Q_b, R_b, n_b} into
 //   C = max_b c_b,  W = sum_b W_b e^{c_b - C},  P = sum_b P_b e^{c_b - C},
 //   Q = sum_b Q_b e^{2 (c_b - C)},  R = sum_b R_b e^{c_b - C},  n = sum_b n_b.
-// On the FP64 path (COMP) W and P (the energy's denominator and numerator) are
-// carried as unevaluated double-doubles (Neumaier compensation per thread,
-// TwoSum across threads), so E = P / W is the quotient of correctly rounded
-// sums up to O(2^-100).  The mixed path's block sums are FP32-accurate, so it
-// adds W and P in plain FP64 (relative error ~1e-13 over thousands of blocks,
-// far below its 1e-9 hartree energy error) at half the FP64 arithmetic, which
-// is what bounds this kernel here.  Q and R (effective sample size, variance)
-// are plain FP64 sums;
+// W and P (the energy's denominator and numerator: Eq. 4's z(t) and the
+// space-averaged energy) are carried as unevaluated double-doubles on both
+// paths -- a Neumaier-compensated sum per thread, TwoSum across the threads
+// of a warp and across warps -- so E = P / W is the quotient of sums correct
+// to O(2^-100) relative, independent of the number of blocks and of their
+// order.  Q and R (effective sample size, variance) are plain FP64 sums;
 // n is an integer count, exact in FP64.  The shifts c_b are integer-valued, so
 // the factors e^{c_b - C} for C - c_b < kExpTable come from a table the block
 // fills once with the same exp calls (the FP64 exponential per record was what
@@ -48,7 +46,6 @@ __device__ __forceinline__ DD dd_shfl_xor(DD v, int o) {
 constexpr int kReduceThreads = 256;
 constexpr int kExpTable = 64;   // e^{-k}, k = 0 .. kExpTable - 1
 
-template <bool COMP>
 __global__ void __launch_bounds__(kReduceThreads)
 reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
                    SeriesRow* __restrict__ series, int64_t series_cap, int64_t row_base) {
@@ -82,17 +79,12 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
         if (k >= 0.0 && k < (double)kExpTable && (double)(int)k == k) f = s_exp[(int)k];
         else f = exp(-k);
         const double w = r.W * f, p = r.P * f;
-        if (COMP) {
-            double t = sW + w;
-            cW += fabs(sW) >= fabs(w) ? (sW - t) + w : (w - t) + sW;
-            sW = t;
-            t = sP + p;
-            cP += fabs(sP) >= fabs(p) ? (sP - t) + p : (p - t) + sP;
-            sP = t;
-        } else {
-            sW += w;
-            sP += p;
-        }
+        double t = sW + w;
+        cW += fabs(sW) >= fabs(w) ? (sW - t) + w : (w - t) + sW;
+        sW = t;
+        t = sP + p;
+        cP += fabs(sP) >= fabs(p) ? (sP - t) + p : (p - t) + sP;
+        sP = t;
         sQ += r.Q * f * f;
         sR += r.R * f;
         sN += r.n;
@@ -100,7 +92,7 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
     DD acc[5] = {{sW, cW}, {sP, cP}, {sQ, 0.0}, {sR, 0.0}, {sN, 0.0}};
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        if (COMP && k < 2) {
+        if (k < 2) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc[k] = dd_add(acc[k], dd_shfl_xor(acc[k], o));
         } else {
@@ -114,7 +106,7 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
         for (int k = 0; k < 5; ++k) {
             tot[k] = s_acc[k][0];
             for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-                if (COMP && k < 2) tot[k] = dd_add(tot[k], s_acc[k][w]);
+                if (k < 2) tot[k] = dd_add(tot[k], s_acc[k][w]);
                 else tot[k].hi += s_acc[k][w].hi;
             }
         }
@@ -177,14 +169,10 @@ __global__ void export_mixed_kernel(StateMixed st, int64_t off, int64_t n, doubl
 
 cudaError_t launch_reduce_rows(const PartialRec* part, int nblk, const BlockMap& bm, int rows,
                                SeriesRow* series, int64_t series_cap, int64_t row_base,
-                               bool compensated, cudaStream_t stream) {
+                               cudaStream_t stream) {
     dim3 grid(rows, bm.n_inst);
-    if (compensated)
-        reduce_rows_kernel<true><<<grid, kReduceThreads, 0, stream>>>(part, nblk, bm, series,
-                                                                      series_cap, row_base);
-    else
-        reduce_rows_kernel<false><<<grid, kReduceThreads, 0, stream>>>(part, nblk, bm, series,
-                                                                       series_cap, row_base);
+    reduce_rows_kernel<<<grid, kReduceThreads, 0, stream>>>(part, nblk, bm, series, series_cap,
+                                                            row_base);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_normal_moments", "gfk_kernel_count")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
             "i2f", "f2f")
-GFK_NOALLOC_SCRATCH_BYTES = 16 << 20
+GFK_NOALLOC_SCRATCH_BYTES = 32 << 20
 GFK_NOALLOC_MAX_WALKERS = 1 << 22
 
 

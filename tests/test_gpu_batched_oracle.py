@@ -1,0 +1,101 @@
+"""The batched, graph-replayed, autotuned launch of the twelve-instance workload
+({1^1S, 2^3S, P_z} x dt {0.01, 0.005, 0.0025, 0.00125}, uneven walker counts drawn
+log-uniformly as in workloads.batched, here at 1/256 of the benchmark's counts),
+checked walker by walker and step by step against the oracle (GPU).
+
+Each instance is an independent replication set of the space average (the
+law-of-large-numbers step after the invariance principle), so the oracle replays
+each instance alone, with its own Philox stream, and the batched launch must give
+every walker of every instance the oracle's trajectory.
+
+FP64 path: every walker whose oracle trajectory stays at least NODE_DISTANCE bohr
+from the node of its trial function agrees to 1e-12 (positions and log-weight); the
+others (counted) to 1e-8; kills agree for all; E(t) agrees to 1e-13 relative plus
+the near-node walkers' share (oracle_tracks.energy_error_budget), which is zero for
+the nodeless 1^1S instances.
+Mixed path: kill decisions agree for every walker whose oracle trajectory stays at
+least NODE_DISTANCE_FP32 bohr from the node (FP32 positions are ~1e-5 bohr from the
+FP64 ones after a few hundred moves), positions stay at FP32 distance.
+"""
+import numpy as np
+import pytest
+
+from oracle_tracks import NODE_DISTANCE, energy_error_budget, walk_tracking_node
+from paper_1703_08977_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+NODE_DISTANCE_FP32 = 1e-2
+MOVES = (150, 70)
+
+
+def _run_batched(gfk, prec):
+    insts, _ = wl.batched(scale=1.0 / 256)
+    descs = [gfk.InstanceDesc(n_walkers=q["n_walkers"], dt=q["dt"], e_trial=q["e_trial"],
+                              seed=q["seed"], state=q["state"], prec=prec,
+                              rng_stream=q["rng_stream"]) for q in insts]
+    trials = [(q["kind"], q["params"]) for q in insts]
+    ctx = gfk.Context(descs, trials=trials)
+    ctx.set_graph(True)
+    shape = gfk.gfk_autotune(ctx.handle, 64)[:2]
+    for m in MOVES:
+        ctx.propagate(m)
+    out = [(ctx.walkers(i), ctx.energy(i)["E"], ctx.counters(i)) for i in range(len(insts))]
+    # replay both captured graphs after a reset: the same walkers and sums
+    ctx.reset()
+    for m in MOVES:
+        ctx.propagate(m)
+    for i in range(len(insts)):
+        for u, v in zip(out[i][0], ctx.walkers(i)):
+            np.testing.assert_array_equal(u, v)
+        np.testing.assert_array_equal(out[i][1], ctx.energy(i)["E"])
+    ctx.close()
+    return insts, out, shape
+
+
+def _oracle(q, keep_series):
+    return walk_tracking_node(q["kind"], q["params"], n_walkers=q["n_walkers"], steps=sum(MOVES),
+                              dt=q["dt"], e_trial=q["e_trial"], seed=q["seed"],
+                              inst=q["rng_stream"], keep_series=keep_series)
+
+
+def test_batched_fp64_matches_oracle(gfk_lib):
+    gfk = gfk_lib
+    insts, out, shape = _run_batched(gfk, gfk.GFK_PREC_FP64)
+    n_near = 0
+    for q, ((x, lw, al), E, cnt) in zip(insts, out):
+        w, d_min, k_near = _oracle(q, keep_series=True)
+        a = w.alive.astype(bool)
+        np.testing.assert_array_equal(al.astype(bool), a)
+        np.testing.assert_array_equal(cnt[:2], w.counters[:2])
+        assert np.all(np.isneginf(lw[~a]))
+        dx = np.abs(x - w.x).max(axis=1) / np.maximum(1.0, np.abs(w.x).max(axis=1))
+        dl = np.zeros_like(dx)
+        dl[a] = np.abs(lw[a] - w.logw[a]) / np.maximum(1.0, np.abs(w.logw[a]))
+        dev = np.maximum(dx, dl)
+        near = d_min < NODE_DISTANCE
+        n_near += int(near.sum())
+        if q["state"] == 0:
+            assert not near.any()          # the ground state has no node
+        assert dev[~near].max(initial=0.0) <= 1e-12, (q["state"], q["dt"], dev[~near].max())
+        assert dev[near].max(initial=0.0) <= 1e-8, (q["state"], q["dt"], dev[near].max())
+        s = w.series()["E"]
+        bound = energy_error_budget(w, k_near)
+        assert np.all(np.abs(E - s) <= bound), (q["state"], q["dt"], np.max(np.abs(E - s) / bound))
+    print(f"launch shape {shape}, near-node walkers {n_near}")
+
+
+def test_batched_mixed_matches_oracle(gfk_lib):
+    gfk = gfk_lib
+    insts, out, shape = _run_batched(gfk, gfk.GFK_PREC_MIXED)
+    for q, ((x, lw, al), E, cnt) in zip(insts, out):
+        w, d_min, _ = _oracle(q, keep_series=False)
+        a = w.alive.astype(bool)
+        far = d_min >= NODE_DISTANCE_FP32
+        np.testing.assert_array_equal(al.astype(bool)[far], a[far])
+        both = a & al.astype(bool) & far
+        dx = np.abs(x - w.x).max(axis=1)[both]
+        assert np.median(dx) < 1e-5 and np.quantile(dx, 0.99) < 1e-3, (np.median(dx), dx.max())
+        dl = np.abs(lw - w.logw)[both]
+        assert np.median(dl) < 1e-5, np.median(dl)
+        assert np.max(np.abs(E - w.series()["E"])) < 2e-4

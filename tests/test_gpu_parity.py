@@ -2,9 +2,10 @@
 
 FP64 path: per walker |dX|_inf <= 1e-12 max(1, |X|_inf) and
 |dlogw| <= 1e-12 max(1, |logw|); per step |dE| <= 1e-13 |E|.  Walkers of the
-excited states that pass within 1e-6 bohr of the node are ill-conditioned
-(the drift there is ~1/distance, so one-ulp differences in exp() between the
-two libms are amplified); they are compared with a looser bound and counted.
+excited states whose oracle trajectory passes within NODE_DISTANCE bohr of the
+node are ill-conditioned (the drift there is ~1/distance, so one-ulp
+differences in exp() between the two libms are amplified); they are compared
+with a looser bound, and E(t) with a bound that adds their share.
 """
 import math
 
@@ -12,12 +13,16 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle_tracks import NODE_DISTANCE, energy_error_budget, walk_tracking_node
 from paper_1703_08977_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
 REL_WALKER = 1e-12
 REL_E = 1e-13
+# FP32 positions are ~1e-5 bohr from the FP64 ones after a few hundred moves; a
+# walker whose trajectory comes closer than this to the node may straddle it
+NODE_DISTANCE_FP32 = 1e-2
 
 
 def _gpu_run(gfk, kind, params, n, steps, dt, et, seed, prec, stream_id=0, ee_on=1,
@@ -76,7 +81,11 @@ def test_fp64_ground_state_config_full(gfk_lib):
 @pytest.mark.parametrize("name", ["triplet_2s3", "pz_plus", "fn3", "fn7", "ground_poly"])
 def test_fp64_trial_families_ragged(gfk_lib, name):
     """Every trial family on a ragged population (several blocks plus a partial one),
-    300 steps, compared walker by walker; node kills must agree exactly."""
+    300 steps, compared walker by walker; node kills must agree exactly.  Walkers whose
+    oracle trajectory stays at least NODE_DISTANCE bohr from the node of the trial
+    function (all walkers of the nodeless ground state) agree to 1e-12; the near-node
+    ones, ill-conditioned by the ~1/distance drift there, to 1e-8; E(t) to 1e-13
+    relative plus the near-node walkers' share of it."""
     gfk = gfk_lib
     kind, p, et = {
         "triplet_2s3": (1, wl.triplet_2s3(), -2.175),
@@ -87,15 +96,19 @@ def test_fp64_trial_families_ragged(gfk_lib, name):
     }[name]
     n, steps, dt, seed = 1000 + 37, 300, 0.01, 7
     g = _gpu_run(gfk, kind, p, n, steps, dt, et, seed, gfk.GFK_PREC_FP64, stream_id=3)
-    w = _oracle_run(kind, p, n, steps, dt, et, seed, stream_id=3)
+    w, d_min, k_near = walk_tracking_node(kind, p, n_walkers=n, steps=steps, dt=dt, e_trial=et,
+                                          seed=seed, inst=3, keep_series=True)
     dx, dl = _walker_errors(g, w)
-    bad = (dx > REL_WALKER) | (dl > REL_WALKER)
-    # ill-conditioned walkers (near a node) may drift apart at the 1e-12 level; they
-    # must be rare and still agree to 1e-8
-    assert bad.sum() <= max(2, n // 200), (bad.sum(), dx.max(), dl.max())
-    assert dx.max() <= 1e-8 and dl.max() <= 1e-8, (dx.max(), dl.max())
+    dev = np.maximum(dx, dl)
+    near = d_min < NODE_DISTANCE
+    if kind == 0:
+        assert not near.any()
+    assert dev[~near].max(initial=0.0) <= REL_WALKER, dev[~near].max()
+    assert dev[near].max(initial=0.0) <= 1e-8, dev[near].max()
     s = w.series()
-    np.testing.assert_allclose(g["energy"]["E"], s["E"], rtol=1e-11, atol=0)
+    bound = energy_error_budget(w, k_near)
+    assert np.all(np.abs(g["energy"]["E"] - s["E"]) <= bound), \
+        np.max(np.abs(g["energy"]["E"] - s["E"]) / bound)
     np.testing.assert_array_equal(g["sums"][:, 5], s["n_alive"])
     np.testing.assert_array_equal(g["counters"][:2], w.counters[:2])
 
@@ -190,18 +203,20 @@ def test_mixed_orbital_pairs_track_fp64_oracle(gfk_lib, name):
     """The mixed path's orbital-pair kernels against the oracle: the 2^3S trial (all
     orbitals without r and z prefactor terms: the specialised evaluation) and trial
     function 3 ((r0 - r) prefactor: the generic one), 2059 walkers x 100 moves.  Kill
-    decisions agree except for walkers whose FP32 and FP64 paths straddle the node
-    within rounding (at most 0.5 %), positions stay at FP32 distance, and E(t) within
+    decisions agree for every walker whose oracle trajectory stays at least
+    NODE_DISTANCE_FP32 bohr from the node (closer ones may straddle it within FP32
+    rounding of their positions), positions stay at FP32 distance, and E(t) within
     2e-4."""
     gfk = gfk_lib
     kind, p, et = {"triplet_2s3": (1, wl.triplet_2s3(), -2.1752),
                    "fn3": (1, wl.fn3(), -2.124)}[name]
     n, steps = 2048 + 11, 100
     g = _gpu_run(gfk, kind, p, n, steps, 0.01, et, 3, gfk.GFK_PREC_MIXED, launch=(128, 2))
-    w = _oracle_run(kind, p, n, steps, 0.01, et, 3)
-    same = g["alive"].astype(bool) == w.alive.astype(bool)
-    assert (~same).sum() <= n // 200, (~same).sum()
-    both = same & w.alive.astype(bool)
+    w, d_min, _ = walk_tracking_node(kind, p, n_walkers=n, steps=steps, dt=0.01, e_trial=et,
+                                     seed=3)
+    far = d_min >= NODE_DISTANCE_FP32
+    np.testing.assert_array_equal(g["alive"].astype(bool)[far], w.alive.astype(bool)[far])
+    both = far & w.alive.astype(bool) & g["alive"].astype(bool)
     dx = np.abs(g["x"] - w.x).max(axis=1)[both]
     assert np.median(dx) < 1e-5 and np.quantile(dx, 0.99) < 1e-3, (np.median(dx), dx.max())
     assert np.max(np.abs(g["energy"]["E"] - w.series()["E"])) < 2e-4
