@@ -629,17 +629,18 @@ def run_ours(args):
 
 
 def profile_case(args):
-    """A small case for ncu captures: the ground-state trial, two launches of
+    """A small case for ncu captures: the workloads' trial function of state
+    --profile-state (default 0, the ground state), two launches of
     --profile-moves moves each (default 64) on --profile-walkers walkers (default
     2^22 mixed, 2^20 FP64; the state is larger than L2 either way), mixed path (or
     FP64 with --prec 0), Gaussian or Bernoulli noise (--noise)."""
     import torch
-    from paper_1703_08977_gb300 import gfk
-    kind, params = 0, [2.0, 0.5, 0.5]
+    from paper_1703_08977_gb300 import gfk, workloads as wl
+    kind, params = wl.trial_for_state(args.profile_state)
     n = args.profile_walkers or (1 << 22 if args.prec == 1 else 1 << 20)
     dt = 1.0 / 900.0 if args.noise == 1 else 0.005
-    d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=-2.9037, seed=SEED, prec=args.prec,
-                         noise=args.noise)
+    d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=wl.E_T[args.profile_state], seed=SEED,
+                         prec=args.prec, noise=args.noise, state=args.profile_state)
     launch = (args.threads or 128, args.wpt or 2) if args.prec == 1 else (128, 1)
     m = args.profile_moves
     with gfk.Context([d], trials=[(kind, params)], launch=launch) as ctx:
@@ -648,7 +649,8 @@ def profile_case(args):
         torch.cuda.synchronize()
         e = ctx.energy(0)["E"]
     print(json.dumps({"profile_case": True, "walkers": n, "moves": 2 * m, "prec": args.prec,
-                      "noise": args.noise, "launch": launch, "E_final": float(e[-1])}))
+                      "noise": args.noise, "state": args.profile_state, "launch": launch,
+                      "E_final": float(e[-1])}))
 
 
 def main():
@@ -671,6 +673,8 @@ def main():
     ap.add_argument("--noise", type=int, default=0, help="profile case: 0 Gaussian, 1 Bernoulli")
     ap.add_argument("--profile-walkers", type=int, default=0)
     ap.add_argument("--profile-moves", type=int, default=64)
+    ap.add_argument("--profile-state", type=int, default=0, choices=(0, 1, 2),
+                    help="profile case: trial function of state 0 (1^1S), 1 (2^3S), 2 (P_z)")
     ap.add_argument("--adam", action="store_true", help="adjoint workload: run 50 Adam steps")
     args = ap.parse_args()
     if args.profile_case:

@@ -129,14 +129,21 @@ typedef struct {
 gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_stream,
                       gfk_ctx** out);
 
-/* Set instance inst's trial function (host params, copied).  Allowed before
- * the first gfk_propagate, or after gfk_reset.  GFK_ESTATE otherwise;
- * GFK_EINVAL for a malformed parameter vector. */
+/* Set instance inst's trial function (host params, copied): the importance
+ * function phi_0 of the GFK split H = H0 + V_P ("Path Integral Theory"
+ * section, before Eq. 4), whose drift grad(phi)/phi steers the walk and whose
+ * local energy gives the weight of Eq. 4; the paper's trial-function list
+ * (functions 3 to 7) and its variational tuning remark (parameters chosen to
+ * minimise the variance of the local energy) are what the parameter vectors
+ * of gfk_trial_kind cover.  Allowed before the first gfk_propagate, or after
+ * gfk_reset.  GFK_ESTATE otherwise; GFK_EINVAL for a malformed parameter
+ * vector. */
 gfk_status gfk_set_trial(gfk_ctx* ctx, int32_t inst, int32_t trial_kind,
                          const double* params, int32_t n_params);
 
 /* Choose the launch shape of the walk kernels: threads per block
- * (64, 128, 256 or 512) and walkers per thread (1, 2 or 4).  Results per
+ * (64, 128, 256 or 512) and walkers per thread (1, 2 or 4; 4 only with at
+ * most 128 threads per block, GFK_EINVAL otherwise).  Results per
  * walker do not depend on it; population sums differ only by rounding order
  * (FP64 path) or by the FP32 rounding of the block shift (mixed path).
  * Allowed at any time between calls. */
@@ -154,7 +161,8 @@ gfk_status gfk_set_launch(gfk_ctx* ctx, int32_t threads_per_block, int32_t walke
 gfk_status gfk_set_graph(gfk_ctx* ctx, int32_t enable);
 
 /* Choose the launch shape by measurement: for every threads-per-block in
- * {64, 128, 256, 512} and walkers-per-thread in {1, 2, 4} (FP64: 1), time the
+ * {64, 128, 256, 512} and walkers-per-thread in {1, 2, 4} (FP64: 1; 4 with
+ * at most 128 threads), time the
  * walk kernel and the merge of its block records on probe_steps moves
  * (1..4096) of this context's own population,
  * restoring the population and counters after each candidate, then keep the
@@ -202,7 +210,11 @@ gfk_status gfk_energy(gfk_ctx* ctx, int32_t inst, double* e_mixed, double* ln_z,
  * Synchronises the stream.  GFK_EOVERFLOW if cap < S + 1. */
 gfk_status gfk_sums(gfk_ctx* ctx, int32_t inst, double* host_rows, int64_t cap);
 
-/* Copy instance inst's walkers to host memory (any pointer may be NULL):
+/* Copy instance inst's walkers to host memory: the N_rep independent
+ * replications of the space average (the paths Y_m of the discretisation
+ * section whose weights are averaged after the invariance principle), each
+ * with its position and its Feynman-Kac log-weight -int (E_L - E_T) dt of
+ * Eq. 4 (any pointer may be NULL):
  * x6 (n_walkers * 6 doubles, walker-major), logw (n_walkers doubles, -inf for
  * dead walkers), alive (n_walkers bytes).  Mixed-precision positions are
  * widened exactly from FP32.  Synchronises the stream.  GFK_ESTATE before the
@@ -335,6 +347,20 @@ gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* lane_ops_per_
  * 2 the library logf.  Runs on the current device and on `cuda_stream`, which
  * it synchronises.  GFK_EINVAL for a bad method or a NULL output. */
 gfk_status gfk_normal_moments(int32_t method, void* cuda_stream, double* moments);
+
+/* The FP32 trial evaluation of the GFK_PREC_MIXED walk at caller-given
+ * positions (a diagnostic: the same device code the walk kernels run).
+ * host_x holds n walkers x 6 floats (walker-major).  lanes = 1 evaluates each
+ * walker alone, lanes = 2 two at a time in the packed form of the walk
+ * kernels with 2 or 4 walkers per thread (an odd last walker is paired with
+ * itself); both give the same results bit for bit.  Outputs (host, any may be
+ * NULL): host_b n x 6 drift components, host_el n local energies, host_sign n
+ * signs of psi (0 where psi is exactly zero).  Runs on the current device and
+ * on cuda_stream, which it synchronises; takes its device memory from the
+ * stream-ordered pool.  GFK_EINVAL for a bad argument or parameter vector. */
+gfk_status gfk_eval_f32(int32_t trial_kind, const double* params, int32_t n_params,
+                        int32_t ee_on, int64_t n, const float* host_x, int32_t lanes,
+                        float* host_b, float* host_el, int32_t* host_sign, void* cuda_stream);
 
 /* Forget the population: the next gfk_propagate re-initialises it (step 0). */
 gfk_status gfk_reset(gfk_ctx* ctx);

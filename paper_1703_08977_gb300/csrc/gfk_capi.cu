@@ -3,6 +3,7 @@
 // All arithmetic of the walk runs in the kernels of gfk_fp64.cu, gfk_mixed.cu
 // and gfk_reduce.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstddef>
@@ -102,6 +103,16 @@ struct gfk_ctx {
 };
 
 namespace {
+
+// An NVTX range around one C-ABI call (header-only NVTX: a no-op unless a
+// profiler that records NVTX ranges is attached), so that timelines show
+// create / propagate / energy / grad around the kernels they launch.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int g_fault_alloc_countdown = -1;   // GFK_FAULT_ALLOC=n: the n-th allocation fails
 
@@ -643,6 +654,7 @@ const char* gfk_last_error(gfk_ctx* ctx) { return ctx ? ctx->last_error.c_str() 
 
 gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_stream,
                       gfk_ctx** out) {
+    NvtxRange nvtx_("gfk_create");
     if (!out) return GFK_EINVAL;
     *out = nullptr;
     if (!inst || n_inst < 1 || n_inst > GFK_MAX_INSTANCES) return GFK_EINVAL;
@@ -741,12 +753,14 @@ gfk_status gfk_set_launch(gfk_ctx* ctx, int32_t threads_per_block, int32_t walke
     if (walkers_per_thread != 1 && walkers_per_thread != 2 && walkers_per_thread != 4)
         return GFK_EINVAL;
     if (ctx->prec == GFK_PREC_FP64 && walkers_per_thread != 1) return GFK_EINVAL;
+    if (walkers_per_thread == 4 && threads_per_block > kMaxThreadsWpt4) return GFK_EINVAL;
     ctx->threads = threads_per_block;
     ctx->wpt = walkers_per_thread;
     return GFK_OK;
 }
 
 gfk_status gfk_propagate(gfk_ctx* ctx, int64_t n_steps) {
+    NvtxRange nvtx_("gfk_propagate");
     if (!ctx || n_steps < 0) return GFK_EINVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
@@ -848,6 +862,7 @@ gfk_status gfk_set_graph(gfk_ctx* ctx, int32_t enable) {
 
 gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads,
                         int32_t* best_wpt, double* best_rate) {
+    NvtxRange nvtx_("gfk_autotune");
     if (!ctx || probe_steps < 1 || probe_steps > 4096) return GFK_EINVAL;
     DeviceGuard g(ctx->device);
     if (!ctx->initialized) {
@@ -898,6 +913,7 @@ gfk_status gfk_autotune(gfk_ctx* ctx, int64_t probe_steps, int32_t* best_threads
     const int kind = launch_kind(ctx);
     for (int ti = 0; ti < 4 && e == cudaSuccess && st == GFK_OK; ++ti) {
         for (int wi = 0; wi < n_wp && e == cudaSuccess && st == GFK_OK; ++wi) {
+            if (wp[wi] == 4 && thr[ti] > kMaxThreadsWpt4) continue;   // not a compiled shape
             const int save_t = ctx->threads, save_w = ctx->wpt;
             ctx->threads = thr[ti];
             ctx->wpt = wp[wi];
@@ -977,6 +993,7 @@ gfk_status gfk_sums(gfk_ctx* ctx, int32_t inst, double* host_rows, int64_t cap) 
 
 gfk_status gfk_energy(gfk_ctx* ctx, int32_t inst, double* e_mixed, double* ln_z, double* ess,
                       int64_t cap, double* e_final) {
+    NvtxRange nvtx_("gfk_energy");
     gfk_status st = check_inst(ctx, inst);
     if (st != GFK_OK) return st;
     if (!ctx->initialized) return GFK_ESTATE;
@@ -1006,6 +1023,7 @@ gfk_status gfk_energy(gfk_ctx* ctx, int32_t inst, double* e_mixed, double* ln_z,
 }
 
 gfk_status gfk_get_walkers(gfk_ctx* ctx, int32_t inst, double* x6, double* logw, uint8_t* alive) {
+    NvtxRange nvtx_("gfk_get_walkers");
     gfk_status st = check_inst(ctx, inst);
     if (st != GFK_OK) return st;
     if (!ctx->initialized) return GFK_ESTATE;
@@ -1152,6 +1170,7 @@ gfk_status gfk_restore(gfk_ctx* ctx, const void* host_blob, int64_t bytes) {
 
 gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_steps,
                     int32_t ckpt_every, double* grad, int32_t n_params, double* loss) {
+    NvtxRange nvtx_("gfk_grad");
     gfk_status st = check_inst(ctx, inst);
     if (st != GFK_OK) return st;
     if (loss_kind != 0 && loss_kind != 1) return GFK_EINVAL;

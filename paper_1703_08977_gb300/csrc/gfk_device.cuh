@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "gfk_lanes.cuh"
 #include "gfk_types.h"
 
 namespace gfk {
@@ -232,14 +233,26 @@ __device__ __forceinline__ void pair_move_words_all(const PhiloxPre (&pre)[WPT],
 // the hardware square root and of the hardware cosine and sine, measured
 // exhaustively over all radius words and angles, and matches the variance to
 // the drift's FP32 time step.
-__device__ __forceinline__ float radius2_f32(uint32_t w, float r2_fix) {
+// The lane forms (one walker, or two in float2 lanes: the same rounded
+// operations, paired where they are plain arithmetic) and the one-walker
+// functions built on them.
+template <typename L>
+__device__ __forceinline__ L radius2_lanes(L wf, float r2_fix) {   // wf = (float)w per lane
     constexpr float kInv32 = 1.0f / 4294967296.0f;                        // 2^-32
     constexpr float kHalfInv32 = 0.5f / 4294967296.0f;                    // 2^-33
     constexpr float kMinus2Ln2 = -1.3862943611198906f;
-    const float ua = fmaf((float)w, kInv32, kHalfInv32);
-    float l2;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(ua));
-    return fmaxf(fmaf(kMinus2Ln2, l2, r2_fix), 0.0f);                    // -2 ln u >= 0
+    const L ua = lfma(wf, splat<L>(kInv32), splat<L>(kHalfInv32));
+    L l2;
+#pragma unroll
+    for (int k = 0; k < LaneCount<L>::value; ++k) {
+        float v;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(v) : "f"(lane_at(ua, k)));
+        set_lane(l2, k, v);
+    }
+    return lmax(lfma(splat<L>(kMinus2Ln2), l2, splat<L>(r2_fix)), splat<L>(0.0f));  // -2 ln u >= 0
+}
+__device__ __forceinline__ float radius2_f32(uint32_t w, float r2_fix) {
+    return radius2_lanes<float>((float)w, r2_fix);
 }
 
 // The Box-Muller radius from its square (hardware square root; 0 gives 0).
@@ -249,23 +262,52 @@ __device__ __forceinline__ float radius_f32(float r2) {
     return rho;
 }
 
-// Cosine and sine of the angle 2 pi (u_b - 1/2) from its word (23-bit grid).
-__device__ __forceinline__ void angle_f32(uint32_t w, float& s, float& c) {
+// The angle 2 pi (u_b - 1/2) from its word's 23-bit grid value 1 + k 2^-23
+// (the bit pattern 0x3F800000 | (w >> 9)); then the hardware sine and cosine.
+__device__ __forceinline__ float angle_grid(uint32_t w) {
+    return __int_as_float(0x3F800000 | (w >> 9));
+}
+template <typename L>
+__device__ __forceinline__ L angle_lanes(L grid) {
     constexpr float kHalfUlp = 1.0f / 16777216.0f;                        // 2^-24
     constexpr float kTwoPi = 6.2831853071795865f;
-    const float ubc = (__int_as_float(0x3F800000 | (w >> 9)) - 1.5f) + kHalfUlp;
-    __sincosf(kTwoPi * ubc, &s, &c);
+    return lmul(splat<L>(kTwoPi), ladd(lsub(grid, splat<L>(1.5f)), splat<L>(kHalfUlp)));
+}
+__device__ __forceinline__ void angle_f32(uint32_t w, float& s, float& c) {
+    __sincosf(angle_lanes<float>(angle_grid(w)), &s, &c);
 }
 
-__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6], float r2_fix) {
+// Six N(0,1) variates per walker from its six words (Box-Muller on (w0,w1),
+// (w2,w3), (w4,w5)) for the walkers of a lane group (w[k]: lane k's words).
+template <typename L>
+__device__ __forceinline__ void normals6_lanes(const uint32_t (*w)[6], L xi[6], float r2_fix) {
+    constexpr int W = LaneCount<L>::value;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float rho = radius_f32(radius2_f32(w[2 * j], r2_fix));
-        float s, c;
-        angle_f32(w[2 * j + 1], s, c);
-        xi[2 * j] = -rho * c;
-        xi[2 * j + 1] = -rho * s;
+        L wf, grid;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            set_lane(wf, k, (float)w[k][2 * j]);
+            set_lane(grid, k, angle_grid(w[k][2 * j + 1]));
+        }
+        const L r2 = radius2_lanes<L>(wf, r2_fix);
+        const L ang = angle_lanes<L>(grid);
+        L rho, sn, cs;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            float sv, cv;
+            __sincosf(lane_at(ang, k), &sv, &cv);
+            set_lane(rho, k, radius_f32(lane_at(r2, k)));
+            set_lane(sn, k, sv);
+            set_lane(cs, k, cv);
+        }
+        const L nrho = lneg(rho);
+        xi[2 * j] = lmul(nrho, cs);
+        xi[2 * j + 1] = lmul(nrho, sn);
     }
+}
+__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6], float r2_fix) {
+    normals6_lanes<float>(reinterpret_cast<const uint32_t(*)[6]>(w), xi, r2_fix);
 }
 
 // ---------------------------------------------------------------------------
@@ -346,12 +388,20 @@ __device__ __forceinline__ void bernoulli6_steps(uint32_t& s, float sdt, float s
 //   straight to X would round it to the grid of X's binade each time, a
 //   binade-dependent step length (a systematic diffusion error of up to
 //   ulp(X)/sdt).  The sub-ulp part sdt_lo rides on the drift's multiply-add.
+template <typename L>
+__device__ __forceinline__ L move_gauss_lanes(L x, L b, L xi, L dt, L sdt) {
+    return ladd(x, lfma(sdt, xi, lmul(b, dt)));
+}
+template <typename L>
+__device__ __forceinline__ L move_bern_lanes(L x, L b, L step, L step_lo, L dt) {
+    return ladd(x, ladd(lfma(b, dt, step_lo), step));
+}
 __device__ __forceinline__ float move_gauss_f32(float x, float b, float xi, float dt, float sdt) {
-    return x + fmaf(sdt, xi, b * dt);
+    return move_gauss_lanes<float>(x, b, xi, dt, sdt);
 }
 __device__ __forceinline__ float move_bern_f32(float x, float b, float step, float step_lo,
                                                float dt) {
-    return x + (fmaf(b, dt, step_lo) + step);
+    return move_bern_lanes<float>(x, b, step, step_lo, dt);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,6 +436,7 @@ template <typename R>
 struct TrialDev {
     int kind, nterms;
     int poly;                      // any c_k != 0 (else the Jastrow polynomial is skipped)
+    int plain;                     // kind 1 whose orbitals all lack r and z prefactor terms
     R Z, Zm2, Z2;                  // kind 0: Z, Z - 2, Z^2
     R a, beta, ee, eem2a, eebeta;  // Jastrow: a, beta, ee (0/1), ee - 2a, ee*beta
     R c2, c3, c4, c5;              // 2c1, 3c2, 4c3, 5c4 (du/drho coefficients)
@@ -394,6 +445,10 @@ struct TrialDev {
     R al[GFK_MAX_TERMS][2], c0[GFK_MAX_TERMS][2], c1[GFK_MAX_TERMS][2], cz[GFK_MAX_TERMS][2];
     R km2[GFK_MAX_TERMS][2];       // alpha - 2
     R hal2[GFK_MAX_TERMS][2];      // alpha^2 / 2
+    // FP32 lane evaluation (gfk_lanes.cuh): parameter products formed here
+    R mZ, m2beta;                  // -Z, -2 beta
+    R mal[GFK_MAX_TERMS][2];       // -alpha
+    R sc[GFK_MAX_TERMS];           // s c0A c0B (orbitals without prefactor terms)
 };
 
 template <typename R>
@@ -401,6 +456,10 @@ __host__ __device__ __forceinline__ void load_trial(const TrialHost& h, int ee_o
     t.kind = h.kind;
     t.nterms = h.nterms;
     t.poly = (h.ck[0] != 0.0 || h.ck[1] != 0.0 || h.ck[2] != 0.0 || h.ck[3] != 0.0) ? 1 : 0;
+    t.plain = h.kind == GFK_TRIAL_ORBITAL_PAIRS ? 1 : 0;
+    for (int i = 0; i < h.nterms && i < GFK_MAX_TERMS; ++i)
+        for (int e = 0; e < 2; ++e)
+            if (h.c1[i][e] != 0.0 || h.cz[i][e] != 0.0) t.plain = 0;
     t.Z = (R)h.Z;
     t.Zm2 = (R)(h.Z - 2.0);
     t.Z2 = (R)(h.Z * h.Z);
@@ -426,8 +485,12 @@ __host__ __device__ __forceinline__ void load_trial(const TrialHost& h, int ee_o
             t.cz[i][e] = (R)h.cz[i][e];
             t.km2[i][e] = (R)(h.alpha[i][e] - 2.0);
             t.hal2[i][e] = (R)(0.5 * h.alpha[i][e] * h.alpha[i][e]);
+            t.mal[i][e] = (R)(-h.alpha[i][e]);
         }
+        t.sc[i] = (R)(h.s[i] * h.c0[i][0] * h.c0[i][1]);
     }
+    t.mZ = (R)(-h.Z);
+    t.m2beta = (R)(-2.0 * h.beta);
 }
 
 // Result of one trial evaluation.
@@ -481,6 +544,26 @@ __device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
     return o;
 }
 
+}  // namespace gfk
+
+#include "gfk_eval_f32.cuh"   // the FP32 evaluation (one walker, or two in float2 lanes)
+
+namespace gfk {
+
+// The FP32 evaluation in EvalOut<float> form (one walker: the lane code with
+// L = float, so that it equals either lane of the paired evaluation bit for bit).
+template <int KIND, bool UNROLL, int POLY>
+__device__ __forceinline__ void eval_f32(const TrialDev<float>& t, const float x[6],
+                                         EvalOut<float>& o) {
+    EvalLanes<float> e;
+    eval_lanes<KIND, float, UNROLL, POLY>(t, x, e);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) o.b[d] = e.b[d];
+    o.el = e.el;
+    o.sign = e.sign[0];
+    o.rmin = e.rmin;
+}
+
 // Kind 0: psi = exp(-Z r1 - Z r2 + u(r12)).
 //   b_1 = -Z r1_hat + u' e12,  b_2 = -Z r2_hat - u' e12   (e12 = (r1 - r2)/r12)
 //   E_L = (Z - 2)(1/r1 + 1/r2) - Z^2 + (ee - 2u')/r12 - u'' - u'^2
@@ -488,7 +571,10 @@ __device__ __forceinline__ JastrowOut<R> jastrow(const TD& t, R r12, R i12) {
 // (the nuclear 1/r terms cancel exactly for Z = 2).
 template <typename R, typename TD, int POLY = -1>
 __device__ __forceinline__ void eval_kind0(const TD& t, const R x[6], EvalOut<R>& o) {
-    if constexpr (POLY < 0) {
+    if constexpr (sizeof(R) == 4) {           // FP32: the lane evaluation
+        eval_f32<0, false, POLY>(t, x, o);
+        return;
+    } else if constexpr (POLY < 0) {
         if (has_poly(t)) eval_kind0<R, TD, 1>(t, x, o);
         else eval_kind0<R, TD, 0>(t, x, o);
         return;
@@ -593,7 +679,10 @@ __device__ __forceinline__ void kind1_term(const TrialDev<R>& t, int k, R r1, R 
 // kernel's parameter bank); otherwise they run to t.nterms (fewer registers).
 template <typename R, bool UNROLL = false, bool PLAIN = false, int POLY = -1>
 __device__ __forceinline__ void eval_kind1(const TrialDev<R>& t, const R x[6], EvalOut<R>& o) {
-    if constexpr (POLY < 0) {
+    if constexpr (sizeof(R) == 4) {           // FP32: the lane evaluation
+        eval_f32<PLAIN ? 3 : 1, UNROLL, POLY>(t, x, o);
+        return;
+    } else if constexpr (POLY < 0) {
         if (has_poly(t)) eval_kind1<R, UNROLL, PLAIN, 1>(t, x, o);
         else eval_kind1<R, UNROLL, PLAIN, 0>(t, x, o);
         return;

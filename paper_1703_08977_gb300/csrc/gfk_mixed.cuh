@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "gfk_block.cuh"
 #include "gfk_device.cuh"
@@ -132,15 +133,26 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 // PARAM: every instance the launch covers has the same trial function, which
 // arrives as the kernel argument tk (constant-bank operands, no shared-memory
 // loads, no registers); otherwise each block loads its instance's trial into
-// shared memory (kind 0 then copies its 16 parameters into registers).  The
-// launcher uses PARAM for the orbital-pair kinds only: it speeds them up by
-// ~11 % and slows the kind-0 walk by ~2 % against the register copy.
+// shared memory (kind 0 then copies its parameters into registers).  The
+// launcher uses PARAM for the orbital-pair kinds only.
+//
+// Lanes: the thread's walkers are evaluated in groups of two, the two lanes of
+// a float2 (gfk_lanes.cuh: packed FP32 instructions, one issue slot for both
+// walkers); with one walker per thread the same code runs on plain floats.
+// Walker k of the thread is lane k % 2 of group k / 2.  Every walker moves on
+// every step whether it is alive or not (no per-lane selects on the
+// positions); a walker killed by a move has its position, a log-weight of
+// -inf and a zero sign stored at that move, and only walkers alive at the end
+// store their state then.
 template <int KIND, int WPT, int NOISE, bool PARAM, bool CKPT = false>
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(WPT == 4 ? kMaxThreadsWpt4 : kMaxThreads)
 walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                   uint32_t step0, int nsteps, PartialRec* __restrict__ part, int nblk,
                   unsigned long long* __restrict__ counters, int blk0,
                   const __grid_constant__ TrialDev<float> tk) {
+    using L = typename std::conditional<WPT == 1, float, float2>::type;
+    constexpr int LW = LaneCount<L>::value;       // walkers per lane group
+    constexpr int NG = WPT / LW;                   // lane groups per thread
     __shared__ TrialDev<float> s_trial;
     // the per-warp log-weight shift each ring buffer's window used
     __shared__ double s_shift[2][kMaxWarps];
@@ -164,15 +176,18 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     // FP32 time step, noise scale and radius constant chosen on the host so the
     // diffusion matches the drift, and the other derived constants, all formed
     // on the host (gfk_mixed_consts.h)
-    const float dt = I.dt_f32, sdt = I.sdt_f32, sdt_lo = I.sdt_lo, r2_fix = I.r2_fix;
+    const float r2_fix = I.r2_fix;
+    const L dtL = splat<L>(I.dt_f32), sdtL = splat<L>(I.sdt_f32);
+    const float sdt = I.sdt_f32, sdt_lo = I.sdt_lo;
     const float et = I.et_f32;
+    const L etL = splat<L>(et);
     const double dt64 = I.dt;
     const double et_fix = I.et_fix;          // per-move E_T rounding, restored at each fold
     constexpr float kLog2e = 1.4426950408889634f;
-    const float dt_log2e = I.dt_log2e;
+    const L dtl2eL = splat<L>(I.dt_log2e);
     const uint32_t k0 = I.k0, k1 = I.k1;
     const int T = blockDim.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = T >> 5;
     float* const s_ring = s_dyn;
     unsigned* const s_cnt = reinterpret_cast<unsigned*>(s_dyn + 2 * kRing * 4 * nwarps);
@@ -183,10 +198,10 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     uint32_t lcg[WPT];           // Bernoulli mode: generator state before this move
     int64_t slot[WPT];
     bool valid[WPT];
-    float x[WPT][6], b[WPT][6];
-    double L[WPT];
-    float dsh[WPT], S[WPT], comp[WPT];   // dsh: (L - c) log2(e), formed at each fold
+    double Lw[WPT];              // FP64 log-weight base
     int sg[WPT];
+    L x[NG][6], b[NG][6];
+    L S[NG], comp[NG], dsh[NG];  // dsh: (L - c) log2(e), formed at each fold
 #pragma unroll
     for (int k = 0; k < WPT; ++k) {
         const int64_t id = (int64_t)(blk - bm.begin[inst]) * T * WPT + (int64_t)k * T + threadIdx.x;
@@ -200,120 +215,157 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         carry[k][0] = carry[k][1] = 0u;
         slot[k] = I.off + id;
         sg[k] = 0;
-        L[k] = -INFINITY;
+        Lw[k] = -INFINITY;
+        float xk[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid[k]) load_mixed(st, slot[k], xk, Lw[k], sg[k]);
 #pragma unroll
-        for (int d = 0; d < 6; ++d) { x[k][d] = 0.f; b[k][d] = 0.f; }
-        if (valid[k]) load_mixed(st, slot[k], x[k], L[k], sg[k]);
-        if (sg[k] != 0) {
-            EvalOut<float> ev;
-            eval_trial<KIND, float, PARAM, kPoly>(t, x[k], ev);
+        for (int d = 0; d < 6; ++d) set_lane(x[k / LW][d], k % LW, xk[d]);
+    }
 #pragma unroll
-            for (int d = 0; d < 6; ++d) b[k][d] = ev.b[d];
-        }
-        S[k] = 0.f;
-        comp[k] = 0.f;
+    for (int g = 0; g < NG; ++g) {
+        // the drift at the start (unused by walkers that are dead)
+        EvalLanes<L> ev;
+        eval_lanes<KIND, L, PARAM, kPoly>(t, x[g], ev);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) b[g][d] = ev.b[d];
+        S[g] = splat<L>(0.f);
+        comp[g] = splat<L>(0.f);
     }
     unsigned n_nonfinite = 0, n_node = 0, n_coal = 0;
     // per-warp shift: the warp's largest log-weight (0 if the warp has none alive)
-    double lmax = -INFINITY;
+    double lmaxw = -INFINITY;
 #pragma unroll
     for (int k = 0; k < WPT; ++k)
-        if (sg[k] != 0) lmax = fmax(lmax, L[k]);
-    double c = warp_max(lmax);
+        if (sg[k] != 0) lmaxw = fmax(lmaxw, Lw[k]);
+    double c = warp_max(lmaxw);
     c = isfinite(c) ? floor(c) : 0.0;      // integer-valued shift
 #pragma unroll
-    for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) * kLog2e : 0.f;
+    for (int k = 0; k < WPT; ++k)
+        set_lane(dsh[k / LW], k % LW, sg[k] != 0 ? (float)(Lw[k] - c) * kLog2e : 0.f);
     int fold_len = 0;
     int buf = 0;
 
     for (int s = 0; s < nsteps; ++s) {
         const uint32_t step = step0 + (uint32_t)s;
-        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
         unsigned na = 0;
-        // Gaussian noise: the normals of all WPT walkers first (the Philox
-        // words under one even / odd branch), so the moves that follow are one
-        // branch-free stretch (+2.4 % against drawing each walker's words in
-        // its own iteration); the Bernoulli steps, branch-free already, are
-        // drawn per walker (0.6 % faster there).  Every walker slot runs the
-        // same instructions (dead or past the end included) so the compiler
-        // can interleave the WPT walkers; only the commit of the new state is
-        // predicated.
-        float xi[WPT][6], xlo[WPT][6];
+        // Gaussian noise: the normals of all walkers first (the Philox words
+        // under one even / odd branch), so the moves that follow are one
+        // branch-free stretch; the Bernoulli steps are drawn per group.
+        L xi[NG][6], xlo[NG][6];
         if (NOISE == 0) {
             uint32_t words[WPT][6];
             pair_move_words_all<WPT>(pre, carry, step, s == 0, k0, k1, words);
 #pragma unroll
-            for (int k = 0; k < WPT; ++k) normals6_f32(words[k], xi[k], r2_fix);
+            for (int g = 0; g < NG; ++g) normals6_lanes<L>(&words[g * LW], xi[g], r2_fix);
         }
+        L q[4];
 #pragma unroll
-        for (int k = 0; k < WPT; ++k) {
-            const bool alive = sg[k] != 0;
-            float xn[6];
-            if (NOISE == 1)
-                bernoulli6_steps(lcg[k], sdt, sdt_lo, xi[k], xlo[k]);   // +-sdt, +-sdt_lo
+        for (int g = 0; g < NG; ++g) {
+            if (NOISE == 1) {
+#pragma unroll
+                for (int j = 0; j < LW; ++j) {
+                    float st6[6], lo6[6];
+                    bernoulli6_steps(lcg[g * LW + j], sdt, sdt_lo, st6, lo6);   // +-sdt, +-sdt_lo
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) {
+                        set_lane(xi[g][d], j, st6[d]);
+                        set_lane(xlo[g][d], j, lo6[d]);
+                    }
+                }
+            }
+            L xn[6];
 #pragma unroll
             for (int d = 0; d < 6; ++d)
-                xn[d] = NOISE == 1 ? move_bern_f32(x[k][d], b[k][d], xi[k][d], xlo[k][d], dt)
-                                   : move_gauss_f32(x[k][d], b[k][d], xi[k][d], dt, sdt);
-            EvalOut<float> ev;
-            eval_trial<KIND, float, PARAM, kPoly>(t, xn, ev);
+                xn[d] = NOISE == 1 ? move_bern_lanes(x[g][d], b[g][d], xi[g][d], xlo[g][d], dtL)
+                                   : move_gauss_lanes(x[g][d], b[g][d], xi[g][d], dtL, sdtL);
+            EvalLanes<L> ev;
+            eval_lanes<KIND, L, PARAM, kPoly>(t, xn, ev);
             // a non-finite position is a non-finite kill, then a sign change a
-            // node kill, then a non-finite drift or local energy (the position
-            // test runs every move, without a branch: +0.4 to +1.3 % against
-            // testing it only after a sign change, bitwise the same)
-            const bool node = (ev.sign != sg[k]) &
-                              finite_(((xn[0] + xn[1]) + (xn[2] + xn[3])) + (xn[4] + xn[5]));
-            const bool fin = eval_finite(ev);
-            const bool stay = alive && !node && fin;
-            n_coal += (alive && ev.rmin < 1e-5f) ? 1u : 0u;
-            n_node += (alive && node) ? 1u : 0u;
-            n_nonfinite += (alive && !node && !fin) ? 1u : 0u;
+            // node kill, then a non-finite drift or local energy
+            const L xs = ladd(ladd(ladd(xn[0], xn[1]), ladd(xn[2], xn[3])), ladd(xn[4], xn[5]));
+            const L fs = eval_check_sum(ev);
+            L el = ev.el;
+            bool stay[LW];
+#pragma unroll
+            for (int j = 0; j < LW; ++j) {
+                const int k = g * LW + j;
+                const bool alive = sg[k] != 0;
+                const bool node = (ev.sign[j] != sg[k]) & finite_(lane_at(xs, j));
+                const bool fin = finite_(lane_at(fs, j));
+                stay[j] = alive && !node && fin;
+                n_coal += (alive && lane_at(ev.rmin, j) < 1e-5f) ? 1u : 0u;
+                n_node += (alive && node) ? 1u : 0u;
+                n_nonfinite += (alive && !node && !fin) ? 1u : 0u;
+                if (alive && !stay[j] && valid[k]) {
+                    // killed by this move: it stays here (rare; stored now)
+                    float xk[6];
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) xk[d] = lane_at(xn[d], j);
+                    store_mixed(st, slot[k], xk, -INFINITY, 0);
+                }
+                sg[k] = stay[j] ? sg[k] : 0;
+                if (!stay[j]) set_lane(el, j, et);
+                na += stay[j] ? 1u : 0u;
+            }
 #pragma unroll
             for (int d = 0; d < 6; ++d) {
-                x[k][d] = alive ? xn[d] : x[k][d];      // a walker killed now stays here
-                b[k][d] = ev.b[d];                      // read only while the walker lives
+                x[g][d] = xn[d];
+                b[g][d] = ev.b[d];
             }
-            sg[k] = stay ? sg[k] : 0;
             // Kahan: S accumulates E_L - E_T since the last fold
-            const float el = stay ? ev.el : et;
-            const float y = (el - et) - comp[k];
-            const float tsum = S[k] + y;
-            comp[k] = (tsum - S[k]) - y;
-            S[k] = tsum;
-            const float w = stay ? ex2_approx(fmaf(-S[k], dt_log2e, dsh[k])) : 0.f;
-            const float we = w * el;
-            q0 += w;
-            q1 += we;
-            q2 += w * w;
-            q3 += we * el;
-            na += stay ? 1u : 0u;
+            const L y = lsub(lsub(el, etL), comp[g]);
+            const L tsum = ladd(S[g], y);
+            comp[g] = lsub(lsub(tsum, S[g]), y);
+            S[g] = tsum;
+            L w = lex2(lfma(lneg(S[g]), dtl2eL, dsh[g]));
+#pragma unroll
+            for (int j = 0; j < LW; ++j)
+                if (!stay[j]) set_lane(w, j, 0.f);
+            const L we = lmul(w, el);
+            const L ww = lmul(w, w);
+            const L wee = lmul(we, el);
+            if (g == 0) {
+                q[0] = w; q[1] = we; q[2] = ww; q[3] = wee;
+            } else {
+                q[0] = ladd(q[0], w); q[1] = ladd(q[1], we);
+                q[2] = ladd(q[2], ww); q[3] = ladd(q[3], wee);
+            }
+        }
+        // the thread's four sums (over its walkers: the lanes added last)
+        float qs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float v = lane_at(q[u], 0);
+#pragma unroll
+            for (int j = 1; j < LW; ++j) v = v + lane_at(q[u], j);
+            qs[u] = v;
         }
         // the lane's four sums go to the warp's staging rows (column = move of
         // the group x 4 + quantity); every fourth move, and at the end of a
         // window, the warp adds the columns up (half a column per lane, the
         // halves joined by one shuffle) and writes them to the ring
         const int m4 = s & 3;
-        s_stage[(m4 * 4 + 0) * kStageStride + lane] = q0;
-        s_stage[(m4 * 4 + 1) * kStageStride + lane] = q1;
-        s_stage[(m4 * 4 + 2) * kStageStride + lane] = q2;
-        s_stage[(m4 * 4 + 3) * kStageStride + lane] = q3;
+        s_stage[(m4 * 4 + 0) * kStageStride + lane_id] = qs[0];
+        s_stage[(m4 * 4 + 1) * kStageStride + lane_id] = qs[1];
+        s_stage[(m4 * 4 + 2) * kStageStride + lane_id] = qs[2];
+        s_stage[(m4 * 4 + 3) * kStageStride + lane_id] = qs[3];
         na = __reduce_add_sync(0xffffffffu, na);
         const int r = s % kRing;
-        if (lane == 0) s_cnt[(buf * kRing + r) * nwarps + warp] = na;
+        if (lane_id == 0) s_cnt[(buf * kRing + r) * nwarps + warp] = na;
         if (m4 == 3 || r == kRing - 1 || s == nsteps - 1) {
             __syncwarp();
-            const int col = lane & 15, half = lane >> 4;
+            const int col = lane_id & 15, half = lane_id >> 4;
             const bool staged = (col >> 2) <= m4;
             float v = 0.f;
             if (staged) {
                 const float* src = s_stage + col * kStageStride + 16 * half;
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-                for (int t = 0; t < 16; t += 4) {
-                    a0 += src[t];
-                    a1 += src[t + 1];
-                    a2 += src[t + 2];
-                    a3 += src[t + 3];
+                for (int u = 0; u < 16; u += 4) {
+                    a0 += src[u];
+                    a1 += src[u + 1];
+                    a2 += src[u + 2];
+                    a3 += src[u + 3];
                 }
                 v = (a0 + a1) + (a2 + a3);
             }
@@ -324,38 +376,47 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         }
         ++fold_len;
         if (r == kRing - 1 || s == nsteps - 1) {
-            if (lane == 0) s_shift[buf][warp] = c;
+            if (lane_id == 0) s_shift[buf][warp] = c;
             // fold the FP32 increments into the FP64 base; new per-warp shift
-            lmax = -INFINITY;
+            lmaxw = -INFINITY;
 #pragma unroll
             for (int k = 0; k < WPT; ++k) {
+                const float Sk = lane_at(S[k / LW], k % LW), ck = lane_at(comp[k / LW], k % LW);
                 if (sg[k] != 0) {
-                    L[k] = L[k] - (((double)S[k] - (double)comp[k]) + (double)fold_len * et_fix) * dt64;
-                    lmax = fmax(lmax, L[k]);
+                    Lw[k] = Lw[k] - (((double)Sk - (double)ck) + (double)fold_len * et_fix) * dt64;
+                    lmaxw = fmax(lmaxw, Lw[k]);
                 } else {
-                    L[k] = -INFINITY;
+                    Lw[k] = -INFINITY;
                 }
-                S[k] = 0.f;
-                comp[k] = 0.f;
+            }
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                S[g] = splat<L>(0.f);
+                comp[g] = splat<L>(0.f);
             }
             fold_len = 0;
-            c = warp_max(lmax);
+            c = warp_max(lmaxw);
             c = isfinite(c) ? floor(c) : 0.0;
 #pragma unroll
-            for (int k = 0; k < WPT; ++k) dsh[k] = sg[k] != 0 ? (float)(L[k] - c) * kLog2e : 0.f;
+            for (int k = 0; k < WPT; ++k)
+                set_lane(dsh[k / LW], k % LW, sg[k] != 0 ? (float)(Lw[k] - c) * kLog2e : 0.f);
             // position checkpoint (StateMixed::ckpt) after move step; compiled
-            // into the gradient's forward kernels only (CKPT), since the extra
-            // code at the fold slowed the other walks by up to 1.7 %
+            // into the gradient's forward kernels only (CKPT).  Walkers that are
+            // dead by then keep moving and write meaningless positions, which the
+            // adjoint never reads (their final weight is zero).
             if (CKPT) {
                 const uint32_t done = step + 1u;
-                const uint32_t j = done / (uint32_t)st.ckpt_every;
-                if (done % (uint32_t)st.ckpt_every == 0u && j >= 1u && j < (uint32_t)st.ckpt_count) {
-                    float4* base = st.ckpt + (int64_t)j * 2 * st.ckpt_slots;
+                const uint32_t jc = done / (uint32_t)st.ckpt_every;
+                if (done % (uint32_t)st.ckpt_every == 0u && jc >= 1u && jc < (uint32_t)st.ckpt_count) {
+                    float4* base = st.ckpt + (int64_t)jc * 2 * st.ckpt_slots;
 #pragma unroll
                     for (int k = 0; k < WPT; ++k) {
                         if (!valid[k]) continue;
-                        base[slot[k]] = make_float4(x[k][0], x[k][1], x[k][2], x[k][3]);
-                        base[st.ckpt_slots + slot[k]] = make_float4(x[k][4], x[k][5], 0.f, 0.f);
+                        const int g = k / LW, j = k % LW;
+                        base[slot[k]] = make_float4(lane_at(x[g][0], j), lane_at(x[g][1], j),
+                                                    lane_at(x[g][2], j), lane_at(x[g][3], j));
+                        base[st.ckpt_slots + slot[k]] =
+                            make_float4(lane_at(x[g][4], j), lane_at(x[g][5], j), 0.f, 0.f);
                     }
                 }
             }
@@ -381,9 +442,9 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                         // the factor in FP32 (it multiplies FP32 warp sums)
                         const float f = ex2_approx((float)(s_shift[buf][w] - cb) * kLog2e);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float fk = k == 2 ? f * f : f;
-                            acc[k] += (double)(ring[k * nwarps + w] * fk);
+                        for (int u = 0; u < 4; ++u) {
+                            const float fk = u == 2 ? f * f : f;
+                            acc[u] += (double)(ring[u * nwarps + w] * fk);
                         }
                     }
                 } else {
@@ -398,9 +459,16 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             buf ^= 1;
         }
     }
+    // walkers alive now store their state (the ones killed during the launch
+    // were stored when they died; dead ones are unchanged in memory)
 #pragma unroll
-    for (int k = 0; k < WPT; ++k)
-        if (valid[k]) store_mixed(st, slot[k], x[k], sg[k] != 0 ? L[k] : -INFINITY, sg[k]);
+    for (int k = 0; k < WPT; ++k) {
+        if (!valid[k] || sg[k] == 0) continue;
+        float xk[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) xk[d] = lane_at(x[k / LW][d], k % LW);
+        store_mixed(st, slot[k], xk, Lw[k], sg[k]);
+    }
     flush_counters(counters, inst, n_nonfinite, n_node, n_coal);
 }
 

@@ -9,9 +9,11 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "gfk_device.cuh"
 #include "gfk_mixed_consts.h"
+#include "gfk_trial_parse.h"
 #include "gfk_types.h"
 
 namespace {
@@ -225,5 +227,89 @@ extern "C" gfk_status gfk_normal_moments(int32_t method, void* cuda_stream, doub
     moments[0] = h[0] / n_radius;
     moments[1] = h[1] / n_radius;
     for (int q = 2; q < kNumMoments; ++q) moments[q] = h[q] / n_angle;
+    return GFK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gfk_eval_f32: the mixed walk's FP32 trial evaluation at given positions, one
+// walker at a time (float lanes) or two at a time (float2 lanes), through the
+// per-block dispatch the walk kernels use (eval_lanes, KIND 2).
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int W>
+__global__ void eval_f32_kernel(gfk::TrialDev<float> t, int64_t n, const float* __restrict__ x,
+                                float* __restrict__ b, float* __restrict__ el,
+                                int* __restrict__ sign) {
+    using L = typename std::conditional<W == 1, float, float2>::type;
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * W;
+    if (i0 >= n) return;
+    L xl[6];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const int64_t i = i0 + j < n ? i0 + j : i0;    // an odd last walker pairs with itself
+#pragma unroll
+        for (int d = 0; d < 6; ++d) gfk::set_lane(xl[d], j, x[6 * i + d]);
+    }
+    gfk::EvalLanes<L> ev;
+    gfk::eval_lanes<2, L>(t, xl, ev);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const int64_t i = i0 + j;
+        if (i >= n) break;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) b[6 * i + d] = gfk::lane_at(ev.b[d], j);
+        el[i] = gfk::lane_at(ev.el, j);
+        sign[i] = ev.sign[j];
+    }
+}
+
+}  // namespace
+
+extern "C" gfk_status gfk_eval_f32(int32_t trial_kind, const double* params, int32_t n_params,
+                                   int32_t ee_on, int64_t n, const float* host_x, int32_t lanes,
+                                   float* host_b, float* host_el, int32_t* host_sign,
+                                   void* cuda_stream) {
+    if (!host_x || n < 1 || n > (1ll << 26) || (lanes != 1 && lanes != 2)) return GFK_EINVAL;
+    if (ee_on != 0 && ee_on != 1) return GFK_EINVAL;
+    gfk::TrialHost th;
+    if (!gfk::parse_trial_params(trial_kind, params, n_params, &th)) return GFK_EINVAL;
+    gfk::TrialDev<float> t;
+    gfk::load_trial<float>(th, ee_on, t);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const size_t nb = (size_t)n;
+    char* d = nullptr;
+    const size_t bytes = nb * (6 + 6 + 1) * sizeof(float) + nb * sizeof(int);
+    if (cudaMallocAsync((void**)&d, bytes, stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GFK_ENOMEM;
+    }
+    float* dx = (float*)d;
+    float* db = dx + 6 * nb;
+    float* del = db + 6 * nb;
+    int* dsg = (int*)(del + nb);
+    cudaError_t e = cudaMemcpyAsync(dx, host_x, nb * 6 * sizeof(float), cudaMemcpyHostToDevice,
+                                    stream);
+    const int th_per_block = 128;
+    const int64_t threads = (n + lanes - 1) / lanes;
+    const int blocks = (int)((threads + th_per_block - 1) / th_per_block);
+    if (e == cudaSuccess) {
+        if (lanes == 1) eval_f32_kernel<1><<<blocks, th_per_block, 0, stream>>>(t, n, dx, db, del, dsg);
+        else eval_f32_kernel<2><<<blocks, th_per_block, 0, stream>>>(t, n, dx, db, del, dsg);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && host_b)
+        e = cudaMemcpyAsync(host_b, db, nb * 6 * sizeof(float), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && host_el)
+        e = cudaMemcpyAsync(host_el, del, nb * sizeof(float), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && host_sign)
+        e = cudaMemcpyAsync(host_sign, dsg, nb * sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFreeAsync(d, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GFK_ECUDA;
+    }
     return GFK_OK;
 }

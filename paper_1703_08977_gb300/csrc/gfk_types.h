@@ -89,6 +89,10 @@ struct StateMixed {
 constexpr int kRing = 64;
 constexpr int kMaxThreads = 512;
 constexpr int kMaxWarps = kMaxThreads / 32;
+// The mixed walk with 4 walkers per thread (two packed pairs, two independent
+// dependency chains per thread) is compiled for blocks of at most 128 threads,
+// which lets it hold its state in up to 255 registers per thread.
+constexpr int kMaxThreadsWpt4 = 128;
 // Row stride (floats) of the mixed walk's per-warp staging rows: 32 lanes plus
 // one, so that reading a column across the warp hits 32 distinct banks.
 constexpr int kStageStride = 33;

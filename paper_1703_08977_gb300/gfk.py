@@ -33,7 +33,7 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
            "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc",
            "gfk_measure_peak", "gfk_set_graph", "gfk_autotune", "gfk_grad",
-           "gfk_normal_moments", "gfk_kernel_count")
+           "gfk_normal_moments", "gfk_kernel_count", "gfk_eval_f32")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
             "i2f", "f2f")
 GFK_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -102,6 +102,9 @@ def load(build_if_needed: bool = True):
             "gfk_measure_peak": ([c.c_int32, P, dp], c.c_int),
             "gfk_normal_moments": ([c.c_int32, P, dp], c.c_int),
             "gfk_kernel_count": ([P, c.POINTER(c.c_int64), c.c_int32], c.c_int),
+            "gfk_eval_f32": ([c.c_int32, dp, c.c_int32, c.c_int32, c.c_int64,
+                              c.POINTER(c.c_float), c.c_int32, c.POINTER(c.c_float),
+                              c.POINTER(c.c_float), c.POINTER(c.c_int32), P], c.c_int),
             "gfk_set_graph": ([P, c.c_int32], c.c_int),
             "gfk_grad": ([P, c.c_int32, c.c_int32, c.c_int64, c.c_int32, dp, c.c_int32, dp],
                          c.c_int),
@@ -346,6 +349,24 @@ def gfk_measure_peak(op, stream=None) -> float:
     v = ctypes.c_double()
     _check(load().gfk_measure_peak(int(op), stream, ctypes.byref(v)), "gfk_measure_peak")
     return v.value
+
+
+def gfk_eval_f32(kind, params, x, lanes=2, ee_on=1, stream=None):
+    """The mixed walk's FP32 trial evaluation at positions x (n, 6): (b (n, 6) float32,
+    E_L (n,) float32, sign (n,) int32)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xv = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 6)
+    n = xv.shape[0]
+    b = np.empty((n, 6), dtype=np.float32)
+    el = np.empty(n, dtype=np.float32)
+    sg = np.empty(n, dtype=np.int32)
+    if stream is None:
+        stream = _current_stream_ptr()
+    fp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    _check(load().gfk_eval_f32(int(kind), _dp(p), len(p), int(ee_on), n, fp(xv), int(lanes),
+                               fp(b), fp(el), sg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               stream), "gfk_eval_f32")
+    return b, el, sg
 
 
 RADIUS_METHODS = ("kernel", "hw_log2", "logf")

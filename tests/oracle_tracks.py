@@ -56,10 +56,11 @@ def energy_error_budget(w, k_near, rel_far=1e-13, rel_near=1e-8):
     that it is an ordinary walker).  Needs the history that
     walk_tracking_node(keep_series=True) keeps."""
     E = w.series()["E"]
+    rel_far = np.broadcast_to(np.asarray(rel_far, dtype=float), E.shape)
     out = np.zeros(len(w.history))
     for k, (logw, el, alive) in enumerate(w.history):
         a = alive.astype(bool)
-        out[k] = rel_far * abs(E[k]) if np.isfinite(E[k]) else 0.0
+        out[k] = rel_far[k] * abs(E[k]) if np.isfinite(E[k]) else 0.0
         sel = a & (k_near <= k)
         if not sel.any():
             continue

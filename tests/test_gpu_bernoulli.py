@@ -105,7 +105,7 @@ def test_bernoulli_launch_shape_resume_and_shards(gfk_lib, prec):
     kw = dict(dt=0.0025, e_trial=-2.1752, seed=6, prec=prec, noise=gfk.GFK_NOISE_BERNOULLI)
     d = gfk.InstanceDesc(n_walkers=1500, **kw)
     one = gfk.Context([d], trials=[(1, p)], launch=(128, 1 if prec == 0 else 2)).propagate(256)
-    other = gfk.Context([d], trials=[(1, p)], launch=(512, 1 if prec == 0 else 4)).propagate(256)
+    other = gfk.Context([d], trials=[(1, p)], launch=(512, 1) if prec == 0 else (64, 4)).propagate(256)
     two = gfk.Context([d], trials=[(1, p)]).propagate(64)
     blob = two.checkpoint()
     three = gfk.Context([d], trials=[(1, p)])
