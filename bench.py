@@ -318,7 +318,8 @@ def measure_peaks():
     the rooflines use: FP32 and FP64 fused multiply-add and the special-function unit's
     ex2, rsqrt, lg2 and sin (gfk_measure_peak, about 10 ms each)."""
     from paper_1703_08977_gb300 import gfk
-    return {op: gfk.gfk_measure_peak(op) for op in ("ffma", "dfma", "ex2", "rsq", "lg2", "sin")}
+    return {op: gfk.gfk_measure_peak(op)
+            for op in ("ffma", "ffma2", "dfma", "ex2", "rsq", "lg2", "sin")}
 
 
 def walk_rooflines(name, insts, avg_launch_ms, ws_per_launch, peaks, n_sm, sm_max, sm_mhz):
@@ -328,7 +329,9 @@ def walk_rooflines(name, insts, avg_launch_ms, ws_per_launch, peaks, n_sm, sm_ma
     counts = _op_counts(insts)
     rate = ws_per_launch / (avg_launch_ms / 1e3)          # walker-steps/s in the walk kernel
     achieved = counts["flops"] * rate / 1e12
-    peak = 2.0 * peaks["ffma"] / 1e12
+    # the FP32 multiply-add rate, scalar or packed, whichever is higher
+    fma_rate = max(peaks["ffma"], peaks.get("ffma2", 0.0))
+    peak = 2.0 * fma_rate / 1e12
     derived = n_sm * LANES_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
     prof = WALK_PROFILE.get(name)
     valid = bool(prof) and prof["src_sha"] == _src_sha()
@@ -336,7 +339,8 @@ def walk_rooflines(name, insts, avg_launch_ms, ws_per_launch, peaks, n_sm, sm_ma
             "frac": achieved / peak,
             "traffic": prof["bytes_per_walker_step"] * ws_per_launch if valid else None,
             "kernel": "walk_mixed_kernel",
-            "peak_basis": "of measured: FFMA lane rate (gfk_measure_peak, this run) x 2 flops",
+            "peak_basis": "of measured: the higher of the FFMA and packed FFMA2 lane rates "
+                          "(gfk_measure_peak, this run) x 2 flops",
             "peak_derived": derived, "frac_of_derived": achieved / derived,
             "derived_basis": f"{n_sm} SMs x {LANES_PER_SM_CLK} FP32 lanes x 2 flops x "
                              f"{sm_max:.0f} MHz",

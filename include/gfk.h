@@ -324,12 +324,13 @@ gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32_t trial_ki
  * PTX instruction on every SM; *lane_ops_per_s receives thread-level
  * operations per second (one fma = one op; GFK_PEAK_IMAD_WIDE counts one
  * mad.wide plus one xor per op; GFK_PEAK_F2F counts each of the two
- * conversions of a float -> double -> float round trip).  Takes about 10 ms;
+ * conversions of a float -> double -> float round trip; GFK_PEAK_FFMA2 counts
+ * the two fused multiply-adds of one packed fma.rn.f32x2).  Takes about 10 ms;
  * synchronises cuda_stream; allocates 4 bytes from the stream-ordered pool. */
 typedef enum {
     GFK_PEAK_FFMA = 0, GFK_PEAK_DFMA, GFK_PEAK_IMAD, GFK_PEAK_IMAD_HI, GFK_PEAK_IMAD_WIDE,
     GFK_PEAK_LOP3, GFK_PEAK_EX2, GFK_PEAK_RSQ, GFK_PEAK_LG2, GFK_PEAK_SIN, GFK_PEAK_I2F,
-    GFK_PEAK_F2F, GFK_PEAK_COUNT
+    GFK_PEAK_F2F, GFK_PEAK_FFMA2, GFK_PEAK_COUNT
 } gfk_peak_op;
 gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* lane_ops_per_s);
 

@@ -209,6 +209,25 @@ __device__ __forceinline__ void pair_move_words_all(const PhiloxPre (&pre)[WPT],
     }
 }
 
+// The words of both moves 2m and 2m+1 for all WPT walkers of a thread: the
+// three blocks of pair index m (tags 0, 1, 2), without a branch (the walk's
+// two-move iterations).
+template <int WPT>
+__device__ __forceinline__ void pair_words_both(const PhiloxPre (&pre)[WPT], uint32_t m,
+                                                uint32_t k0, uint32_t k1,
+                                                uint32_t (&wa)[WPT][6], uint32_t (&wb)[WPT][6]) {
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) {
+        Words4 t0, t1;
+        philox10_pair(pre[k], m, k0, k1, t0, t1);
+        const Words4 t2 = philox10_tag(pre[k], m, 2u, k0, k1);
+        wa[k][0] = t0.w[0]; wa[k][1] = t0.w[1]; wa[k][2] = t0.w[2];
+        wa[k][3] = t0.w[3]; wa[k][4] = t1.w[0]; wa[k][5] = t1.w[1];
+        wb[k][0] = t1.w[2]; wb[k][1] = t1.w[3]; wb[k][2] = t2.w[0];
+        wb[k][3] = t2.w[1]; wb[k][4] = t2.w[2]; wb[k][5] = t2.w[3];
+    }
+}
+
 // FP32: the same words.  The radius uniform keeps the full 32-bit resolution,
 // u_a = fl(fl(w) 2^-32 + 2^-33) (exact for w < 2^23, where the Gaussian tail
 // lives; elsewhere within an FP32 ulp of (w + 1/2) 2^-32).  A coarser grid

@@ -245,19 +245,11 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     int fold_len = 0;
     int buf = 0;
 
-    for (int s = 0; s < nsteps; ++s) {
-        const uint32_t step = step0 + (uint32_t)s;
+    // One move of every walker of the thread from its increments xi (and the
+    // Bernoulli steps' sub-ulp parts xlo), then its sums to the warp's staging
+    // rows and the alive count to the ring.
+    auto advance = [&](int s, L (&xi)[NG][6], L (&xlo)[NG][6]) {
         unsigned na = 0;
-        // Gaussian noise: the normals of all walkers first (the Philox words
-        // under one even / odd branch), so the moves that follow are one
-        // branch-free stretch; the Bernoulli steps are drawn per group.
-        L xi[NG][6], xlo[NG][6];
-        if (NOISE == 0) {
-            uint32_t words[WPT][6];
-            pair_move_words_all<WPT>(pre, carry, step, s == 0, k0, k1, words);
-#pragma unroll
-            for (int g = 0; g < NG; ++g) normals6_lanes<L>(&words[g * LW], xi[g], r2_fix);
-        }
         L q[4];
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
@@ -352,6 +344,13 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         na = __reduce_add_sync(0xffffffffu, na);
         const int r = s % kRing;
         if (lane_id == 0) s_cnt[(buf * kRing + r) * nwarps + warp] = na;
+        ++fold_len;
+    };
+    // After move s: the warp's column sums every fourth move, and the fold and
+    // the block's records at the end of each kRing-move window.
+    auto after = [&](int s) {
+        const int m4 = s & 3;
+        const int r = s % kRing;
         if (m4 == 3 || r == kRing - 1 || s == nsteps - 1) {
             __syncwarp();
             const int col = lane_id & 15, half = lane_id >> 4;
@@ -374,7 +373,6 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                 s_ring[((buf * kRing + r - m4 + (col >> 2)) * 4 + (col & 3)) * nwarps + warp] = v;
             __syncwarp();                        // the staging rows are rewritten next move
         }
-        ++fold_len;
         if (r == kRing - 1 || s == nsteps - 1) {
             if (lane_id == 0) s_shift[buf][warp] = c;
             // fold the FP32 increments into the FP64 base; new per-warp shift
@@ -400,12 +398,12 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 #pragma unroll
             for (int k = 0; k < WPT; ++k)
                 set_lane(dsh[k / LW], k % LW, sg[k] != 0 ? (float)(Lw[k] - c) * kLog2e : 0.f);
-            // position checkpoint (StateMixed::ckpt) after move step; compiled
+            // position checkpoint (StateMixed::ckpt) after move s; compiled
             // into the gradient's forward kernels only (CKPT).  Walkers that are
             // dead by then keep moving and write meaningless positions, which the
             // adjoint never reads (their final weight is zero).
             if (CKPT) {
-                const uint32_t done = step + 1u;
+                const uint32_t done = step0 + (uint32_t)s + 1u;
                 const uint32_t jc = done / (uint32_t)st.ckpt_every;
                 if (done % (uint32_t)st.ckpt_every == 0u && jc >= 1u && jc < (uint32_t)st.ckpt_count) {
                     float4* base = st.ckpt + (int64_t)jc * 2 * st.ckpt_slots;
@@ -458,6 +456,43 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             }
             buf ^= 1;
         }
+    };
+
+    int s = 0;
+    if (NOISE == 0 && (step0 & 1u) == 0u) {
+        // Gaussian noise from an even move: two moves per iteration.  The three
+        // Philox blocks of the pair index serve both moves (words 0-5 and 6-11),
+        // so they are drawn without a branch, and the second move's words and
+        // normals are independent of the first move's arithmetic, which the
+        // scheduler can interleave with them.  After the first move of a pair
+        // (an even s) there is no column sum, fold or end of launch.
+        for (; s + 1 < nsteps; s += 2) {
+            uint32_t wa[WPT][6], wb[WPT][6];
+            pair_words_both<WPT>(pre, (step0 + (uint32_t)s) >> 1, k0, k1, wa, wb);
+            L xa[NG][6], xb[NG][6], xlo[NG][6];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                normals6_lanes<L>(&wa[g * LW], xa[g], r2_fix);
+                normals6_lanes<L>(&wb[g * LW], xb[g], r2_fix);
+            }
+            advance(s, xa, xlo);
+            advance(s + 1, xb, xlo);
+            after(s + 1);
+        }
+    }
+    for (; s < nsteps; ++s) {
+        const uint32_t step = step0 + (uint32_t)s;
+        // Gaussian noise: the normals of all walkers first (the Philox words
+        // under one even / odd branch); the Bernoulli steps are drawn per group.
+        L xi[NG][6], xlo[NG][6];
+        if (NOISE == 0) {
+            uint32_t words[WPT][6];
+            pair_move_words_all<WPT>(pre, carry, step, s == 0, k0, k1, words);
+#pragma unroll
+            for (int g = 0; g < NG; ++g) normals6_lanes<L>(&words[g * LW], xi[g], r2_fix);
+        }
+        advance(s, xi, xlo);
+        after(s);
     }
     // walkers alive now store their state (the ones killed during the launch
     // were stored when they died; dead ones are unchanged in memory)

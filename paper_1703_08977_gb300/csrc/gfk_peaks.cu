@@ -28,11 +28,13 @@ __global__ void __launch_bounds__(kThreads) peak_kernel(unsigned* __restrict__ s
     unsigned u[kChains];
     float f[kChains];
     double d[kChains];
+    unsigned long long f2[kChains];      // packed float pairs (GFK_PEAK_FFMA2)
 #pragma unroll
     for (int j = 0; j < kChains; ++j) {
         u[j] = t * 2654435761u + seed + j;
         f[j] = 1.0f + (float)(u[j] & 1023) * 1e-4f;
         d[j] = (double)f[j];
+        f2[j] = ((unsigned long long)__float_as_uint(f[j]) << 32) | __float_as_uint(f[j] + 0.5f);
     }
     for (int i = 0; i < kIters; ++i) {
 #pragma unroll
@@ -64,12 +66,17 @@ __global__ void __launch_bounds__(kThreads) peak_kernel(unsigned* __restrict__ s
                 asm volatile("{ .reg .f32 v; cvt.rn.f32.u32 v, %0; mov.b32 %0, v; }" : "+r"(u[j]));
             } else if (OP == GFK_PEAK_F2F) {
                 asm volatile("{ .reg .f64 v; cvt.f64.f32 v, %0; cvt.rn.f32.f64 %0, v; }" : "+f"(f[j]));
+            } else if (OP == GFK_PEAK_FFMA2) {
+                asm volatile("fma.rn.f32x2 %0, %0, %1, %2;"
+                             : "+l"(f2[j]) : "l"(0x3F7FF9723F7FF972ull), "l"(0x38D1B71738D1B717ull));
             }
         }
     }
     unsigned acc = 0;
 #pragma unroll
-    for (int j = 0; j < kChains; ++j) acc ^= u[j] ^ __float_as_uint(f[j]) ^ (unsigned)__double_as_longlong(d[j]);
+    for (int j = 0; j < kChains; ++j)
+        acc ^= u[j] ^ __float_as_uint(f[j]) ^ (unsigned)__double_as_longlong(d[j]) ^
+               (unsigned)(f2[j] ^ (f2[j] >> 32));
     if (acc == 0x9E3779B9u) sink[0] = acc;   // practically never; keeps the chains live
 }
 
@@ -124,11 +131,13 @@ extern "C" gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* la
         case GFK_PEAK_SIN: e = time_op<GFK_PEAK_SIN>(blocks, sink, s, &ms); break;
         case GFK_PEAK_I2F: e = time_op<GFK_PEAK_I2F>(blocks, sink, s, &ms); break;
         case GFK_PEAK_F2F: e = time_op<GFK_PEAK_F2F>(blocks, sink, s, &ms); break;
+        case GFK_PEAK_FFMA2: e = time_op<GFK_PEAK_FFMA2>(blocks, sink, s, &ms); break;
         default: e = cudaErrorInvalidValue; break;
     }
     cudaFreeAsync(sink, s);
     if (e != cudaSuccess) return GFK_ECUDA;
-    const double ops = (double)blocks * kThreads * kChains * kIters * (op == GFK_PEAK_F2F ? 2 : 1);
+    const double ops = (double)blocks * kThreads * kChains * kIters *
+                       (op == GFK_PEAK_F2F || op == GFK_PEAK_FFMA2 ? 2 : 1);
     *lane_ops_per_s = ops / (ms * 1e-3);
     return GFK_OK;
 }

@@ -35,7 +35,7 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_measure_peak", "gfk_set_graph", "gfk_autotune", "gfk_grad",
            "gfk_normal_moments", "gfk_kernel_count", "gfk_eval_f32")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
-            "i2f", "f2f")
+            "i2f", "f2f", "ffma2")
 GFK_NOALLOC_SCRATCH_BYTES = 32 << 20
 GFK_NOALLOC_MAX_WALKERS = 1 << 22
 

@@ -140,3 +140,50 @@ def test_mixed_grad_does_not_depend_on_checkpoint_interval(gfk_lib):
             assert l == l64, (K, l, l64)
         assert abs(l - l64) <= 1e-7 * abs(l64), (K, l, l64)
         np.testing.assert_allclose(g, g64, rtol=2e-5, atol=2e-5 * np.abs(g64).max())
+
+
+def test_grad_at_the_gradient_workload_size(gfk_lib):
+    """The gradient workload at full size (2^18 walkers, 2000 moves at dt 0.005,
+    checkpoints every 64 moves, the start theta = [2, 0.5, 0.5, 0, 0, 0, 0]): the
+    FP64 adjoint against Richardson-extrapolated common-random-number central
+    differences of the same loss (the final space-averaged energy, from gfk_energy
+    of the FP64 walk), to 1e-6 of the gradient's largest component; and the mixed
+    gradient (FP32 forward with FP64 weights) against the FP64 one, whose relative
+    difference is stated here: below 1e-5."""
+    gfk = gfk_lib
+    n, S, dt, K, h = 1 << 18, 2000, 0.005, 64, 1e-4
+    theta = [2.0, 0.5, 0.5, 0.0, 0.0, 0.0, 0.0]
+
+    def ctx(prec, th):
+        d = gfk.InstanceDesc(n_walkers=n, dt=dt, e_trial=-2.9037, seed=0, prec=prec)
+        return gfk.Context([d], trials=[(0, th)])
+
+    with ctx(gfk.GFK_PREC_FP64, theta) as c:
+        l64, g64 = gfk.gfk_grad(c.handle, 0, 0, S, K)
+        # the same loss through the forward walk and the per-step sums
+        c.propagate(S)
+        assert abs(c.energy(0)["E"][-1] - l64) <= 1e-12 * abs(l64)
+
+        def central(step):
+            fd = np.zeros(7)
+            for k in range(7):
+                vals = []
+                for sgn in (+1, -1):
+                    th = list(theta)
+                    th[k] += sgn * step
+                    c.reset()
+                    c.set_trial(0, 0, th)
+                    c.propagate(S)
+                    vals.append(c.energy(0)["E"][-1])
+                fd[k] = (vals[0] - vals[1]) / (2 * step)
+            return fd
+
+        d1 = central(h)
+        d2 = central(h / 2)
+    rich = (4 * d2 - d1) / 3
+    scale = np.abs(rich).max()
+    assert np.abs(g64 - rich).max() <= 1e-6 * scale, (np.abs(g64 - rich).max() / scale, g64, rich)
+    with ctx(gfk.GFK_PREC_MIXED, theta) as c:
+        l32, g32 = gfk.gfk_grad(c.handle, 0, 0, S, K)
+    assert abs(l32 - l64) < 1e-6, (l32, l64)
+    assert np.abs(g32 - g64).max() <= 1e-5 * np.abs(g64).max(), (g32, g64)
