@@ -93,14 +93,18 @@ SPECIAL_UNIT = {"fp_sqrt": "rsq", "fp_exp": "ex2", "fp_log": "lg2", "fp_sin": "s
 # Issue slots: 4 schedulers x 32 lanes per SM and clock.
 LANES_PER_SM_CLK = 128
 # ncu figures of the mixed walk kernel at the bench's launch shape (2^20 walkers x
-# 1024 moves, 128 threads x 2 walkers), valid only for the kernel sources they
-# were taken on (sha256 prefix of WALK_SOURCES): DRAM bytes (read + write) and
-# executed thread instructions per walker-step, and the issue-active fraction.
+# 1024 moves, 128 threads x 2 walkers; one capture per noise mode), valid only for
+# the kernel sources they were taken on (sha256 prefix of WALK_SOURCES): DRAM bytes
+# (read + write) and executed thread instructions per walker-step, the
+# issue-active fraction and the busiest pipe (the FMA-heavy pipe, which also runs
+# the integer multiplies of the Philox rounds).
 WALK_PROFILE = {       # workload -> capture
-    "ground": {"src_sha": "50abc19209121823", "bytes_per_walker_step": 0.19995,
-               "inst_per_walker_step": None, "issue_active": None},
-    "bernoulli": {"src_sha": "50abc19209121823", "bytes_per_walker_step": 0.19977,
-                  "inst_per_walker_step": None, "issue_active": None},
+    "ground": {"src_sha": "c27ddbbc1728fdcd", "bytes_per_walker_step": 0.19977,
+               "inst_per_walker_step": 240.7, "issue_active": 0.686,
+               "fmaheavy_active": 0.750},
+    "bernoulli": {"src_sha": "c27ddbbc1728fdcd", "bytes_per_walker_step": 0.19963,
+                  "inst_per_walker_step": 155.2, "issue_active": 0.742,
+                  "fmaheavy_active": 0.694},
 }
 
 # Sources the mixed walk kernel is compiled from (the kernels and the device
@@ -355,6 +359,7 @@ def walk_rooflines(name, insts, avg_launch_ms, ws_per_launch, peaks, n_sm, sm_ma
     inst = prof.get("inst_per_walker_step") if valid else None
     issue = {"frac": inst * rate / (n_sm * LANES_PER_SM_CLK * clk) if inst else None,
              "inst_per_walker_step": inst, "ncu_issue_active": prof.get("issue_active") if valid else None,
+             "ncu_fmaheavy_pipe_active": prof.get("fmaheavy_active") if valid else None,
              "basis": f"executed thread instructions (ncu) / ({n_sm} SMs x {LANES_PER_SM_CLK} "
                       "issue lanes x sampled SM clock)"}
     return roof, mufu, issue
