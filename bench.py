@@ -389,6 +389,16 @@ def measure_adjoint(steps, warmup, adam=True):
                 loss, g = gfk.gfk_grad(ctx.handle, 0, 0, S, K)
             el = (time.perf_counter() - t0) / reps
             res[name] = {"value": n * S / el, "seconds": el, "loss": loss, "grad": g.tolist()}
+            if prec == gfk.GFK_PREC_MIXED:
+                # the whole trajectory kept in HBM (ckpt_every 0): no recompute
+                gfk.gfk_grad(ctx.handle, 0, 0, S, 0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    loss0, g0 = gfk.gfk_grad(ctx.handle, 0, 0, S, 0)
+                el0 = (time.perf_counter() - t0) / reps
+                res["stored"] = {"value": n * S / el0, "seconds": el0,
+                                 "bitwise_equal": bool(np.array_equal(g0, g) and loss0 == loss)}
     clk = clocks.stop()
     gerr = np.abs(np.array(res["mixed"]["grad"]) - np.array(res["fp64"]["grad"])).max() / \
         np.abs(np.array(res["fp64"]["grad"])).max()
@@ -400,6 +410,13 @@ def measure_adjoint(steps, warmup, adam=True):
                          "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"]},
            "gradient_mixed_vs_fp64_rel": float(gerr),
            "gradient_mixed": res["mixed"]["grad"], "gradient_fp64": res["fp64"]["grad"],
+           "stored_trajectory": {
+               "value": res["stored"]["value"], "unit": UNIT,
+               "ms_per_step": 1e3 * res["stored"]["seconds"],
+               "trajectory_bytes": 24 * n * (S + 1),
+               "gradient_bitwise_equal_to_checkpointed": res["stored"]["bitwise_equal"],
+               "note": "ckpt_every 0: the forward keeps every position in HBM and the reverse "
+                       "sweep reads them instead of recomputing 64-move segments"},
            "gpu_launches": 5 + 2 * ((S + K - 1) // K) + 1,
            "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
            "roofline": None,

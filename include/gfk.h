@@ -244,16 +244,22 @@ gfk_status gfk_restore(gfk_ctx* ctx, const void* host_blob, int64_t bytes);
  * context's precision -- the same trajectories gfk_propagate produces --
  * keeping the positions every ckpt_every moves (1..1024), then sweeps the
  * adjoint of the Euler-Maruyama recursion backwards, recomputing each segment
- * from its checkpoint.  Loss 0: E = sum_i w_i E_L(X_i) / sum_i w_i at the last
+ * from its checkpoint.  ckpt_every = 0 trades memory for that recompute: the
+ * mixed path's forward keeps every position (the whole trajectory) and the
+ * sweep reads it in 64-move segments, with nothing recomputed; the gradient is
+ * bitwise the one of ckpt_every = 64 (the FP64 path runs ckpt_every = 64).
+ * Loss 0: E = sum_i w_i E_L(X_i) / sum_i w_i at the last
  * move (the quantity of Eq. 4's space average); loss 1: the weighted variance
  * of E_L at the last move.  Only the Jastrow-product family is supported
  * (GFK_EINVAL otherwise); grad receives the derivatives with respect to all
  * seven parameters [Z, a, beta, c1, c2, c3, c4] (n_params must be 7), *loss
  * the loss (may be NULL).  Does not touch the context's population.
  * Synchronises the stream.  Needs working memory of about
- * n_walkers x (n_steps / ckpt_every + ckpt_every) x 48 bytes (FP64), which the
- * context allocates on the first call, keeps for later calls (growing it when
- * one needs more) and frees in gfk_destroy. */
+ * n_walkers x (n_steps / ckpt_every + ckpt_every) x 48 bytes (FP64; 32 bytes
+ * mixed), or n_walkers x (n_steps + 1) x 24 bytes for ckpt_every = 0 on the
+ * mixed path (12.6 GB for 2^18 walkers and 2000 moves), which the context
+ * allocates on the first call, keeps for later calls (growing it when one
+ * needs more) and frees in gfk_destroy; GFK_ENOMEM when it cannot. */
 gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_steps,
                     int32_t ckpt_every, double* grad, int32_t n_params, double* loss);
 
@@ -374,6 +380,29 @@ const char* gfk_status_string(gfk_status s);
 
 /* The last CUDA error message recorded by ctx ("" if none). */
 const char* gfk_last_error(gfk_ctx* ctx);
+
+/* Bounds checks of the debug build (the library compiled with -DGFK_DEBUG,
+ * libgfk_debug.so; not a passage of the paper: a tool for changing the
+ * library).  That build registers every device buffer it allocates, the
+ * allocation-free entry point's scratch and the caller buffers passed to it,
+ * and its kernels check each access to walker state, block records, per-step
+ * series, exported walkers and the gradient's checkpoints, segments and
+ * trajectory against those ranges.  A failed check skips the access (a load
+ * reads zeros), sets a bit in a device status word and records the first
+ * failing device address; no kernel traps.  Registration synchronises the
+ * device, so the debug build is slow and is not for timing.
+ *   *debug_build  1 in the debug build, 0 in the release build (which has no
+ *                 checks and reports zeros)
+ *   *flags        the bits that failed since the last clear: 1 walker state,
+ *                 2 block record, 4 series row or exported walker, 8
+ *                 checkpoint / segment / trajectory, 16 more live buffers than
+ *                 the table holds (checks were off)
+ *   *first_addr   the first failing address (0 if none)
+ *   clear != 0    resets flags and address after reading them
+ * Any pointer may be NULL.  Reads the current device's word (synchronous);
+ * GFK_ECUDA if that fails. */
+gfk_status gfk_debug_status(int32_t* debug_build, uint32_t* flags, uint64_t* first_addr,
+                            int32_t clear);
 
 #ifdef __cplusplus
 }

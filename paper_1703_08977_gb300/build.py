@@ -2,6 +2,12 @@
 
     python -m paper_1703_08977_gb300.build            # build if sources changed
     python -m paper_1703_08977_gb300.build --force    # rebuild
+    python -m paper_1703_08977_gb300.build --debug    # libgfk_debug.so (bounds checks)
+
+The debug library is compiled with -DGFK_DEBUG and relocatable device code
+(its kernels in every unit share one table of registered buffers and one
+status word, defined in gfk_debug.cu); gfk.load() takes it when the
+environment sets GFK_DEBUG=1.
 """
 from __future__ import annotations
 
@@ -17,6 +23,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgfk.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libgfk_debug.so")
+DEBUG_FLAGS = ["-DGFK_DEBUG", "-rdc=true"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -42,15 +51,15 @@ def _deps():
         glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(INCLUDE, "gfk.h"), __file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src: str, extra_flags) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra_flags, out_dir: str = BUILD) -> str:
+    obj = os.path.join(out_dir, os.path.basename(src) + ".o")
     cmd = [nvcc(), *ARCH, *COMMON, *PER_FILE.get(os.path.basename(src), []), *extra_flags,
            "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,29 +70,32 @@ def _compile(src: str, extra_flags) -> str:
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+def build(force: bool = False, verbose_ptxas: bool = False, debug: bool = False) -> str:
+    lib, out_dir = (LIB_DEBUG, BUILD_DEBUG) if debug else (LIB, BUILD)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + (DEBUG_FLAGS if debug else [])
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        objs = list(ex.map(lambda s: _compile(s, extra, out_dir), srcs))
+    tmp = lib + f".tmp{os.getpid()}"
+    # relocatable device code (debug) is device-linked by nvcc here
+    cmd = [nvcc(), *ARCH, *(["-rdc=true"] if debug else []), "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--ptxas-v", action="store_true", help="print register / smem use")
+    ap.add_argument("--debug", action="store_true", help="the bounds-checked debug library")
     a = ap.parse_args()
-    print(build(force=a.force or a.ptxas_v, verbose_ptxas=a.ptxas_v))
+    print(build(force=a.force or a.ptxas_v, verbose_ptxas=a.ptxas_v, debug=a.debug))
 
 
 if __name__ == "__main__":

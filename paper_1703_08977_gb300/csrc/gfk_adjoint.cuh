@@ -19,11 +19,15 @@
 // evaluation's statements, then their adjoints in reverse order) gives both
 // gradients, 6 + 7 numbers, at a few times the cost of the evaluation.
 //
-// Positions are not stored for the whole walk: the forward keeps them every K
-// moves (checkpoints), and the backward recomputes each K-move segment from
-// its checkpoint with the same noise (Philox words, or the walker's Superduper
-// generator skipped ahead to the segment's first move) and the same arithmetic
-// as the forward kernel of its precision, then sweeps it in reverse.
+// Positions: the forward keeps them every K moves (checkpoints), and the
+// backward recomputes each K-move segment from its checkpoint with the same
+// noise (Philox words, or the walker's Superduper generator skipped ahead to
+// the segment's first move) and the same arithmetic as the forward kernel of
+// its precision, then sweeps it in reverse.  Where device memory allows, the
+// mixed path's forward instead keeps the whole trajectory (24 bytes per walker
+// and move) and the backward sweeps the same K-move segments straight from it
+// with nothing recomputed: the same positions, so the same gradient bit for
+// bit.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,11 +49,17 @@ struct AdjTerminal {
 template <typename T> struct PosIO;
 template <> struct PosIO<double> {
     // checkpoint / segment planes: [6][n] doubles
+    __device__ __forceinline__ static bool ok(const double* base, int64_t n, int64_t i) {
+        return GFK_DBG_OK(base + i, sizeof(double), kDbgPositions) &&
+               GFK_DBG_OK(base + 5 * n + i, sizeof(double), kDbgPositions);
+    }
     __device__ __forceinline__ static void load(const double* base, int64_t n, int64_t i, double x[6]) {
+        const bool in = ok(base, n, i);
 #pragma unroll
-        for (int d = 0; d < 6; ++d) x[d] = base[d * n + i];
+        for (int d = 0; d < 6; ++d) x[d] = in ? base[d * n + i] : 0.0;
     }
     __device__ __forceinline__ static void store(double* base, int64_t n, int64_t i, const double x[6]) {
+        if (!ok(base, n, i)) return;
 #pragma unroll
         for (int d = 0; d < 6; ++d) base[d * n + i] = x[d];
     }
@@ -57,12 +67,22 @@ template <> struct PosIO<double> {
 };
 template <> struct PosIO<float> {
     // planes: two float4 per walker (x1,y1,z1,x2), (y2,z2,-,-) -- the state layout
+    __device__ __forceinline__ static bool ok(const float* base, int64_t n, int64_t i) {
+        return GFK_DBG_OK(reinterpret_cast<const float4*>(base) + i, sizeof(float4), kDbgPositions) &&
+               GFK_DBG_OK(reinterpret_cast<const float4*>(base) + n + i, sizeof(float4),
+                          kDbgPositions);
+    }
     __device__ __forceinline__ static void load(const float* base, int64_t n, int64_t i, float x[6]) {
+        if (!ok(base, n, i)) {
+            for (int d = 0; d < 6; ++d) x[d] = 0.f;
+            return;
+        }
         const float4 a = reinterpret_cast<const float4*>(base)[i];
         const float4 b = reinterpret_cast<const float4*>(base)[n + i];
         x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y;
     }
     __device__ __forceinline__ static void store(float* base, int64_t n, int64_t i, const float x[6]) {
+        if (!ok(base, n, i)) return;
         reinterpret_cast<float4*>(base)[i] = make_float4(x[0], x[1], x[2], x[3]);
         reinterpret_cast<float4*>(base)[n + i] = make_float4(x[4], x[5], 0.f, 0.f);
     }
@@ -77,12 +97,22 @@ template <> struct PosIO<float> {
 // from the (256-byte aligned) segment buffer, as 16-byte vector loads need.
 template <typename T> struct SegIO : PosIO<T> {};
 template <> struct SegIO<float> {
+    __device__ __forceinline__ static bool ok(const float* base, int64_t ns, int64_t i) {
+        return GFK_DBG_OK(reinterpret_cast<const float4*>(base) + i, sizeof(float4), kDbgPositions) &&
+               GFK_DBG_OK(reinterpret_cast<const float2*>(base + 4 * ns) + i, sizeof(float2),
+                          kDbgPositions);
+    }
     __device__ __forceinline__ static void load(const float* base, int64_t ns, int64_t i, float x[6]) {
+        if (!ok(base, ns, i)) {
+            for (int d = 0; d < 6; ++d) x[d] = 0.f;
+            return;
+        }
         const float4 a = reinterpret_cast<const float4*>(base)[i];
         const float2 b = reinterpret_cast<const float2*>(base + 4 * ns)[i];
         x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y;
     }
     __device__ __forceinline__ static void store(float* base, int64_t ns, int64_t i, const float x[6]) {
+        if (!ok(base, ns, i)) return;
         reinterpret_cast<float4*>(base)[i] = make_float4(x[0], x[1], x[2], x[3]);
         reinterpret_cast<float2*>(base + 4 * ns)[i] = make_float2(x[4], x[5]);
     }
@@ -428,7 +458,9 @@ adj_terminal_final_kernel(const double* __restrict__ part_max,
 }
 
 // The reverse sweep: one thread per walker, all segments from the last to the
-// first; per block the summed parameter adjoint theta_bar.
+// first; per block the summed parameter adjoint theta_bar.  traj: the whole
+// trajectory in the segment layout (plane m = the positions after move m), or
+// NULL to recompute each segment from its checkpoint into seg.
 // Blocks per SM the reverse sweep is compiled for: the FP32 sweep runs 6
 // (80 registers, no spills; against 4 blocks at 120 registers +0.4 %, 5 blocks
 // -0.8 %, 8 blocks with spills -2.5 %: more resident walkers also widen the
@@ -440,7 +472,7 @@ template <typename T>
 __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
 adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, int J,
                     int loss_kind, const T* __restrict__ ckpt, T* __restrict__ seg,
-                    const double* __restrict__ ew, const AdjTerminal* __restrict__ term,
+                    const T* __restrict__ traj, const double* __restrict__ ew, const AdjTerminal* __restrict__ term,
                     double* __restrict__ part_theta) {
     __shared__ TrialDev<T> s_trial;
     __shared__ double s_red[kNumTheta][kAdjThreads / 32];
@@ -478,15 +510,22 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
             for (int j = J - 1; j >= 0; --j) {
                 const int n_lo = j * K;
                 const int n_hi = (n_lo + K < S) ? n_lo + K : S;
-                // recompute the segment's positions n_lo .. n_hi
-                T x[6];
-                PosIO<T>::load(ckpt + (int64_t)j * PosIO<T>::kWords * n, n, i, x);
-                if (bern) {
-                    if (poly) adj_recompute<1, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
-                    else adj_recompute<1, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
-                } else {
-                    if (poly) adj_recompute<0, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
-                    else adj_recompute<0, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                // the segment's positions n_lo .. n_hi: planes m - p0 of pos
+                const T* pos = traj;
+                int p0 = 0;
+                if (traj == nullptr) {
+                    // recomputed from the checkpoint
+                    T x[6];
+                    PosIO<T>::load(ckpt + (int64_t)j * PosIO<T>::kWords * n, n, i, x);
+                    if (bern) {
+                        if (poly) adj_recompute<1, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                        else adj_recompute<1, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                    } else {
+                        if (poly) adj_recompute<0, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                        else adj_recompute<0, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                    }
+                    pos = seg;
+                    p0 = n_lo;
                 }
                 // sweep it backwards
                 const int n_top = (j == J - 1) ? n_hi : n_hi - 1;
@@ -496,11 +535,11 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 // each move loads the position of the next (earlier) one, so the
                 // load's latency hides behind a gradient evaluation (+2.2 %)
                 T xv[6];
-                SegIO<T>::load(seg + (int64_t)(n_top - n_lo) * SegIO<T>::kWords * ns, ns, i, xv);
+                SegIO<T>::load(pos + (int64_t)(n_top - p0) * SegIO<T>::kWords * ns, ns, i, xv);
                 for (int m = n_top; m >= n_lo; --m) {
                     T xnext[6];
                     const int mp = m > n_lo ? m - 1 : m;
-                    SegIO<T>::load(seg + (int64_t)(mp - n_lo) * SegIO<T>::kWords * ns, ns, i, xnext);
+                    SegIO<T>::load(pos + (int64_t)(mp - p0) * SegIO<T>::kWords * ns, ns, i, xnext);
                     // phi = w . b + wE E_L at X_m
                     T wv[6];
 #pragma unroll
@@ -558,7 +597,7 @@ adj_grad_final_kernel(const double* __restrict__ part_theta, int nblk, double* _
 // Host side of one precision: terminal passes, reverse sweep, final sum.
 template <typename T>
 cudaError_t adj_run(const InstDev* inst, int64_t n, int S, int K, int loss_kind, const T* ckpt,
-                    T* seg, const T* pos_final, const double* logw_final, double* ew,
+                    T* seg, const T* traj, const T* pos_final, const double* logw_final, double* ew,
                     double* part_max, double* part_sums, double* part_theta, AdjTerminal* term,
                     double* grad, cudaStream_t stream) {
     const int nblk = (int)((n + kAdjThreads - 1) / kAdjThreads);
@@ -569,7 +608,7 @@ cudaError_t adj_run(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
     adj_terminal_final_kernel<<<1, kFinalThreads, 0, stream>>>(part_max, part_sums, nblk, loss_kind,
                                                             term);
     adj_backward_kernel<T><<<nblk, kAdjThreads, 0, stream>>>(inst, n, S, K, J, loss_kind, ckpt, seg,
-                                                              ew, term, part_theta);
+                                                              traj, ew, term, part_theta);
     adj_grad_final_kernel<<<1, kFinalThreads, 0, stream>>>(part_theta, nblk, grad);
     return cudaGetLastError();
 }

@@ -6,11 +6,12 @@
 namespace gfk {
 
 cudaError_t launch_adjoint_f32(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
-                               const float* ckpt, float* seg, const float* pos_final,
+                               const float* ckpt, float* seg, const float* traj,
+                               const float* pos_final,
                                const double* logw_final, double* ew, double* part_max,
                                double* part_sums, double* part_theta, void* term, double* grad,
                                cudaStream_t stream) {
-    return adj_run<float>(inst, n, S, K, loss_kind, ckpt, seg, pos_final, logw_final, ew, part_max,
+    return adj_run<float>(inst, n, S, K, loss_kind, ckpt, seg, traj, pos_final, logw_final, ew, part_max,
                           part_sums, part_theta, (AdjTerminal*)term, grad, stream);
 }
 

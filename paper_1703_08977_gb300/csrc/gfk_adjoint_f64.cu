@@ -9,7 +9,7 @@ cudaError_t launch_adjoint_f64(const InstDev* inst, int64_t n, int S, int K, int
                                const double* logw_final, double* ew, double* part_max,
                                double* part_sums, double* part_theta, void* term, double* grad,
                                cudaStream_t stream) {
-    return adj_run<double>(inst, n, S, K, loss_kind, ckpt, seg, pos_final, logw_final, ew, part_max,
+    return adj_run<double>(inst, n, S, K, loss_kind, ckpt, seg, nullptr, pos_final, logw_final, ew, part_max,
                            part_sums, part_theta, (AdjTerminal*)term, grad, stream);
 }
 

@@ -154,11 +154,14 @@ gfk_status dev_alloc(gfk_ctx* ctx, void** p, size_t bytes) {
         return GFK_ENOMEM;
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    debug_register(*p, bytes);
     return GFK_OK;
 }
 
 void dev_free(void* p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+    debug_unregister(p);
+    cudaFree(p);
 }
 
 // Grows a device buffer of the context to at least `bytes` (its contents are
@@ -1174,7 +1177,7 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
     gfk_status st = check_inst(ctx, inst);
     if (st != GFK_OK) return st;
     if (loss_kind != 0 && loss_kind != 1) return GFK_EINVAL;
-    if (n_steps < 1 || n_steps > 0x7fffffffll || ckpt_every < 1 || ckpt_every > 1024)
+    if (n_steps < 1 || n_steps > 0x7fffffffll || ckpt_every < 0 || ckpt_every > 1024)
         return GFK_EINVAL;
     if (!grad || n_params != 7) return GFK_EINVAL;
     if (!ctx->has_trial[inst]) return GFK_ESTATE;
@@ -1186,7 +1189,10 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
     }
     const bool f64 = ctx->prec == GFK_PREC_FP64;
     const int64_t n = ctx->desc[inst].n_walkers;
-    const int S = (int)n_steps, K = ckpt_every;
+    // ckpt_every 0: the mixed forward keeps the whole trajectory and the sweep
+    // reads it in 64-move segments; the FP64 path checkpoints every 64 moves
+    const bool keep_all = ckpt_every == 0 && !f64;
+    const int S = (int)n_steps, K = ckpt_every == 0 ? kRing : ckpt_every;
     const int J = (S + K - 1) / K;
     const size_t tsz = f64 ? sizeof(double) : sizeof(float);
     const int words = f64 ? 6 : 8;                       // position words per walker
@@ -1213,10 +1219,13 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
     const int part_rows = ckpt_in_kernel ? std::min(S, kGradChunk) : K;
     const size_t o_part = take(sizeof(PartialRec) * (size_t)part_rows * nblk);
     const size_t o_cnt = take(sizeof(unsigned long long) * kNumCounters);
-    const size_t o_ckpt = take(tsz * words * (size_t)n * J);
+    const size_t o_ckpt = take(keep_all ? 0 : tsz * words * (size_t)n * J);
     // the reverse sweep's segment planes use an even walker stride (SegIO)
     const size_t n_even = (size_t)((n + 1) & ~(int64_t)1);
-    const size_t o_seg = take(std::max(tsz * words * n_even * (K + 1), sizeof(double) * 7 * (size_t)n));
+    const size_t o_seg = take(std::max(keep_all ? 0 : tsz * words * n_even * (K + 1),
+                                       sizeof(double) * 7 * (size_t)n));
+    // the whole trajectory: S + 1 planes of 6 floats per walker (SegIO layout)
+    const size_t o_traj = take(keep_all ? sizeof(float) * 6 * n_even * ((size_t)S + 1) : 0);
     const size_t o_logw = take(sizeof(double) * (size_t)n);
     const size_t o_ew = take(sizeof(double) * 2 * (size_t)n);
     const size_t o_pmax = take(sizeof(double) * nblk_adj);
@@ -1258,14 +1267,20 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
         e = f64 ? launch_init_fp64(kind, shape.threads, (int)nblk, d_inst, bm, s64, part, cnt, ctx->stream)
                 : launch_init_mixed(kind, shape.threads, (int)nblk, d_inst, bm, smx, part, cnt, ctx->stream);
     if (ckpt_in_kernel) {
-        // checkpoint 0 is the initial state; the walk kernel writes 1 .. J - 1
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ckpt, base + o_state, tsz * words * (size_t)n,
-                                cudaMemcpyDeviceToDevice, ctx->stream);
-        smx.ckpt = (float4*)ckpt;
-        smx.ckpt_slots = n;
-        smx.ckpt_every = K;
-        smx.ckpt_count = J;
+        if (keep_all) {
+            // every position, the initial ones included, from the walk kernel
+            smx.traj = (float*)(base + o_traj);
+            smx.traj_stride = (int64_t)n_even;
+        } else {
+            // checkpoint 0 is the initial state; the walk kernel writes 1 .. J - 1
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ckpt, base + o_state, tsz * words * (size_t)n,
+                                    cudaMemcpyDeviceToDevice, ctx->stream);
+            smx.ckpt = (float4*)ckpt;
+            smx.ckpt_slots = n;
+            smx.ckpt_every = K;
+            smx.ckpt_count = J;
+        }
         for (int done = 0; done < S && e == cudaSuccess; done += kGradChunk) {
             const int steps = std::min(kGradChunk, S - done);
             e = launch_walk_mixed(mixed_walk_kind(kind, &ctx->trial[inst], 1), ctx->noise,
@@ -1274,6 +1289,7 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
                                   ctx->desc[inst].ee_on, ctx->stream);
         }
         smx.ckpt = nullptr;
+        smx.traj = nullptr;
     }
     for (int j = 0; j < J && !ckpt_in_kernel && e == cudaSuccess; ++j) {
         const size_t plane_bytes = tsz * words * (size_t)n;
@@ -1307,7 +1323,9 @@ gfk_status gfk_grad(gfk_ctx* ctx, int32_t inst, int32_t loss_kind, int64_t n_ste
                                    ctx->stream);
         else
             e = launch_adjoint_f32(d_inst, n, S, K, loss_kind, (const float*)ckpt,
-                                   (float*)(base + o_seg), (const float*)(base + o_state),
+                                   (float*)(base + o_seg),
+                                   keep_all ? (const float*)(base + o_traj) : nullptr,
+                                   (const float*)(base + o_state),
                                    logw_final, (double*)(base + o_ew), (double*)(base + o_pmax),
                                    (double*)(base + o_psum), (double*)(base + o_pth), term, grad_d,
                                    ctx->stream);

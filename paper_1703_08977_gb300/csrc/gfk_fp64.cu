@@ -25,6 +25,15 @@
 
 namespace gfk {
 
+// The debug build's check of a walker's slot in the state planes (true in the
+// release build).
+__device__ __forceinline__ bool f64_slot_ok(const StateF64& st, int64_t slot) {
+    return GFK_DBG_OK(st.x + slot, sizeof(double), kDbgState) &&
+           GFK_DBG_OK(st.x + 5 * st.stride + slot, sizeof(double), kDbgState) &&
+           GFK_DBG_OK(st.logw + slot, sizeof(double), kDbgState) &&
+           GFK_DBG_OK(st.sgn + slot, 1, kDbgState);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kMaxThreads)
 init_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
@@ -69,10 +78,12 @@ init_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
             q[3] = ev.el * ev.el;
             q[4] = 1.0;
         }
+        if (f64_slot_ok(st, slot)) {
 #pragma unroll
-        for (int d = 0; d < 6; ++d) st.x[d * st.stride + slot] = x[d];
-        st.logw[slot] = logw;
-        st.sgn[slot] = (int8_t)sg;
+            for (int d = 0; d < 6; ++d) st.x[d * st.stride + slot] = x[d];
+            st.logw[slot] = logw;
+            st.sgn[slot] = (int8_t)sg;
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -88,7 +99,7 @@ init_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
         PartialRec rec;
         rec.c = 0.0;
         rec.W = r[0]; rec.P = r[1]; rec.Q = r[2]; rec.R = r[3]; rec.n = r[4];
-        part[blk] = rec;
+        if (GFK_DBG_OK(part + blk, sizeof(PartialRec), kDbgRecord)) part[blk] = rec;
     }
     flush_counters(counters, inst, n_nonfinite, n_node, 0u);
 }
@@ -121,7 +132,7 @@ walk_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
     double x[6] = {0, 0, 0, 0, 0, 0};
     double logw = -INFINITY;
     int sg = 0;
-    if (valid) {
+    if (valid && f64_slot_ok(st, slot)) {
 #pragma unroll
         for (int d = 0; d < 6; ++d) x[d] = st.x[d * st.stride + slot];
         logw = st.logw[slot];
@@ -190,12 +201,13 @@ walk_fp64_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateF64 st,
                 PartialRec rec;
                 rec.c = c;
                 rec.W = acc[0]; rec.P = acc[1]; rec.Q = acc[2]; rec.R = acc[3]; rec.n = acc[4];
-                part[(int64_t)(s - r + rr) * nblk + blk] = rec;
+                PartialRec* dst = part + (int64_t)(s - r + rr) * nblk + blk;
+                if (GFK_DBG_OK(dst, sizeof(PartialRec), kDbgRecord)) *dst = rec;
             }
             c = block_max_shift(sg != 0 ? logw : -INFINITY, s_red);
         }
     }
-    if (valid) {
+    if (valid && f64_slot_ok(st, slot)) {
 #pragma unroll
         for (int d = 0; d < 6; ++d) st.x[d * st.stride + slot] = x[d];
         st.logw[slot] = logw;

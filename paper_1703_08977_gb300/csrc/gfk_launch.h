@@ -65,8 +65,11 @@ cudaError_t launch_adjoint_f64(const InstDev* inst, int64_t n, int S, int K, int
                                const double* logw_final, double* ew, double* part_max,
                                double* part_sums, double* part_theta, void* term, double* grad,
                                cudaStream_t stream);
+// traj: the forward's whole trajectory (StateMixed::traj), or NULL to
+// recompute the segments from the checkpoints
 cudaError_t launch_adjoint_f32(const InstDev* inst, int64_t n, int S, int K, int loss_kind,
-                               const float* ckpt, float* seg, const float* pos_final,
+                               const float* ckpt, float* seg, const float* traj,
+                               const float* pos_final,
                                const double* logw_final, double* ew, double* part_max,
                                double* part_sums, double* part_theta, void* term, double* grad,
                                cudaStream_t stream);

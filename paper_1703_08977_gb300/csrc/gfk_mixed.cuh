@@ -44,8 +44,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// The debug build's check of a walker's slot in the state planes (true in the
+// release build).
+__device__ __forceinline__ bool mixed_slot_ok(const StateMixed& st, int64_t slot) {
+    return GFK_DBG_OK(st.p0 + slot, sizeof(float4), kDbgState) &&
+           GFK_DBG_OK(st.p1 + slot, sizeof(float4), kDbgState) &&
+           GFK_DBG_OK(st.sgn + slot, 1, kDbgState);
+}
+
 __device__ __forceinline__ void store_mixed(const StateMixed& st, int64_t slot, const float x[6],
                                             double logw, int sg) {
+    if (!mixed_slot_ok(st, slot)) return;
     const long long bits = __double_as_longlong(logw);
     st.p0[slot] = make_float4(x[0], x[1], x[2], x[3]);
     st.p1[slot] = make_float4(x[4], x[5], __int_as_float((int)(bits & 0xffffffffLL)),
@@ -53,8 +62,29 @@ __device__ __forceinline__ void store_mixed(const StateMixed& st, int64_t slot, 
     st.sgn[slot] = (int8_t)sg;
 }
 
+// Positions of walker i after global move m in the trajectory planes
+// (StateMixed::traj).  Streaming stores: the adjoint reads them back once,
+// long after the walk has moved on.
+__device__ __forceinline__ void store_traj(const StateMixed& st, uint32_t m, int64_t i,
+                                           float x0, float x1, float x2, float x3, float x4,
+                                           float x5) {
+    float* pl = st.traj + (int64_t)m * 6 * st.traj_stride;
+    if (!GFK_DBG_OK(reinterpret_cast<float4*>(pl) + i, sizeof(float4), kDbgPositions) ||
+        !GFK_DBG_OK(reinterpret_cast<float2*>(pl + 4 * st.traj_stride) + i, sizeof(float2),
+                    kDbgPositions))
+        return;
+    __stcs(reinterpret_cast<float4*>(pl) + i, make_float4(x0, x1, x2, x3));
+    __stcs(reinterpret_cast<float2*>(pl + 4 * st.traj_stride) + i, make_float2(x4, x5));
+}
+
 __device__ __forceinline__ void load_mixed(const StateMixed& st, int64_t slot, float x[6],
                                            double& logw, int& sg) {
+    if (!mixed_slot_ok(st, slot)) {
+        for (int d = 0; d < 6; ++d) x[d] = 0.f;
+        logw = -INFINITY;
+        sg = 0;
+        return;
+    }
     const float4 a = st.p0[slot];
     const float4 b = st.p1[slot];
     x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y;
@@ -125,7 +155,7 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         PartialRec rec;
         rec.c = 0.0;
         rec.W = r[0]; rec.P = r[1]; rec.Q = r[2]; rec.R = r[3]; rec.n = r[4];
-        part[blk] = rec;
+        if (GFK_DBG_OK(part + blk, sizeof(PartialRec), kDbgRecord)) part[blk] = rec;
     }
     flush_counters(counters, inst, n_nonfinite, n_node, 0u);
 }
@@ -144,6 +174,10 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 // positions); a walker killed by a move has its position, a log-weight of
 // -inf and a zero sign stored at that move, and only walkers alive at the end
 // store their state then.
+//
+// CKPT: the gradient's forward.  It writes the position checkpoints
+// (StateMixed::ckpt) at its folds, or the whole trajectory (StateMixed::traj)
+// at every move, whichever of the two is set.
 template <int KIND, int WPT, int NOISE, bool PARAM, bool CKPT = false>
 __global__ void __launch_bounds__(WPT == 4 ? kMaxThreadsWpt4 : kMaxThreads)
 walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
@@ -218,6 +252,8 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         Lw[k] = -INFINITY;
         float xk[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (valid[k]) load_mixed(st, slot[k], xk, Lw[k], sg[k]);
+        if (CKPT && st.traj != nullptr && step0 == 0u && valid[k])
+            store_traj(st, 0u, slot[k] - I.off, xk[0], xk[1], xk[2], xk[3], xk[4], xk[5]);
 #pragma unroll
         for (int d = 0; d < 6; ++d) set_lane(x[k / LW][d], k % LW, xk[d]);
     }
@@ -270,6 +306,17 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             for (int d = 0; d < 6; ++d)
                 xn[d] = NOISE == 1 ? move_bern_lanes(x[g][d], b[g][d], xi[g][d], xlo[g][d], dtL)
                                    : move_gauss_lanes(x[g][d], b[g][d], xi[g][d], dtL, sdtL);
+            if (CKPT && st.traj != nullptr) {
+                // the whole trajectory (gfk_grad's forward): every walker's
+                // position after this move, dead ones included (the adjoint
+                // skips walkers whose final weight is zero)
+#pragma unroll
+                for (int j = 0; j < LW; ++j)
+                    if (valid[g * LW + j])
+                        store_traj(st, step0 + (uint32_t)s + 1u, slot[g * LW + j] - I.off,
+                                   lane_at(xn[0], j), lane_at(xn[1], j), lane_at(xn[2], j),
+                                   lane_at(xn[3], j), lane_at(xn[4], j), lane_at(xn[5], j));
+            }
             EvalLanes<L> ev;
             eval_lanes<KIND, L, PARAM, kPoly>(t, xn, ev);
             // a non-finite position is a non-finite kill, then a sign change a
@@ -398,11 +445,11 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 #pragma unroll
             for (int k = 0; k < WPT; ++k)
                 set_lane(dsh[k / LW], k % LW, sg[k] != 0 ? (float)(Lw[k] - c) * kLog2e : 0.f);
-            // position checkpoint (StateMixed::ckpt) after move s; compiled
-            // into the gradient's forward kernels only (CKPT).  Walkers that are
+            // position checkpoint (StateMixed::ckpt) after move s, in the
+            // gradient's forward kernels (CKPT) when it is set.  Walkers that are
             // dead by then keep moving and write meaningless positions, which the
             // adjoint never reads (their final weight is zero).
-            if (CKPT) {
+            if (CKPT && st.ckpt != nullptr) {
                 const uint32_t done = step0 + (uint32_t)s + 1u;
                 const uint32_t jc = done / (uint32_t)st.ckpt_every;
                 if (done % (uint32_t)st.ckpt_every == 0u && jc >= 1u && jc < (uint32_t)st.ckpt_count) {
@@ -410,6 +457,10 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 #pragma unroll
                     for (int k = 0; k < WPT; ++k) {
                         if (!valid[k]) continue;
+                        if (!GFK_DBG_OK(base + slot[k], sizeof(float4), kDbgPositions) ||
+                            !GFK_DBG_OK(base + st.ckpt_slots + slot[k], sizeof(float4),
+                                        kDbgPositions))
+                            continue;
                         const int g = k / LW, j = k % LW;
                         base[slot[k]] = make_float4(lane_at(x[g][0], j), lane_at(x[g][1], j),
                                                     lane_at(x[g][2], j), lane_at(x[g][3], j));
@@ -452,7 +503,8 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                 rec.c = cb;
                 rec.W = acc[0]; rec.P = acc[1]; rec.Q = acc[2]; rec.R = acc[3];
                 rec.n = (double)n_alive;
-                part[(int64_t)(s - r + rr) * nblk + blk] = rec;
+                PartialRec* dst = part + (int64_t)(s - r + rr) * nblk + blk;
+                if (GFK_DBG_OK(dst, sizeof(PartialRec), kDbgRecord)) *dst = rec;
             }
             buf ^= 1;
         }
@@ -560,7 +612,7 @@ void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, int blk0, int
     TrialDev<float> tk;
     std::memset(&tk, 0, sizeof(tk));
     if (one_trial) load_trial<float>(*one_trial, ee_on, tk);
-    if (st.ckpt != nullptr) {
+    if (st.ckpt != nullptr || st.traj != nullptr) {
         // gfk_grad's forward: kind 0, or the per-block dispatch for a trial
         // function with Jastrow polynomial terms
         if (kind == 0)

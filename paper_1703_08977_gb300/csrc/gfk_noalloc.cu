@@ -151,6 +151,13 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     rows_fit = rows_fit > 1024 ? 1024 : (rows_fit / kRing) * kRing;
     if (rows_fit < kRing) return GFK_EINVAL;   // cannot happen up to GFK_NOALLOC_MAX_WALKERS
 
+    // debug build: the scratch and the caller's buffers join the checked ranges
+    debug_register(scratch, GFK_NOALLOC_SCRATCH_BYTES);
+    debug_register(dev_p0, sizeof(float4) * (size_t)d.n_walkers);
+    debug_register(dev_p1, sizeof(float4) * (size_t)d.n_walkers);
+    debug_register(dev_sgn, (size_t)d.n_walkers);
+    debug_register(dev_rows, sizeof(SeriesRow) * (size_t)(n_steps + (init ? 1 : 0)));
+
     StateMixed sm{};
     sm.p0 = (float4*)dev_p0;
     sm.p1 = (float4*)dev_p1;

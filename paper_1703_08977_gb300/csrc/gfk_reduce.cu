@@ -57,6 +57,11 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
     const int inst = blockIdx.y;
     const int b0 = bm.begin[inst], b1 = bm.begin[inst + 1];
     const PartialRec* rp = part + (int64_t)row * nblk;
+    // debug build: the row's records of this instance must lie in the buffer
+    // (uniform over the block, so every thread returns together)
+    if (b1 > b0 && !(GFK_DBG_OK(rp + b0, sizeof(PartialRec), kDbgRecord) &&
+                     GFK_DBG_OK(rp + b1 - 1, sizeof(PartialRec), kDbgRecord)))
+        return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     double m = -INFINITY;
@@ -117,7 +122,8 @@ reduce_rows_kernel(const PartialRec* __restrict__ part, int nblk, BlockMap bm,
         out.Q = tot[2].hi;
         out.R = tot[3].hi;
         out.n = tot[4].hi;
-        series[(int64_t)inst * series_cap + row_base + row] = out;
+        SeriesRow* dst = series + (int64_t)inst * series_cap + row_base + row;
+        if (GFK_DBG_OK(dst, sizeof(SeriesRow), kDbgSeries)) *dst = out;
     }
 }
 
@@ -144,6 +150,13 @@ __global__ void export_fp64_kernel(StateF64 st, int64_t off, int64_t n, double* 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t slot = off + i;
+    if (!(GFK_DBG_OK(st.x + slot, sizeof(double), kDbgState) &&
+          GFK_DBG_OK(st.x + 5 * st.stride + slot, sizeof(double), kDbgState) &&
+          GFK_DBG_OK(st.logw + slot, sizeof(double), kDbgState) &&
+          GFK_DBG_OK(st.sgn + slot, 1, kDbgState) &&
+          GFK_DBG_OK(x6 + 6 * i, 6 * sizeof(double), kDbgSeries) &&
+          GFK_DBG_OK(logw + i, sizeof(double), kDbgSeries) && GFK_DBG_OK(alive + i, 1, kDbgSeries)))
+        return;
 #pragma unroll
     for (int d = 0; d < 6; ++d) x6[6 * i + d] = st.x[d * st.stride + slot];
     const int sg = st.sgn[slot];
@@ -156,6 +169,12 @@ __global__ void export_mixed_kernel(StateMixed st, int64_t off, int64_t n, doubl
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t slot = off + i;
+    if (!(GFK_DBG_OK(st.p0 + slot, sizeof(float4), kDbgState) &&
+          GFK_DBG_OK(st.p1 + slot, sizeof(float4), kDbgState) &&
+          GFK_DBG_OK(st.sgn + slot, 1, kDbgState) &&
+          GFK_DBG_OK(x6 + 6 * i, 6 * sizeof(double), kDbgSeries) &&
+          GFK_DBG_OK(logw + i, sizeof(double), kDbgSeries) && GFK_DBG_OK(alive + i, 1, kDbgSeries)))
+        return;
     const float4 a = st.p0[slot];
     const float4 b = st.p1[slot];
     x6[6 * i + 0] = a.x; x6[6 * i + 1] = a.y; x6[6 * i + 2] = a.z;

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "gfk.h"   // include/ is on the include path
+#include "gfk_debug.h"
 
 namespace gfk {
 
@@ -82,6 +83,14 @@ struct StateMixed {
     float4* ckpt;
     int64_t ckpt_slots;
     int32_t ckpt_every, ckpt_count;
+    // Optional whole trajectory written by the walk kernel (gfk_grad's forward
+    // when it keeps every position): the positions after global move m (m = 0:
+    // the initial ones, written by a launch that starts at move 0) of walker i
+    // (slot - off) go to traj + m * 6 * traj_stride as (x1, y1, z1, x2) at
+    // float4 [i] and (y2, z2) at float2 [2 * traj_stride + i] -- the adjoint's
+    // segment layout (traj_stride even).  NULL: none.
+    float* traj;
+    int64_t traj_stride;
 };
 
 // Steps between flushes of the per-step block sums; also the mixed path's

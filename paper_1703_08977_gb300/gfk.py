@@ -33,7 +33,7 @@ EXPORTS = ("gfk_create", "gfk_set_trial", "gfk_set_launch", "gfk_propagate", "gf
            "gfk_checkpoint", "gfk_restore", "gfk_profile", "gfk_profile_read", "gfk_reset",
            "gfk_destroy", "gfk_status_string", "gfk_last_error", "gfk_propagate_noalloc",
            "gfk_measure_peak", "gfk_set_graph", "gfk_autotune", "gfk_grad",
-           "gfk_normal_moments", "gfk_kernel_count", "gfk_eval_f32")
+           "gfk_normal_moments", "gfk_kernel_count", "gfk_eval_f32", "gfk_debug_status")
 PEAK_OPS = ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "lop3", "ex2", "rsq", "lg2", "sin",
             "i2f", "f2f", "ffma2")
 GFK_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -67,12 +67,17 @@ def library_path() -> str:
 
 
 def load(build_if_needed: bool = True):
-    """Load libgfk.so (building it in-tree first if sources changed)."""
+    """Load libgfk.so (building it in-tree first if sources changed); with GFK_DEBUG=1 in
+    the environment, the bounds-checked libgfk_debug.so instead (gfk_debug_status)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build() if build_if_needed else _build.LIB
+        debug = os.environ.get("GFK_DEBUG", "0") not in ("", "0")
+        if debug:
+            path = _build.build(debug=True) if build_if_needed else _build.LIB_DEBUG
+        else:
+            path = _build.build() if build_if_needed else _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"libgfk.so missing at {path}; build it with "
                                "python -m paper_1703_08977_gb300.build")
@@ -113,6 +118,8 @@ def load(build_if_needed: bool = True):
             "gfk_propagate_noalloc": ([c.POINTER(gfk_instance_desc), c.c_int32, dp, c.c_int32,
                                        P, P, P, c.c_int32, c.c_int64, c.c_int64, P, P, P],
                                       c.c_int),
+            "gfk_debug_status": ([c.POINTER(c.c_int32), c.POINTER(c.c_uint32),
+                                  c.POINTER(c.c_uint64), c.c_int32], c.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -293,6 +300,15 @@ def gfk_grad(ctx, inst, loss_kind, n_steps, ckpt_every=64):
     _check(load().gfk_grad(ctx, int(inst), int(loss_kind), int(n_steps), int(ckpt_every), _dp(g),
                            7, ctypes.byref(l)), "gfk_grad", ctx)
     return l.value, g
+
+
+def gfk_debug_status(clear=True):
+    """(debug_build, flags, first_addr) of the debug build's bounds checks (zeros in the
+    release build); clears them when `clear`."""
+    b, f, a = ctypes.c_int32(), ctypes.c_uint32(), ctypes.c_uint64()
+    _check(load().gfk_debug_status(ctypes.byref(b), ctypes.byref(f), ctypes.byref(a),
+                                   int(bool(clear))), "gfk_debug_status")
+    return b.value, f.value, a.value
 
 
 def gfk_set_graph(ctx, enable=True):

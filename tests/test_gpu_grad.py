@@ -96,6 +96,8 @@ def test_grad_leaves_population_and_rejects_bad_calls(gfk_lib):
             gfk.gfk_grad(a.handle, 0, 2, 10, 8)         # unknown loss
         with pytest.raises(gfk.GfkError):
             gfk.gfk_grad(a.handle, 0, 0, 0, 8)          # no moves
+        with pytest.raises(gfk.GfkError):
+            gfk.gfk_grad(a.handle, 0, 0, 10, -1)        # no such checkpoint interval
     from paper_1703_08977_gb300 import workloads as wl
     d = gfk.InstanceDesc(n_walkers=64, dt=0.01, e_trial=-2.17)
     with gfk.Context([d], trials=[(1, wl.triplet_2s3())]) as c:
@@ -142,6 +144,35 @@ def test_mixed_grad_does_not_depend_on_checkpoint_interval(gfk_lib):
         np.testing.assert_allclose(g, g64, rtol=2e-5, atol=2e-5 * np.abs(g64).max())
 
 
+@pytest.mark.parametrize("noise", [0, 1])
+@pytest.mark.parametrize("theta", [THETA, [2.0, 0.5, 0.5, 0.0, 0.0, 0.0, 0.0]])
+@pytest.mark.parametrize("wpt", [1, 2, 4])
+def test_mixed_grad_from_the_stored_trajectory_is_the_checkpointed_one(gfk_lib, noise, theta,
+                                                                      wpt):
+    """ckpt_every = 0 keeps the forward's whole trajectory and sweeps it with nothing
+    recomputed.  The positions the walk kernel stores are the ones the checkpointed
+    path recomputes (same noise, same arithmetic in every launch shape), and the sweep
+    flushes its FP32 partial sums at the same 64-move boundaries, so loss and gradient
+    are bitwise those of ckpt_every = 64: both losses, Gaussian and Bernoulli noise,
+    with and without Jastrow polynomial terms, 1, 2 and 4 walkers per thread, an odd
+    walker count and a ragged last segment.  The FP64 path runs 64 for 0."""
+    gfk = gfk_lib
+    n, S = 4099, 300
+    for loss_kind in (0, 1):
+        d = gfk.InstanceDesc(n_walkers=n, dt=0.005, e_trial=-2.9, seed=7, rng_stream=1,
+                             noise=noise)
+        with gfk.Context([d], trials=[(0, theta)]) as c:
+            c.set_launch(128, wpt)
+            l64, g64 = gfk.gfk_grad(c.handle, 0, loss_kind, S, 64)
+            l0, g0 = gfk.gfk_grad(c.handle, 0, loss_kind, S, 0)
+        assert l0 == l64, (l0, l64)
+        np.testing.assert_array_equal(g0, g64)
+    d = gfk.InstanceDesc(n_walkers=300, dt=0.005, e_trial=-2.9, seed=7, noise=noise,
+                         prec=gfk.GFK_PREC_FP64)
+    with gfk.Context([d], trials=[(0, theta)]) as c:
+        assert gfk.gfk_grad(c.handle, 0, 0, 100, 0)[0] == gfk.gfk_grad(c.handle, 0, 0, 100, 64)[0]
+
+
 def test_grad_at_the_gradient_workload_size(gfk_lib):
     """The gradient workload at full size (2^18 walkers, 2000 moves at dt 0.005,
     checkpoints every 64 moves, the start theta = [2, 0.5, 0.5, 0, 0, 0, 0]): the
@@ -185,5 +216,9 @@ def test_grad_at_the_gradient_workload_size(gfk_lib):
     assert np.abs(g64 - rich).max() <= 1e-6 * scale, (np.abs(g64 - rich).max() / scale, g64, rich)
     with ctx(gfk.GFK_PREC_MIXED, theta) as c:
         l32, g32 = gfk.gfk_grad(c.handle, 0, 0, S, K)
+        # the whole trajectory kept (12.6 GB): bitwise the checkpointed gradient
+        l0, g0 = gfk.gfk_grad(c.handle, 0, 0, S, 0)
+    assert l0 == l32
+    np.testing.assert_array_equal(g0, g32)
     assert abs(l32 - l64) < 1e-6, (l32, l64)
     assert np.abs(g32 - g64).max() <= 1e-5 * np.abs(g64).max(), (g32, g64)
