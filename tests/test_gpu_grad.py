@@ -160,7 +160,7 @@ def test_mixed_grad_from_the_stored_trajectory_is_the_checkpointed_one(gfk_lib, 
     n, S = 4099, 300
     for loss_kind in (0, 1):
         d = gfk.InstanceDesc(n_walkers=n, dt=0.005, e_trial=-2.9, seed=7, rng_stream=1,
-                             noise=noise)
+                             noise=noise, prec=gfk.GFK_PREC_MIXED)
         with gfk.Context([d], trials=[(0, theta)]) as c:
             c.set_launch(128, wpt)
             l64, g64 = gfk.gfk_grad(c.handle, 0, loss_kind, S, 64)
