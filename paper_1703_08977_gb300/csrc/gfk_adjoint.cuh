@@ -95,9 +95,7 @@ template <> struct PosIO<float> {
 // (two loads, like the state's two float4 planes, but a quarter less
 // traffic); with ns even every float4 plane starts a multiple of 48 bytes
 // from the (256-byte aligned) segment buffer, as 16-byte vector loads need.
-template <typename T> struct SegIO : PosIO<T> {
-    __device__ __forceinline__ static void prefetch(const T*, int64_t, int64_t) {}
-};
+template <typename T> struct SegIO : PosIO<T> {};
 template <> struct SegIO<float> {
     __device__ __forceinline__ static bool ok(const float* base, int64_t ns, int64_t i) {
         return GFK_DBG_OK(reinterpret_cast<const float4*>(base) + i, sizeof(float4), kDbgPositions) &&
@@ -118,16 +116,8 @@ template <> struct SegIO<float> {
         reinterpret_cast<float4*>(base)[i] = make_float4(x[0], x[1], x[2], x[3]);
         reinterpret_cast<float2*>(base + 4 * ns)[i] = make_float2(x[4], x[5]);
     }
-    // asks L2 for the position of walker i in the plane at base (no registers)
-    __device__ __forceinline__ static void prefetch(const float* base, int64_t ns, int64_t i) {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const float4*>(base) + i));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const float2*>(base + 4 * ns) + i));
-    }
     static constexpr int kWords = 6;          // floats per walker per move
 };
-
-// Moves ahead of the sweep whose positions are prefetched into L2 (FP32).
-constexpr int kAdjPrefetch = 4;
 
 // The forward move of the precision, written exactly as the walk kernel of
 // that precision writes it (so the recomputed positions are the forward's).
@@ -547,11 +537,6 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 T xv[6];
                 SegIO<T>::load(pos + (int64_t)(n_top - p0) * SegIO<T>::kWords * ns, ns, i, xv);
                 for (int m = n_top; m >= n_lo; --m) {
-                    // the position kAdjPrefetch moves on, towards L2 (within the
-                    // segment when it is recomputed; anywhere in a stored one)
-                    if (kAdjPrefetch > 0 && m - kAdjPrefetch >= (traj ? 0 : n_lo))
-                        SegIO<T>::prefetch(pos + (int64_t)(m - kAdjPrefetch - p0) * SegIO<T>::kWords * ns,
-                                           ns, i);
                     T xnext[6];
                     const int mp = m > n_lo ? m - 1 : m;
                     SegIO<T>::load(pos + (int64_t)(mp - p0) * SegIO<T>::kWords * ns, ns, i, xnext);
