@@ -99,19 +99,19 @@ LANES_PER_SM_CLK = 128
 # issue-active fraction and the busiest pipe (the FMA-heavy pipe, which also runs
 # the integer multiplies of the Philox rounds).
 WALK_PROFILE = {       # workload -> capture
-    "ground": {"src_sha": "c27ddbbc1728fdcd", "bytes_per_walker_step": 0.19977,
-               "inst_per_walker_step": 240.7, "issue_active": 0.686,
+    "ground": {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.20001,
+               "inst_per_walker_step": 240.6, "issue_active": 0.686,
                "fmaheavy_active": 0.750},
-    "bernoulli": {"src_sha": "c27ddbbc1728fdcd", "bytes_per_walker_step": 0.19963,
+    "bernoulli": {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.19952,
                   "inst_per_walker_step": 155.2, "issue_active": 0.742,
                   "fmaheavy_active": 0.694},
 }
 
 # Sources the mixed walk kernel is compiled from (the kernels and the device
 # code they include); a captured figure holds only while they are unchanged.
-WALK_SOURCES = ("paper_1703_08977_gb300/csrc/gfk_mixed.cuh", "paper_1703_08977_gb300/csrc/gfk_mixed.cu",
-                "paper_1703_08977_gb300/csrc/gfk_mixed_bern.cu", "paper_1703_08977_gb300/csrc/gfk_device.cuh",
-                "paper_1703_08977_gb300/csrc/gfk_block.cuh", "paper_1703_08977_gb300/csrc/gfk_types.h")
+WALK_SOURCES = tuple("paper_1703_08977_gb300/csrc/" + f for f in (
+    "gfk_mixed.cuh", "gfk_mixed.cu", "gfk_mixed_bern.cu", "gfk_device.cuh", "gfk_block.cuh",
+    "gfk_types.h", "gfk_lanes.cuh", "gfk_eval_f32.cuh", "gfk_debug.h"))
 
 
 def _src_sha() -> str:
@@ -669,6 +669,18 @@ def profile_case(args):
                          prec=args.prec, noise=args.noise, state=args.profile_state)
     launch = (args.threads or 128, args.wpt or 2) if args.prec == 1 else (128, 1)
     m = args.profile_moves
+    if args.profile_grad >= 0:
+        # the gradient instead: two gfk_grad calls of --profile-moves moves with
+        # checkpoints every --profile-grad moves (0: the whole trajectory kept),
+        # on the gradient workload's trial function
+        theta = [2.0, 0.5, 0.5, 0.0, 0.0, 0.0, 0.0]
+        with gfk.Context([d], trials=[(0, theta)], launch=launch) as ctx:
+            for _ in range(2):
+                loss, g = gfk.gfk_grad(ctx.handle, 0, 0, m, args.profile_grad)
+        print(json.dumps({"profile_case": True, "gradient": True, "walkers": n, "moves": m,
+                          "ckpt_every": args.profile_grad, "prec": args.prec, "loss": loss,
+                          "grad": g.tolist()}))
+        return
     with gfk.Context([d], trials=[(kind, params)], launch=launch) as ctx:
         ctx.propagate(m)
         ctx.propagate(m)
@@ -699,6 +711,9 @@ def main():
     ap.add_argument("--noise", type=int, default=0, help="profile case: 0 Gaussian, 1 Bernoulli")
     ap.add_argument("--profile-walkers", type=int, default=0)
     ap.add_argument("--profile-moves", type=int, default=64)
+    ap.add_argument("--profile-grad", type=int, default=-1,
+                    help="profile case: run gfk_grad with this checkpoint interval (0: the "
+                         "whole trajectory kept) instead of the walk")
     ap.add_argument("--profile-state", type=int, default=0, choices=(0, 1, 2),
                     help="profile case: trial function of state 0 (1^1S), 1 (2^3S), 2 (P_z)")
     ap.add_argument("--adam", action="store_true", help="adjoint workload: run 50 Adam steps")
