@@ -461,12 +461,18 @@ adj_terminal_final_kernel(const double* __restrict__ part_max,
 // first; per block the summed parameter adjoint theta_bar.  traj: the whole
 // trajectory in the segment layout (plane m = the positions after move m), or
 // NULL to recompute each segment from its checkpoint into seg.
-// Blocks per SM the reverse sweep is compiled for: the FP32 sweep runs 6
-// (80 registers, no spills; against 4 blocks at 120 registers +0.4 %, 5 blocks
-// -0.8 %, 8 blocks with spills -2.5 %: more resident walkers also widen the
-// segment positions' working set in L2), the FP64 one keeps the default.
+// Blocks per SM the reverse sweep is compiled for, and the moves between a
+// position's load and its use: the FP32 sweep runs 5 blocks (96 registers, no
+// spills) loading 3 moves ahead.  Measured on 2^18 walkers x 2000 moves (ms
+// per gradient call, checkpointed / stored trajectory): 1 move ahead at 6
+// blocks 13.82 / 10.90, at 5 blocks 13.79 / 10.68; 2 ahead at 6 blocks (spills)
+// 13.98 / 10.77, at 5 blocks 13.80 / 10.58; 3 ahead at 5 blocks 13.66 / 10.41;
+// 4 ahead at 5 blocks 13.91 / 10.54, at 4 blocks 13.72 / 10.32; 6 ahead at 5
+// blocks 14.14 / 10.67; 8 ahead at 4 blocks 14.25 / 10.72.  The FP64 sweep
+// keeps the default bound.
 template <typename T>
-constexpr int adj_min_blocks() { return sizeof(T) == 4 ? 6 : 1; }
+constexpr int adj_min_blocks() { return sizeof(T) == 4 ? 5 : 1; }
+constexpr int kAdjAhead = 3;
 
 template <typename T>
 __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
@@ -532,14 +538,27 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                 T tseg[kNumTheta];
 #pragma unroll
                 for (int k = 0; k < kNumTheta; ++k) tseg[k] = T(0);
-                // each move loads the position of the next (earlier) one, so the
-                // load's latency hides behind a gradient evaluation (+2.2 %)
-                T xv[6];
-                SegIO<T>::load(pos + (int64_t)(n_top - p0) * SegIO<T>::kWords * ns, ns, i, xv);
+                // each move loads the position kAdjAhead moves on, so the load's
+                // latency hides behind kAdjAhead gradient evaluations
+                T xq[kAdjAhead][6];
+#pragma unroll
+                for (int a = 0; a < kAdjAhead; ++a) {
+                    const int ma = n_top - a >= n_lo ? n_top - a : n_lo;
+                    SegIO<T>::load(pos + (int64_t)(ma - p0) * SegIO<T>::kWords * ns, ns, i, xq[a]);
+                }
+#pragma unroll kAdjAhead
                 for (int m = n_top; m >= n_lo; --m) {
-                    T xnext[6];
-                    const int mp = m > n_lo ? m - 1 : m;
+                    T xv[6], xnext[6];
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) xv[d] = xq[0][d];
+#pragma unroll
+                    for (int a = 0; a + 1 < kAdjAhead; ++a)
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) xq[a][d] = xq[a + 1][d];
+                    const int mp = m - kAdjAhead >= n_lo ? m - kAdjAhead : n_lo;
                     SegIO<T>::load(pos + (int64_t)(mp - p0) * SegIO<T>::kWords * ns, ns, i, xnext);
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) xq[kAdjAhead - 1][d] = xnext[d];
                     // phi = w . b + wE E_L at X_m
                     T wv[6];
 #pragma unroll
@@ -551,8 +570,6 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                     for (int d = 0; d < 6; ++d) lambda[d] += xb[d];
 #pragma unroll
                     for (int k = 0; k < kNumTheta; ++k) tseg[k] += thb[k];
-#pragma unroll
-                    for (int d = 0; d < 6; ++d) xv[d] = xnext[d];
                 }
 #pragma unroll
                 for (int k = 0; k < kNumTheta; ++k) theta[k * kAdjThreads] += (double)tseg[k];
