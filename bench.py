@@ -92,20 +92,24 @@ SPECIAL_UNIT = {"fp_sqrt": "rsq", "fp_exp": "ex2", "fp_log": "lg2", "fp_sin": "s
                 "fp_cos": "sin"}
 # Issue slots: 4 schedulers x 32 lanes per SM and clock.
 LANES_PER_SM_CLK = 128
-# ncu figures of the mixed walk kernel at the bench's launch shape (2^20 walkers x
-# 1024 moves, 128 threads x 2 walkers; one capture per noise mode), valid only for
-# the kernel sources they were taken on (sha256 prefix of WALK_SOURCES): DRAM bytes
-# (read + write) and executed thread instructions per walker-step, the
-# issue-active fraction and the busiest pipe (the FMA-heavy pipe, which also runs
-# the integer multiplies of the Philox rounds).
-WALK_PROFILE = {       # workload -> capture
-    "ground": {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.20001,
-               "inst_per_walker_step": 240.6, "issue_active": 0.686,
-               "fmaheavy_active": 0.750},
-    "bernoulli": {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.19952,
-                  "inst_per_walker_step": 155.2, "issue_active": 0.742,
-                  "fmaheavy_active": 0.694},
+# ncu figures of the mixed walk kernels at the bench's launch shape (2^20 walkers x
+# 1024 moves, 128 threads x 2 walkers; one capture per (state, noise) kernel:
+# `bench.py --profile-case --profile-walkers 1048576 --profile-moves 1024
+# --profile-state S --noise N`), valid only for the kernel sources they were taken
+# on (sha256 prefix of WALK_SOURCES): DRAM bytes (read + write) and executed thread
+# instructions per walker-step, the issue-active fraction and the busiest pipe (the
+# FMA-heavy pipe, which also runs the integer multiplies of the Philox rounds).
+WALK_PROFILE = {       # (state, noise) -> capture of that walk kernel
+    (0, 0): {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.20001,
+             "inst_per_walker_step": 240.6, "issue_active": 0.686, "fmaheavy_active": 0.750},
+    (0, 1): {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.19952,
+             "inst_per_walker_step": 155.2, "issue_active": 0.742, "fmaheavy_active": 0.694},
+    (1, 0): {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.20160,
+             "inst_per_walker_step": 279.1, "issue_active": 0.694, "fmaheavy_active": 0.716},
+    (2, 0): {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.20648,
+             "inst_per_walker_step": 314.9, "issue_active": 0.691, "fmaheavy_active": 0.719},
 }
+
 
 # Sources the mixed walk kernel is compiled from (the kernels and the device
 # code they include); a captured figure holds only while they are unchanged.
@@ -326,6 +330,24 @@ def measure_peaks():
             for op in ("ffma", "ffma2", "dfma", "ex2", "rsq", "lg2", "sin")}
 
 
+def _walk_profile(insts):
+    """The ncu figures of a workload's walk kernels, averaged over its instances by
+    walker count (one kernel per (state, noise) pair); None if a kernel has no capture
+    of the current sources."""
+    sha = _src_sha()
+    keys = ("bytes_per_walker_step", "inst_per_walker_step", "issue_active", "fmaheavy_active")
+    acc = dict.fromkeys(keys, 0.0)
+    total = 0
+    for d in insts:
+        p = WALK_PROFILE.get((d["state"], d["noise"]))
+        if p is None or p["src_sha"] != sha:
+            return None
+        for k in keys:
+            acc[k] += p[k] * d["n_walkers"]
+        total += d["n_walkers"]
+    return {k: v / total for k, v in acc.items()}
+
+
 def walk_rooflines(name, insts, avg_launch_ms, ws_per_launch, peaks, n_sm, sm_max, sm_mhz):
     """The walk kernel's rooflines from its own launch time: FP32 flops against the
     measured FFMA rate (the primary figure), the special-function unit against its
@@ -337,8 +359,8 @@ def walk_rooflines(name, insts, avg_launch_ms, ws_per_launch, peaks, n_sm, sm_ma
     fma_rate = max(peaks["ffma"], peaks.get("ffma2", 0.0))
     peak = 2.0 * fma_rate / 1e12
     derived = n_sm * LANES_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
-    prof = WALK_PROFILE.get(name)
-    valid = bool(prof) and prof["src_sha"] == _src_sha()
+    prof = _walk_profile(insts)
+    valid = prof is not None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": prof["bytes_per_walker_step"] * ws_per_launch if valid else None,
