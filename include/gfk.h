@@ -324,6 +324,26 @@ gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32_t trial_ki
                                  double* dev_rows, unsigned long long* dev_counters,
                                  void* cuda_stream);
 
+/* Forget the population: the next gfk_propagate re-initialises it (step 0). */
+gfk_status gfk_reset(gfk_ctx* ctx);
+
+/* Free the context and everything it allocated.  NULL is ignored. */
+void gfk_destroy(gfk_ctx* ctx);
+
+/* Static description of a status code. */
+const char* gfk_status_string(gfk_status s);
+
+/* The last CUDA error message recorded by ctx ("" if none). */
+const char* gfk_last_error(gfk_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics and measurement utilities.  None of these is a step of the
+ * method: they measure the device (instruction rates), check the FP32
+ * arithmetic of the mixed walk (moments of its normals, its trial evaluation
+ * at given positions) and read the debug build's bounds checks.  The tests
+ * and the benchmark use them; a user of the walk does not need them.
+ * ------------------------------------------------------------------------ */
+
 /* Instruction-throughput microbenchmarks (a measurement utility; the paper has
  * no counterpart): the denominators of the walk kernels' ALU roofline,
  * measured on the current device.  Each op runs independent chains of one
@@ -368,18 +388,6 @@ gfk_status gfk_normal_moments(int32_t method, void* cuda_stream, double* moments
 gfk_status gfk_eval_f32(int32_t trial_kind, const double* params, int32_t n_params,
                         int32_t ee_on, int64_t n, const float* host_x, int32_t lanes,
                         float* host_b, float* host_el, int32_t* host_sign, void* cuda_stream);
-
-/* Forget the population: the next gfk_propagate re-initialises it (step 0). */
-gfk_status gfk_reset(gfk_ctx* ctx);
-
-/* Free the context and everything it allocated.  NULL is ignored. */
-void gfk_destroy(gfk_ctx* ctx);
-
-/* Static description of a status code. */
-const char* gfk_status_string(gfk_status s);
-
-/* The last CUDA error message recorded by ctx ("" if none). */
-const char* gfk_last_error(gfk_ctx* ctx);
 
 /* Bounds checks of the debug build (the library compiled with -DGFK_DEBUG,
  * libgfk_debug.so; not a passage of the paper: a tool for changing the
