@@ -100,15 +100,16 @@ LANES_PER_SM_CLK = 128
 # instructions per walker-step, the issue-active fraction and the busiest pipe (the
 # FMA-heavy pipe, which also runs the integer multiplies of the Philox rounds).
 WALK_PROFILE = {       # (state, noise) -> capture of that walk kernel
-    (0, 0): {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.20001,
-             "inst_per_walker_step": 240.6, "issue_active": 0.686, "fmaheavy_active": 0.750},
-    (0, 1): {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.19952,
+    (0, 0): {"src_sha": "2ab73dc43b42b6b9", "bytes_per_walker_step": 0.19981,
+             "inst_per_walker_step": 243.8, "issue_active": 0.691, "fmaheavy_active": 0.759},
+    (0, 1): {"src_sha": "2ab73dc43b42b6b9", "bytes_per_walker_step": 0.19952,
              "inst_per_walker_step": 155.2, "issue_active": 0.742, "fmaheavy_active": 0.694},
-    (1, 0): {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.20160,
+    (1, 0): {"src_sha": "2ab73dc43b42b6b9", "bytes_per_walker_step": 0.20240,
              "inst_per_walker_step": 279.1, "issue_active": 0.694, "fmaheavy_active": 0.716},
-    (2, 0): {"src_sha": "5d0a66549ac4fb2e", "bytes_per_walker_step": 0.20648,
-             "inst_per_walker_step": 314.9, "issue_active": 0.691, "fmaheavy_active": 0.719},
+    (2, 0): {"src_sha": "2ab73dc43b42b6b9", "bytes_per_walker_step": 0.20737,
+             "inst_per_walker_step": 314.9, "issue_active": 0.691, "fmaheavy_active": 0.718},
 }
+
 
 
 # Sources the mixed walk kernel is compiled from (the kernels and the device

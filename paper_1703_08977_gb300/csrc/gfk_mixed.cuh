@@ -164,9 +164,10 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 // arrives as the kernel argument tk (constant-bank operands, no shared-memory
 // loads, no registers); otherwise each block loads its instance's trial into
 // shared memory (kind 0 then copies its parameters into registers).  The
-// launcher uses PARAM whenever the launch covers one trial function (kind 0
-// walks of two packed walkers per thread: +0.9 %, 9.34 -> 9.26 ms per
-// 1024-move launch of 2^20 walkers; the orbital-pair kinds: +11 %).
+// launcher uses PARAM whenever the launch covers one trial function, except
+// for kind 0 with Bernoulli noise (kind 0, Gaussian noise, two packed walkers
+// per thread: +0.9 %, 9.34 -> 9.26 ms per 1024-move launch of 2^20 walkers;
+// Bernoulli noise: -1.0 %, 5.58 -> 5.63 ms; the orbital-pair kinds: +11 %).
 //
 // Lanes: the thread's walkers are evaluated in groups of two, the two lanes of
 // a float2 (gfk_lanes.cuh: packed FP32 instructions, one issue slot for both
@@ -625,7 +626,7 @@ void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, int blk0, int
                                                        step0, nsteps, part, counters, tk, stream, run);
         return;
     }
-    if (one_trial && kind == 0)
+    if (one_trial && kind == 0 && NOISE == 0)
         launch_walk_mixed_k<0, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                             part, counters, tk, stream, run);
     else if (one_trial && kind == 1)

@@ -57,8 +57,11 @@ def test_triplet_workload_full_size(gfk_lib):
     on the same walkers, within 1e-6 hartree for the FP32 rounding of the walk
     (the ground state's difference stays below 1e-8 over 2000 moves) plus the
     whole contribution w_i (|E_L,i| + |E|) / W of each walker alive on one path
-    and not the other (a walker that straddles the exact node within FP32
-    rounding)."""
+    and not the other.  Such walkers come from the node: one that straddles it
+    within FP32 rounding, or one that a near-node drift kick (|b| dt >> 1)
+    threw hundreds of bohr out, where the unscaled FP64 psi of the FP64 path
+    and of the oracle underflows to exactly 0 (a kill) while the mixed path,
+    which factors the largest exponential out of psi, keeps it alive."""
     gfk = gfk_lib
     n, moves, dt, et, seed = 1 << 20, 1024, 0.0025, wl.E_T[1], 0
     p = wl.triplet_2s3()
@@ -78,18 +81,28 @@ def test_triplet_workload_full_size(gfk_lib):
     n_near = _check_fp64(x64[ids], lw64[ids], al64[ids], w, d_min, "fp64")
     _check_mixed(x32[ids], al32[ids], w, d_min, "mixed")
 
-    # the whole population: mixed vs FP64 at the last move
+    # the whole population: mixed vs FP64 at the last move.  A walker alive on
+    # one path and dead on the other enters with its whole contribution, its
+    # local energy from the path on which it is alive (the oracle's FP64
+    # evaluation, or the mixed walk's own FP32 one).
     mis = np.flatnonzero(al32 != al64)
     c = max(lw64[al64].max(), lw32[al32].max())
     W = np.exp(lw64[al64] - c).sum()
     budget = 1e-6
+    n_far = 0
     if mis.size:
-        lw = np.where(al64[mis], lw64[mis], lw32[mis])
-        xx = np.where(al64[mis][:, None], x64[mis], x32[mis])
-        _, _, el, _ = oracle.trial_eval_many(1, p, xx)
+        in64 = al64[mis]
+        lw = np.where(in64, lw64[mis], lw32[mis])
+        el = np.empty(mis.size)
+        if in64.any():
+            el[in64] = oracle.trial_eval_many(1, p, x64[mis[in64]])[2]
+        if (~in64).any():
+            el[~in64] = gfk.gfk_eval_f32(1, p, x32[mis[~in64]].astype(np.float32))[1]
         budget += float((2.0 * np.exp(lw - c) * (np.abs(el) + abs(e64[-1]))).sum() / W)
-    print(f"near-node sampled walkers {n_near}, alive mismatches {mis.size}, "
-          f"final dE {abs(e32[-1] - e64[-1]):.3e}, budget {budget:.3e}")
+        r = np.linalg.norm(np.where(in64[:, None], x64[mis], x32[mis]).reshape(-1, 2, 3), axis=2)
+        n_far = int((r.min(axis=1) > 300.0).sum())
+    print(f"near-node sampled walkers {n_near}, alive mismatches {mis.size} "
+          f"({n_far} beyond 300 bohr), final dE {abs(e32[-1] - e64[-1]):.3e}, budget {budget:.3e}")
     assert mis.size <= 1e-4 * n, mis.size
     assert abs(e32[-1] - e64[-1]) <= budget, (abs(e32[-1] - e64[-1]), budget)
 
