@@ -668,7 +668,9 @@ def run_ours(args):
     if rank == 0:
         if extras:
             out["workloads"] = extras
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and ws == 1:
+            # the oracle on the host cores: a single-GPU figure, not repeated
+            # while the other ranks of a multi-GPU run wait
             out["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(out), flush=True)
     if ws > 1:
