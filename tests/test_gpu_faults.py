@@ -46,11 +46,13 @@ def test_injected_allocation_failure_reports_enomem(nth):
     assert "ok" in lines and lines[lines.index("ok") + 1] == "10", r.stdout
 
 
+@pytest.mark.parametrize("planted", [0.0, float("nan"), float("inf")])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_planted_nonfinite_walker_is_counted_not_trapped(gfk_lib, prec):
-    """A walker placed on the nucleus (r1 = 0: infinite drift) through a checkpoint blob
-    is killed and counted as non-finite; gfk_energy reports GFK_ENONFINITE with finite
-    outputs; the other walkers continue unchanged."""
+def test_planted_nonfinite_walker_is_counted_not_trapped(gfk_lib, prec, planted):
+    """A walker placed on the nucleus (r1 = 0: infinite drift), or given a NaN or an
+    infinite position, through a checkpoint blob is killed and counted as non-finite;
+    gfk_energy reports GFK_ENONFINITE with finite outputs; the other walkers continue
+    unchanged."""
     gfk = gfk_lib
     n = 256
     d = gfk.InstanceDesc(n_walkers=n, dt=0.01, e_trial=-2.9, seed=2, prec=prec)
@@ -60,9 +62,9 @@ def test_planted_nonfinite_walker_is_counted_not_trapped(gfk_lib, prec):
     n_slots = struct.unpack_from("<q", blob, 24)[0]
     if prec == 0:        # six double planes of n_slots: x1 of the victim to 0, y1, z1 too
         for dim in range(3):
-            struct.pack_into("<d", blob, HEADER + 8 * (dim * n_slots + victim), 0.0)
+            struct.pack_into("<d", blob, HEADER + 8 * (dim * n_slots + victim), planted)
     else:                # float4 plane p0 = (x1, y1, z1, x2)
-        struct.pack_into("<fff", blob, HEADER + 16 * victim, 0.0, 0.0, 0.0)
+        struct.pack_into("<fff", blob, HEADER + 16 * victim, planted, planted, planted)
     b = gfk.Context([d], trials=[(0, wl.ground())])
     b.restore(bytes(blob))
     b.propagate(8)
