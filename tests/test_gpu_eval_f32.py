@@ -62,3 +62,24 @@ def test_fp32_evaluation_rejects_bad_arguments(gfk_lib):
         gfk.gfk_eval_f32(0, wl.ground()[:2], X)
     with pytest.raises(gfk.GfkError):
         gfk.gfk_eval_f32(0, wl.ground(), X, lanes=3)
+
+
+def test_fp32_evaluation_far_from_the_nucleus(gfk_lib):
+    """The FP32 orbital-pair evaluation factors the largest exponential out of psi,
+    so hundreds of bohr out, where the unscaled psi of the FP64 path and of the
+    oracle underflows to exactly 0 (a node kill), the sign stays defined and the
+    drift and local energy finite: the mixed path keeps such a walker alive."""
+    gfk = gfk_lib
+    rng = np.random.default_rng(4)
+    u = rng.normal(0.0, 1.0, (64, 6))
+    u[:, :3] /= np.linalg.norm(u[:, :3], axis=1)[:, None]
+    u[:, 3:] /= np.linalg.norm(u[:, 3:], axis=1)[:, None]
+    X = u.copy()
+    X[:, :3] *= 400.0
+    X[:, 3:] *= 390.0
+    p = wl.triplet_2s3()
+    so = oracle.trial_eval_many(1, p, X)[0]
+    assert np.all(so == 0)
+    b, el, s = gfk.gfk_eval_f32(1, p, X.astype(np.float32))
+    assert np.all(s != 0)
+    assert np.all(np.isfinite(el)) and np.all(np.isfinite(b))

@@ -58,3 +58,26 @@ def test_node_distance_closed_forms():
         Y[:, 5] = -Y[:, 2] + delta
         d = oracle.node_distance(1, wl.fn7(1.1, 1.9, a=0.5, beta=0.6), Y)
         np.testing.assert_allclose(d, delta / math.sqrt(2.0), rtol=20 * delta)
+
+
+def test_unscaled_psi_underflows_far_from_the_nucleus():
+    """The oracle evaluates psi unscaled: for the 2^3S trial both terms'
+    exponentials e^{-(2 r1 + r2/2)} and e^{-(r1/2 + 2 r2)} underflow to 0 once both
+    exponents exceed ~745, so psi is exactly 0 there and the node rule kills a
+    walker that reaches it (the FP32 path, which factors the largest exponential
+    out of psi, keeps such a walker alive).  Below the underflow the sign is
+    defined and the local energy finite."""
+    rng = np.random.default_rng(4)
+    u = rng.normal(0.0, 1.0, (20, 6))
+    u[:, :3] /= np.linalg.norm(u[:, :3], axis=1)[:, None]
+    u[:, 3:] /= np.linalg.norm(u[:, 3:], axis=1)[:, None]
+    p = wl.triplet_2s3()
+    near, far = u.copy(), u.copy()
+    near[:, :3] *= 150.0
+    near[:, 3:] *= 140.0                 # exponents ~ 370 and ~ 355: representable
+    far[:, :3] *= 400.0
+    far[:, 3:] *= 390.0                  # exponents ~ 995 and ~ 980: both underflow
+    s, _, el, _ = oracle.trial_eval_many(1, p, near)
+    assert np.all(s != 0) and np.all(np.isfinite(el))
+    s, _, _, _ = oracle.trial_eval_many(1, p, far)
+    assert np.all(s == 0)
