@@ -222,3 +222,19 @@ def test_grad_at_the_gradient_workload_size(gfk_lib):
     np.testing.assert_array_equal(g0, g32)
     assert abs(l32 - l64) < 1e-6, (l32, l64)
     assert np.abs(g32 - g64).max() <= 1e-5 * np.abs(g64).max(), (g32, g64)
+
+
+def test_stored_trajectory_that_does_not_fit_reports_enomem(gfk_lib):
+    """ckpt_every = 0 asks for n_walkers x (n_steps + 1) x 24 bytes of trajectory; when
+    that cannot be allocated (here 2^12 walkers x 2^30 moves, 1e14 bytes) gfk_grad
+    returns GFK_ENOMEM before walking, and the context stays usable: the same call
+    with checkpoints then succeeds."""
+    gfk = gfk_lib
+    d = gfk.InstanceDesc(n_walkers=1 << 12, dt=0.005, e_trial=-2.9, seed=7,
+                         prec=gfk.GFK_PREC_MIXED)
+    with gfk.Context([d], trials=[(0, THETA)]) as c:
+        with pytest.raises(gfk.GfkError) as err:
+            gfk.gfk_grad(c.handle, 0, 0, 1 << 30, 0)
+        assert err.value.status == gfk.GFK_ENOMEM
+        loss, g = gfk.gfk_grad(c.handle, 0, 0, 64, 64)
+        assert np.isfinite(loss) and np.all(np.isfinite(g))
