@@ -64,13 +64,13 @@ SEED = 0
 # Keyed by (noise, trial case); the cases are the workloads' trial functions
 # per state (0: the 1^1S product, 1: the 2^3S pair, 2: the P_z pair).
 OP_COUNTS = {
-    (0, "ground"): {"flops": 168.0, "special": 18.0, "int": 90.5, "fp_add": 56.0,
+    (0, "ground"): {"flops": 168.0, "special": 18.0, "int": 68.0, "fp_add": 56.0,
                     "fp_mul": 87.0, "fp_div": 25.0, "fp_sqrt": 6.0, "fp_exp": 3.0,
                     "fp_log": 3.0, "fp_sin": 3.0, "fp_cos": 3.0},
-    (0, "triplet_2s3"): {"flops": 212.0, "special": 20.0, "int": 90.5, "fp_add": 67.0,
+    (0, "triplet_2s3"): {"flops": 212.0, "special": 20.0, "int": 68.0, "fp_add": 67.0,
                          "fp_mul": 112.0, "fp_div": 33.0, "fp_sqrt": 6.0, "fp_exp": 5.0,
                          "fp_log": 3.0, "fp_sin": 3.0, "fp_cos": 3.0},
-    (0, "pz"): {"flops": 224.0, "special": 20.0, "int": 90.5, "fp_add": 71.0, "fp_mul": 118.0,
+    (0, "pz"): {"flops": 224.0, "special": 20.0, "int": 68.0, "fp_add": 71.0, "fp_mul": 118.0,
                 "fp_div": 35.0, "fp_sqrt": 6.0, "fp_exp": 5.0, "fp_log": 3.0, "fp_sin": 3.0,
                 "fp_cos": 3.0},
     (1, "ground"): {"flops": 138.0, "special": 6.0, "int": 12.0, "fp_add": 50.0,

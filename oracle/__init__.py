@@ -12,8 +12,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                     run by its CPU interpreter) agrees bitwise.
   move_normals,
   init_normals      pinned: Kolmogorov-Smirnov and moment tests against N(0,1), no
-                    correlation between components or between the two moves of
-                    one Philox pair index.
+                    correlation between components or between consecutive
+                    moves; every angle on the 1024-point grid; the counter
+                    layout against philox4x32_10 (pinned above).
   trial_eval        pinned: closed-form eigenfunctions (E_L constant), 50-digit
                     finite differences of ln|psi|, exchange (anti)symmetry.
   run               pinned: exact weights for an exact eigenfunction, a
@@ -82,6 +83,8 @@ def _load():
         lib.orc_philox4x32_10.restype = None
         lib.orc_uniform.argtypes = [c.c_uint32]
         lib.orc_uniform.restype = c.c_double
+        lib.orc_angle_uniform.argtypes = [c.c_uint32]
+        lib.orc_angle_uniform.restype = c.c_double
         lib.orc_move_normals.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, dp]
         lib.orc_move_normals.restype = None
         lib.orc_init_normals.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, dp]
@@ -130,6 +133,11 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def uniform(word: int) -> float:
     return _load().orc_uniform(int(word))
+
+
+def angle_uniform(k: int) -> float:
+    """The Box-Muller angle uniform (k + 1/2) / 1024 of a 10-bit grid index."""
+    return _load().orc_angle_uniform(int(k))
 
 
 def move_normals(seed: int, walker: int, step: int, inst: int) -> np.ndarray:

@@ -34,13 +34,17 @@
  * SC'11) with Box-Muller normals.  Mode 1 (the paper's own scheme): Bernoulli
  * +-1 increments from the "Superduper" congruential generator, one generator
  * per walker (section "Bernoulli steps" below).  For mode 0 the counter is
- * (walker id, pair index, instance id, tag), the key the two halves of the
- * 64-bit seed.  Moves 2m and 2m+1 share the three blocks of pair index m,
- * tags 0, 1, 2 (12 words): move 2m takes words 0-5, move 2m+1 words 6-11.
- * The initial positions take the blocks of pair index 0 with tags 3 and 4
- * (words 0-5).  Words map to uniforms u = (w + 1/2) 2^-32 and consecutive
- * pairs of uniforms to normals by the Box-Muller transform (Box and Muller
- * 1958): xi = sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b).
+ * (walker id, move index, instance id, tag), the key the two halves of the
+ * 64-bit seed.  Move n (from global step n to n + 1) takes the one block
+ * (walker, n, instance, 0); the initial position the block (walker, 0,
+ * instance, 1).  A block's four words give six normals by the Box-Muller
+ * transform (Box and Muller 1958), xi = sqrt(-2 ln u_a) (cos 2 pi u_b,
+ * sin 2 pi u_b), three times: the radius uniforms u_a = (w_j + 1/2) 2^-32 from
+ * words 0, 1, 2, and the angle uniforms u_b = (k_j + 1/2) / 1024 on an equally
+ * spaced grid of 1024 angles, k_j = bits 10 j .. 10 j + 9 of word 3.  On such
+ * a grid the angular moments cos^p and sin^p average to their continuous
+ * values for every p below 1024, so the normals' moments that drive the walk
+ * are those of the continuous transform.
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused.
  */
@@ -88,52 +92,58 @@ double orc_uniform(uint32_t w)
     return ((double)w + 0.5) * (1.0 / 4294967296.0);
 }
 
-/* Box-Muller pair from two words: xi_a = rho cos(2 pi u_b), xi_b = rho sin(2 pi u_b). */
-static void orc_box_muller(uint32_t wa, uint32_t wb, double* xa, double* xb)
+/* Angle uniform from a 10-bit grid index: (k + 1/2) / 1024. */
+double orc_angle_uniform(uint32_t k)
+{
+    return ((double)k + 0.5) * (1.0 / 1024.0);
+}
+
+/* Box-Muller pair from a radius word and an angle index:
+ * xi_a = rho cos(2 pi u_b), xi_b = rho sin(2 pi u_b), rho = sqrt(-2 ln u_a). */
+static void orc_box_muller(uint32_t wa, uint32_t kb, double* xa, double* xb)
 {
     const double two_pi = 6.283185307179586476925286766559;
     double ua = orc_uniform(wa);
-    double ub = orc_uniform(wb);
+    double ub = orc_angle_uniform(kb);
     double rho = sqrt(-2.0 * log(ua));
     double ang = two_pi * ub;
     *xa = rho * cos(ang);
     *xb = rho * sin(ang);
 }
 
-/* Six standard normals from six words: Box-Muller on (w0,w1), (w2,w3), (w4,w5). */
-static void orc_normals_from_words(const uint32_t w[6], double xi[6])
+/* Six standard normals from the four words of one Philox block: Box-Muller on
+ * the radius words w0, w1, w2 with the angle indices of bits 0-9, 10-19 and
+ * 20-29 of w3. */
+static void orc_normals_from_block(const uint32_t w[4], double xi[6])
 {
-    orc_box_muller(w[0], w[1], &xi[0], &xi[1]);
-    orc_box_muller(w[2], w[3], &xi[2], &xi[3]);
-    orc_box_muller(w[4], w[5], &xi[4], &xi[5]);
+    for (int j = 0; j < 3; ++j)
+        orc_box_muller(w[j], (w[3] >> (10 * j)) & 1023u, &xi[2 * j], &xi[2 * j + 1]);
 }
 
-/* The 12 words of pair index m: Philox blocks with tags 0, 1, 2. */
-static void orc_pair_words(uint64_t seed, uint32_t walker, uint32_t m, uint32_t inst,
-                           uint32_t tag0, uint32_t words[12])
+/* The block (walker, n, inst, tag). */
+static void orc_block(uint64_t seed, uint32_t walker, uint32_t n, uint32_t inst, uint32_t tag,
+                      uint32_t words[4])
 {
     uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
-    for (uint32_t t = 0; t < 3; ++t) {
-        uint32_t ctr[4] = { walker, m, inst, tag0 + t };
-        orc_philox4x32_10(ctr, key, words + 4 * t);
-    }
+    uint32_t ctr[4] = { walker, n, inst, tag };
+    orc_philox4x32_10(ctr, key, words);
 }
 
 /* The six normals of move `step` (from global step `step` to step + 1). */
 void orc_move_normals(uint64_t seed, uint32_t walker, uint32_t step, uint32_t inst,
                       double xi[6])
 {
-    uint32_t words[12];
-    orc_pair_words(seed, walker, step >> 1, inst, 0u, words);
-    orc_normals_from_words(words + 6 * (step & 1u), xi);
+    uint32_t words[4];
+    orc_block(seed, walker, step, inst, 0u, words);
+    orc_normals_from_block(words, xi);
 }
 
-/* The six normals of the initial position: pair index 0, tags 3 and 4. */
+/* The six normals of the initial position: the block (walker, 0, inst, 1). */
 void orc_init_normals(uint64_t seed, uint32_t walker, uint32_t inst, double xi[6])
 {
-    uint32_t words[12];
-    orc_pair_words(seed, walker, 0u, inst, 3u, words);
-    orc_normals_from_words(words, xi);
+    uint32_t words[4];
+    orc_block(seed, walker, 0u, inst, 1u, words);
+    orc_normals_from_block(words, xi);
 }
 
 /* ------------------------------------------------------------------------ */

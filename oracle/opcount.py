@@ -22,9 +22,9 @@ How an operation is counted:
     the absent prefactor terms of an orbital, costs nothing).
   * Negation and absolute value are free (sign modifiers of the operation that
     consumes them).
-  * A step is counted as two consecutive moves of one walker (an even and an odd
-    move, which share the three Philox blocks of their pair index) divided by
-    two.  Each move evaluates the trial function once, at the new position; its
+  * A step is counted as two consecutive moves of one walker divided by two.
+    Each move draws one Philox block; the two blocks share the first-round
+    products of the walker and instance words.  Each move evaluates the trial function once, at the new position; its
     drift serves the next move (the oracle re-evaluates the drift at the old
     position, a convenience of its loop that the walk does not need).
   * The population sums are the four plain accumulations of w, w E_L, w^2 and
@@ -32,12 +32,12 @@ How an operation is counted:
     an accuracy device of the reduction and is not counted.
 
 Categories: fp_add (additions and subtractions), fp_mul, fp_div, fp_sqrt, fp_exp,
-fp_log, fp_sin, fp_cos, fp_pow, cmp (comparisons and finiteness tests), cvt
-(integer to floating-point conversions), int_mulwide (32 x 32 -> 64-bit products),
-int_xor, int_add, int_mul (32-bit products).  "flops" = fp_add + fp_mul + fp_div
-(a fused multiply-add is a multiply and an add, two flops); "special" = the
-transcendental and root operations (one special-function-unit operation each on
-a GPU); "int" = the integer operations.
+fp_log, fp_sin, fp_cos, fp_pow, cmp (comparisons and finiteness tests), cvt (integer to
+floating-point conversions), int_mulwide (32 x 32 -> 64-bit products), int_xor, int_add,
+int_mul (32-bit products), int_bit (bit-field extractions). "flops" = fp_add + fp_mul +
+fp_div (a fused multiply-add is a multiply and an add, two flops); "special" = the
+transcendental and root operations (one special-function-unit operation each on a GPU);
+"int" = the integer operations.
 
     python -m oracle.opcount            # prints the table as JSON
 """
@@ -257,6 +257,15 @@ def imul(a, b):
                                                       b.v if b.id is None else None)))
 
 
+def ifield(a, shift, bits):
+    """(a >> shift) & (2^bits - 1): one bit-field extraction."""
+    t = a.t
+    v = (a.v >> shift) & ((1 << bits) - 1)
+    if a.id is None:
+        return I(t, v)
+    return I(t, v, t.node("int_bit", (a.id,), (shift, bits)))
+
+
 def i2f(w):
     """Integer word to double (the uniform map's conversion)."""
     if w.id is None:
@@ -299,23 +308,26 @@ def uniform(w):
     return (i2f(w) + 0.5) * (1.0 / 4294967296.0)
 
 
-def box_muller(wa, wb):
+def angle_uniform(k):
+    """orc_angle_uniform: (k + 1/2) / 1024."""
+    return (i2f(k) + 0.5) * (1.0 / 1024.0)
+
+
+def box_muller(wa, kb):
     two_pi = 6.283185307179586476925286766559
-    ua, ub = uniform(wa), uniform(wb)
+    ua, ub = uniform(wa), angle_uniform(kb)
     rho = sqrt(-2.0 * log(ua))
     ang = two_pi * ub
     return rho * cos(ang), rho * sin(ang)
 
 
-def move_normals(t, key, walker, m_word, inst, odd):
-    """orc_move_normals: the three blocks of pair index m, words 0-5 or 6-11."""
-    words = []
-    for tag in range(3):
-        words += philox4x32_10([walker, m_word, inst, I(t, tag)], key)
-    w = words[6:12] if odd else words[0:6]
+def move_normals(t, key, walker, n_word, inst):
+    """orc_move_normals: the one block (walker, n, inst, 0); radius words 0-2, the
+    10-bit angle fields of word 3."""
+    w = philox4x32_10([walker, n_word, inst, I(t, 0)], key)
     xi = []
     for j in range(3):
-        xi += list(box_muller(w[2 * j], w[2 * j + 1]))
+        xi += list(box_muller(w[j], ifield(w[3], 10 * j, 10)))
     return xi
 
 
@@ -433,7 +445,7 @@ def count_step(kind, params, noise=0, ee_on=True, x0=None, seed=7, walker=12345,
     key = [i_input(t, seed & M32, "k0"), i_input(t, seed >> 32, "k1")]
     wid = i_input(t, walker, "walker")
     ist = i_input(t, inst, "inst")
-    m_word = i_input(t, 0, "m")
+    n_word = i_input(t, 0, "n")
     lcg = i_input(t, lcg0, "lcg")
     sqrt_dt = math.sqrt(dt)
     outs = []
@@ -441,7 +453,8 @@ def count_step(kind, params, noise=0, ee_on=True, x0=None, seed=7, walker=12345,
     sgn = s0
     for odd in (0, 1):
         if noise == 0:
-            xi = move_normals(t, key, wid, m_word, ist, odd)
+            # moves n and n + 1 (the step counter advanced by one)
+            xi = move_normals(t, key, wid, iadd(n_word, 1) if odd else n_word, ist)
         else:
             lcg, xi = superduper_step(lcg)
         x = [x[d] + b[d] * dt + sqrt_dt * xi[d] for d in range(6)]
@@ -464,12 +477,14 @@ def count_step(kind, params, noise=0, ee_on=True, x0=None, seed=7, walker=12345,
     c["fp_add"] = c.get("fp_add", 0) + 4 * 2
     half = {k: v / 2.0 for k, v in c.items()}
     for k in ("fp_add", "fp_mul", "fp_div", "fp_sqrt", "fp_exp", "fp_log", "fp_sin", "fp_cos",
-              "fp_pow", "cmp", "cvt", "int_mulwide", "int_xor", "int_add", "int_mul"):
+              "fp_pow", "cmp", "cvt", "int_mulwide", "int_xor", "int_add", "int_mul",
+              "int_bit"):
         half.setdefault(k, 0.0)
     half["flops"] = half["fp_add"] + half["fp_mul"] + half["fp_div"]
     half["special"] = sum(half[k] for k in ("fp_sqrt", "fp_exp", "fp_log", "fp_sin", "fp_cos",
                                             "fp_pow"))
-    half["int"] = half["int_mulwide"] + half["int_xor"] + half["int_add"] + half["int_mul"]
+    half["int"] = (half["int_mulwide"] + half["int_xor"] + half["int_add"] + half["int_mul"] +
+                   half["int_bit"])
     if return_values:
         return half, values
     return half

@@ -87,10 +87,17 @@ def test_uniform_map_endpoints():
     assert oracle.uniform(2**31) == 0.5 + 2.0 ** -33
 
 
+def test_angle_uniform_grid():
+    # (k + 1/2) / 1024 for a 10-bit index: the midpoints of 1024 equal cells
+    assert oracle.angle_uniform(0) == 0.5 / 1024
+    assert oracle.angle_uniform(1023) == 1.0 - 0.5 / 1024
+    assert oracle.angle_uniform(512) == 0.5 + 0.5 / 1024
+
+
 def test_normals_are_standard_normal():
     """Box-Muller output: Kolmogorov-Smirnov against N(0,1) per component, unit
-    variance, no correlation between the six components of a move, between the
-    two moves of one Philox pair index, or in the initial positions."""
+    variance, no correlation between the six components of a move, between
+    consecutive moves, or in the initial positions."""
     stats = pytest.importorskip("scipy.stats")
     even = np.array([oracle.move_normals(99, i, 6, 1) for i in range(20000)])
     odd = np.array([oracle.move_normals(99, i, 7, 1) for i in range(20000)])
@@ -110,6 +117,32 @@ def test_normals_are_standard_normal():
                   oracle.move_normals(1, 5, 0, 0), oracle.move_normals(1 << 32, 5, 0, 0),
                   oracle.init_normals(0, 5, 0)):
         assert not np.allclose(a, other)
+
+
+def test_normals_layout_and_angle_grid():
+    """Move n of a walker is the one Philox block (walker, n, instance, 0) and the
+    initial position the block (walker, 0, instance, 1): the radii of its three
+    Box-Muller pairs come from words 0, 1, 2 (rho^2 = -2 ln u, u = (w + 1/2) 2^-32)
+    and every pair's angle lies on the 1024-point grid 2 pi (k + 1/2) / 1024, with
+    k the 10-bit fields of word 3 in order.  The angular moments of such a grid are
+    the continuous ones: the mean of cos^2 over it is 1/2 and of cos^4 3/8."""
+    for seed, walker, step, inst in ((99, 7, 6, 1), (3, 1 << 20, 12345, 0), (1 << 40, 0, 0, 9)):
+        for tag, xi in ((0, oracle.move_normals(seed, walker, step, inst)),
+                        (1, oracle.init_normals(seed, walker, inst))):
+            n = step if tag == 0 else 0
+            w = oracle.philox4x32_10([walker, n, inst, tag],
+                                     [seed & 0xffffffff, seed >> 32]).astype(np.uint64)
+            for j in range(3):
+                a, b = xi[2 * j], xi[2 * j + 1]
+                u = (float(w[j]) + 0.5) * 2.0 ** -32
+                assert abs((a * a + b * b) - (-2.0 * math.log(u))) <= 1e-12 * max(1.0, a * a + b * b)
+                k = (int(w[3]) >> (10 * j)) & 1023
+                ang = math.atan2(b, a) % (2 * math.pi)
+                want = 2 * math.pi * (k + 0.5) / 1024
+                assert abs(math.remainder(ang - want, 2 * math.pi)) <= 1e-12
+    grid = 2 * np.pi * (np.arange(1024) + 0.5) / 1024
+    assert abs(np.mean(np.cos(grid) ** 2) - 0.5) < 1e-15
+    assert abs(np.mean(np.cos(grid) ** 4) - 0.375) < 1e-15
 
 
 # --------------------------------------------------------------------------
