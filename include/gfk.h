@@ -98,11 +98,13 @@ typedef enum { GFK_TRIAL_JASTROW_PRODUCT = 0, GFK_TRIAL_ORBITAL_PAIRS = 1 } gfk_
 /* One independent walk (an "instance"): the paper's statement of the problem
  * -- a symmetry, the trial energy E_T (the paper's lambda_0 of the trial
  * function), the time step dt, the number of replications N_rep and a seed.
- * Random numbers are Philox4x32-10 with counter (walker id, m, rng_stream,
- * tag) and key (seed low, seed high): moves 2m and 2m+1 take words 0-5 and
- * 6-11 of the blocks with tags 0, 1, 2 (Gaussian noise; see gfk_noise for the
- * Bernoulli mode); the walker id is walker_id0 + the walker's index.  The same (seed, rng_stream, walker id) gives the same
- * trajectory in any context and any launch configuration. */
+ * Random numbers are Philox4x32-10 with counter (walker id, n, rng_stream,
+ * tag) and key (seed low, seed high): move n takes the block with tag 0 (its
+ * words 0-2 the Box-Muller radii, its word 3 three 10-bit angle indices on a
+ * 1024-point grid), the initial position the block of n = 0 with tag 1
+ * (Gaussian noise; see gfk_noise for the Bernoulli mode); the walker id is
+ * walker_id0 + the walker's index.  The same (seed, rng_stream, walker id)
+ * gives the same trajectory in any context and any launch configuration. */
 typedef struct {
     int32_t  state;          /* gfk_state                                         */
     int32_t  prec;           /* gfk_prec; all instances of a context share it     */

@@ -162,7 +162,7 @@ __device__ __forceinline__ void adj_steps(const InstDev* inst, float& dt, float&
 
 // Recomputes the positions of moves n_lo + 1 .. n_hi of walker i from its
 // position x at move n_lo and stores them (with x itself) in the segment
-// planes: the forward walk's noise (the same paired Philox words, or the
+// planes: the forward walk's noise (the same Philox block of each move, or the
 // walker's Superduper generator skipped ahead to move n_lo) and arithmetic.
 // NOISE and POLY are fixed for the whole segment, so the loop has no branch.
 template <int NOISE, int POLY, typename T>
@@ -173,7 +173,6 @@ __device__ __forceinline__ void adj_recompute(const TrialDev<T>& tp, const InstD
     const uint32_t id = inst->id0 + (uint32_t)i;
     uint32_t lcg = 0u;
     PhiloxPre pre[1];
-    uint32_t carry[1][2] = {{0u, 0u}};
     if (NOISE == 1) lcg = superduper_at(id, inst->stream, inst->k0, inst->k1, (uint32_t)n_lo);
     else pre[0] = philox_pre(id, inst->stream, inst->k0, inst->k1);
     for (int m = n_lo; m < n_hi; ++m) {
@@ -182,7 +181,7 @@ __device__ __forceinline__ void adj_recompute(const TrialDev<T>& tp, const InstD
             adj_bernoulli(lcg, sdt, inst, xi, xlo);
         } else {
             uint32_t words[1][6];
-            pair_move_words_all<1>(pre, carry, (uint32_t)m, m == n_lo, inst->k0, inst->k1, words);
+            move_words_all<1>(pre, (uint32_t)m, inst->k0, inst->k1, words);
             adj_normals(words[0], xi, inst);
         }
         EvalOut<T> ev;

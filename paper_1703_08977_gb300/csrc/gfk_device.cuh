@@ -41,42 +41,44 @@ __device__ __forceinline__ Words4 philox10(uint32_t c0, uint32_t c1, uint32_t c2
     return o;
 }
 
-// Counter layout: moves 2m and 2m+1 of a walker share the three Philox blocks
-// (walker, m, stream, tag 0 / 1 / 2); move 2m takes words 0-5 of the twelve
-// (tag 0 words 0-3, tag 1 words 0-1), move 2m+1 words 6-11 (tag 1 words 2-3,
-// tag 2 words 0-3).  The initial position takes words 0-5 of the blocks
-// (walker, 0, stream, tag 3 / 4).
+// Counter layout: move n of a walker (from global step n to n + 1) takes the
+// one block (walker, n, stream, 0), the initial position the block
+// (walker, 0, stream, 1).  A block's four words give the six words the
+// Box-Muller transforms read, as (radius word, angle index) pairs: the radius
+// words are the block's words 0, 1, 2 and the angle indices the three 10-bit
+// fields (bits 0-9, 10-19, 20-29) of its word 3.
+__device__ __forceinline__ void block_words(const Words4& b, uint32_t w[6]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        w[2 * j] = b.w[j];
+        w[2 * j + 1] = (b.w[3] >> (10 * j)) & 1023u;
+    }
+}
 __device__ __forceinline__ void move_words(uint32_t walker, uint32_t step, uint32_t stream,
                                            uint32_t k0, uint32_t k1, uint32_t w[6]) {
-    const uint32_t m = step >> 1;
-    if ((step & 1u) == 0u) {
-        Words4 a = philox10(walker, m, stream, 0u, k0, k1);
-        Words4 b = philox10(walker, m, stream, 1u, k0, k1);
-        w[0] = a.w[0]; w[1] = a.w[1]; w[2] = a.w[2]; w[3] = a.w[3]; w[4] = b.w[0]; w[5] = b.w[1];
-    } else {
-        Words4 b = philox10(walker, m, stream, 1u, k0, k1);
-        Words4 c = philox10(walker, m, stream, 2u, k0, k1);
-        w[0] = b.w[2]; w[1] = b.w[3]; w[2] = c.w[0]; w[3] = c.w[1]; w[4] = c.w[2]; w[5] = c.w[3];
-    }
+    block_words(philox10(walker, step, stream, 0u, k0, k1), w);
 }
 
 __device__ __forceinline__ void init_words(uint32_t walker, uint32_t stream, uint32_t k0,
                                            uint32_t k1, uint32_t w[6]) {
-    Words4 a = philox10(walker, 0u, stream, 3u, k0, k1);
-    Words4 b = philox10(walker, 0u, stream, 4u, k0, k1);
-    w[0] = a.w[0]; w[1] = a.w[1]; w[2] = a.w[2]; w[3] = a.w[3]; w[4] = b.w[0]; w[5] = b.w[1];
+    block_words(philox10(walker, 0u, stream, 1u, k0, k1), w);
 }
 
-// Six N(0,1) variates from six words: Box-Muller on (w0,w1), (w2,w3), (w4,w5),
-// xi_a = sqrt(-2 ln u_a) cos(2 pi u_b), xi_b = sqrt(-2 ln u_a) sin(2 pi u_b).
-// FP64: u = (w + 1/2) 2^-32 and library log/sqrt/sin/cos.
+// Six N(0,1) variates from the six words of block_words: Box-Muller on
+// (w0, k0), (w2, k1), (w4, k2), xi_a = sqrt(-2 ln u_a) cos(2 pi u_b),
+// xi_b = sqrt(-2 ln u_a) sin(2 pi u_b), with the radius uniform u_a from the
+// radius word and the angle uniform u_b = (k + 1/2) / 1024 on an equally
+// spaced grid of 1024 angles (on such a grid cos^p and sin^p average to their
+// continuous values for every p below 1024).
+// FP64: u_a = (w + 1/2) 2^-32 and library log/sqrt/sin/cos.
 __device__ __forceinline__ void normals6_f64(const uint32_t w[6], double xi[6]) {
     constexpr double kTwoPi = 6.283185307179586476925286766559;
     constexpr double kInv32 = 1.0 / 4294967296.0;
+    constexpr double kInv10 = 1.0 / 1024.0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         double ua = ((double)w[2 * j] + 0.5) * kInv32;
-        double ub = ((double)w[2 * j + 1] + 0.5) * kInv32;
+        double ub = ((double)w[2 * j + 1] + 0.5) * kInv10;
         double rho = sqrt(-2.0 * log(ua));
         double ang = kTwoPi * ub;
         xi[2 * j] = rho * cos(ang);
@@ -85,11 +87,10 @@ __device__ __forceinline__ void normals6_f64(const uint32_t w[6], double xi[6]) 
 }
 
 // The Philox blocks of one walker share walker id and stream, so their first
-// round differs only in the pair index and the tag, and the blocks of tags 0
-// and 1 also share one product of their second round.  PhiloxPre holds the
-// first-round products that depend only on the walker id and the stream (with
-// the key words folded in).  philox10_pair gives the blocks of tags 0 and 1,
-// philox10_tag one block; both equal philox10 word for word.
+// round depends only on the move index and the tag: PhiloxPre holds the
+// first-round products of the walker id and the stream (with the key words
+// folded in), formed once per launch, and philox10_tag runs the other nine
+// rounds; it equals philox10 word for word.
 struct PhiloxPre {
     uint32_t hiB_k0;    // umulhi(M_B, stream) ^ k0
     uint32_t loB;       // M_B * stream
@@ -127,105 +128,14 @@ __device__ __forceinline__ Words4 philox10_tag(const PhiloxPre& p, uint32_t m, u
     return o;
 }
 
-__device__ __forceinline__ void philox10_pair(const PhiloxPre& p, uint32_t m, uint32_t k0,
-                                              uint32_t k1, Words4& a, Words4& b) {
-    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
-    constexpr uint32_t kBumpA = 0x9E3779B9u, kBumpB = 0xBB67AE85u;
-    // round 1 (key k0, k1): counters (walker, m, stream, tag)
-    const uint32_t r1c0 = p.hiB_k0 ^ m;          // shared
-    const uint32_t r1c1 = p.loB;                 // shared
-    uint32_t a2 = p.hiA_k1;                      // tag 0
-    uint32_t b2 = p.hiA_k1 ^ 1u;                 // tag 1
-    const uint32_t r1c3 = p.loA;                 // shared
-    // round 2 (key + 1 bump)
-    k0 += kBumpA; k1 += kBumpB;
-    const uint32_t hiA = __umulhi(kMulA, r1c0), loA = kMulA * r1c0;     // shared
-    const uint32_t n2 = hiA ^ r1c3 ^ k1;                                  // shared
-    uint32_t ac0, ac1, ac2 = n2, ac3 = loA;
-    uint32_t bc0, bc1, bc2 = n2, bc3 = loA;
-    {
-        uint32_t hiB = __umulhi(kMulB, a2), loB = kMulB * a2;
-        ac0 = hiB ^ r1c1 ^ k0;
-        ac1 = loB;
-        hiB = __umulhi(kMulB, b2);
-        loB = kMulB * b2;
-        bc0 = hiB ^ r1c1 ^ k0;
-        bc1 = loB;
-    }
-#pragma unroll
-    for (int r = 2; r < 10; ++r) {
-        k0 += kBumpA; k1 += kBumpB;
-        uint32_t hA = __umulhi(kMulA, ac0), lA = kMulA * ac0;
-        uint32_t hB = __umulhi(kMulB, ac2), lB = kMulB * ac2;
-        uint32_t n0a = hB ^ ac1 ^ k0, n2a = hA ^ ac3 ^ k1;
-        ac0 = n0a; ac1 = lB; ac2 = n2a; ac3 = lA;
-        hA = __umulhi(kMulA, bc0); lA = kMulA * bc0;
-        hB = __umulhi(kMulB, bc2); lB = kMulB * bc2;
-        uint32_t n0b = hB ^ bc1 ^ k0, n2b = hA ^ bc3 ^ k1;
-        bc0 = n0b; bc1 = lB; bc2 = n2b; bc3 = lA;
-    }
-    a.w[0] = ac0; a.w[1] = ac1; a.w[2] = ac2; a.w[3] = ac3;
-    b.w[0] = bc0; b.w[1] = bc1; b.w[2] = bc2; b.w[3] = bc3;
-}
-
-// The Philox words of one move for all WPT walkers of a thread.  The even
-// move of a pair runs the blocks of tags 0 and 1 and keeps tag 1's last two
-// words (carry) for the odd move, which runs tag 2 (and tag 1 again when the
-// launch starts on an odd move).  The even / odd branch is taken once for all
-// walkers, so the walkers' moves that follow are one branch-free stretch the
-// compiler can interleave.
+// The words of move `step` for all WPT walkers of a thread (block_words of
+// the block (walker, step, stream, 0)).
 template <int WPT>
-__device__ __forceinline__ void pair_move_words_all(const PhiloxPre (&pre)[WPT],
-                                                    uint32_t (&carry)[WPT][2], uint32_t step,
-                                                    bool first, uint32_t k0, uint32_t k1,
-                                                    uint32_t (&words)[WPT][6]) {
-    const uint32_t m = step >> 1;
-    if ((step & 1u) == 0u) {
+__device__ __forceinline__ void move_words_all(const PhiloxPre (&pre)[WPT], uint32_t step,
+                                               uint32_t k0, uint32_t k1,
+                                               uint32_t (&words)[WPT][6]) {
 #pragma unroll
-        for (int k = 0; k < WPT; ++k) {
-            Words4 wa, wb;
-            philox10_pair(pre[k], m, k0, k1, wa, wb);
-            words[k][0] = wa.w[0]; words[k][1] = wa.w[1]; words[k][2] = wa.w[2];
-            words[k][3] = wa.w[3]; words[k][4] = wb.w[0]; words[k][5] = wb.w[1];
-            carry[k][0] = wb.w[2];
-            carry[k][1] = wb.w[3];
-        }
-    } else {
-        if (first) {
-#pragma unroll
-            for (int k = 0; k < WPT; ++k) {
-                const Words4 wb = philox10_tag(pre[k], m, 1u, k0, k1);
-                carry[k][0] = wb.w[2];
-                carry[k][1] = wb.w[3];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < WPT; ++k) {
-            const Words4 wc = philox10_tag(pre[k], m, 2u, k0, k1);
-            words[k][0] = carry[k][0]; words[k][1] = carry[k][1];
-            words[k][2] = wc.w[0]; words[k][3] = wc.w[1]; words[k][4] = wc.w[2];
-            words[k][5] = wc.w[3];
-        }
-    }
-}
-
-// The words of both moves 2m and 2m+1 for all WPT walkers of a thread: the
-// three blocks of pair index m (tags 0, 1, 2), without a branch (the walk's
-// two-move iterations).
-template <int WPT>
-__device__ __forceinline__ void pair_words_both(const PhiloxPre (&pre)[WPT], uint32_t m,
-                                                uint32_t k0, uint32_t k1,
-                                                uint32_t (&wa)[WPT][6], uint32_t (&wb)[WPT][6]) {
-#pragma unroll
-    for (int k = 0; k < WPT; ++k) {
-        Words4 t0, t1;
-        philox10_pair(pre[k], m, k0, k1, t0, t1);
-        const Words4 t2 = philox10_tag(pre[k], m, 2u, k0, k1);
-        wa[k][0] = t0.w[0]; wa[k][1] = t0.w[1]; wa[k][2] = t0.w[2];
-        wa[k][3] = t0.w[3]; wa[k][4] = t1.w[0]; wa[k][5] = t1.w[1];
-        wb[k][0] = t1.w[2]; wb[k][1] = t1.w[3]; wb[k][2] = t2.w[0];
-        wb[k][3] = t2.w[1]; wb[k][4] = t2.w[2]; wb[k][5] = t2.w[3];
-    }
+    for (int k = 0; k < WPT; ++k) block_words(philox10_tag(pre[k], step, 0u, k0, k1), words[k]);
 }
 
 // FP32: the same words.  The radius uniform keeps the full 32-bit resolution,
@@ -236,10 +146,10 @@ __device__ __forceinline__ void pair_words_both(const PhiloxPre (&pre)[WPT], uin
 // singularity), so the normals' variance -- the diffusion constant -- would be
 // low by that fraction and E(t) high by about that fraction of the kinetic
 // energy.  u_a is at least 2^-33 > 0; values that round to 1 give radius 0
-// (the square root of 0 is 0).  The angle uniform uses 23 bits,
-// u_b - 1/2 = ((1 + k 2^-23) - 3/2) + 2^-24 with k = w >> 9, built exactly
-// from the bit pattern 0x3F800000 | k (= 1 + k 2^-23); an equally spaced grid
-// of angles keeps cos^2 and sin^2 at mean 1/2 exactly.  The radius takes the
+// (the square root of 0 is 0).  The angle uniform is the grid point
+// u_b - 1/2 = ((1 + k 2^-10) - 3/2) + 2^-11 of the 10-bit index k, built
+// exactly from the bit pattern 0x3F800000 | (k << 13) (= 1 + k 2^-10); on the
+// equally spaced grid cos^2 and sin^2 average to 1/2 exactly.  The radius takes the
 // hardware log2 with its mean error over the 2^32 words removed (radius2_f32
 // below).  Then the hardware square root, sine and cosine; the angle is taken as
 // 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine are most
@@ -281,23 +191,25 @@ __device__ __forceinline__ float radius_f32(float r2) {
     return rho;
 }
 
-// The angle 2 pi (u_b - 1/2) from its word's 23-bit grid value 1 + k 2^-23
-// (the bit pattern 0x3F800000 | (w >> 9)); then the hardware sine and cosine.
-__device__ __forceinline__ float angle_grid(uint32_t w) {
-    return __int_as_float(0x3F800000 | (w >> 9));
+// The angle 2 pi (u_b - 1/2) from the grid value 1 + k 2^-10 of its 10-bit
+// index k (the bit pattern 0x3F800000 | (k << 13)); then the hardware sine and
+// cosine.
+__device__ __forceinline__ float angle_grid(uint32_t k) {
+    return __int_as_float(0x3F800000 | (k << 13));
 }
 template <typename L>
 __device__ __forceinline__ L angle_lanes(L grid) {
-    constexpr float kHalfUlp = 1.0f / 16777216.0f;                        // 2^-24
+    constexpr float kHalfCell = 1.0f / 2048.0f;                           // 2^-11
     constexpr float kTwoPi = 6.2831853071795865f;
-    return lmul(splat<L>(kTwoPi), ladd(lsub(grid, splat<L>(1.5f)), splat<L>(kHalfUlp)));
+    return lmul(splat<L>(kTwoPi), ladd(lsub(grid, splat<L>(1.5f)), splat<L>(kHalfCell)));
 }
-__device__ __forceinline__ void angle_f32(uint32_t w, float& s, float& c) {
-    __sincosf(angle_lanes<float>(angle_grid(w)), &s, &c);
+__device__ __forceinline__ void angle_f32(uint32_t k, float& s, float& c) {
+    __sincosf(angle_lanes<float>(angle_grid(k)), &s, &c);
 }
 
-// Six N(0,1) variates per walker from its six words (Box-Muller on (w0,w1),
-// (w2,w3), (w4,w5)) for the walkers of a lane group (w[k]: lane k's words).
+// Six N(0,1) variates per walker from its six words (block_words: Box-Muller
+// on (w0,k0), (w2,k1), (w4,k2)) for the walkers of a lane group (w[k]: lane
+// k's words).
 template <typename L>
 __device__ __forceinline__ void normals6_lanes(const uint32_t (*w)[6], L xi[6], float r2_fix) {
     constexpr int W = LaneCount<L>::value;

@@ -6,7 +6,7 @@
 // One thread advances one walker for a whole chunk of steps with its state in
 // registers.  Per step (the discretised Eq. 4 with the drifted diffusion under
 // it):
-//   xi       <- six N(0,1) from Philox4x32-10 words (three blocks per two moves),
+//   xi       <- six N(0,1) from one Philox4x32-10 block (radii and angles),
 //               or (NOISE = 1) six signs +-1 from the walker's Superduper generator
 //   X        <- X + b(X) dt + sqrt(dt) xi                       (Euler-Maruyama)
 //   b, E_L   <- trial function at the new X

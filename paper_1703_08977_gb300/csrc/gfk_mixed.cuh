@@ -5,8 +5,7 @@
 // range, so every load and store is coalesced) for a whole chunk of steps with
 // the state in registers.  Per step and walker (the discretised Eq. 4 and the
 // drifted diffusion under it):
-//   xi     <- six N(0,1): Philox4x32-10 words (three blocks serve two moves),
-//             FP32 Box-Muller; or (NOISE = 1) six signs +-1 from the walker's
+//   xi     <- six N(0,1): one Philox4x32-10 block per move, FP32 Box-Muller; or (NOISE = 1) six signs +-1 from the walker's
 //             Superduper generator, skipped ahead to the launch's first move
 //   X      <- X + (b dt + sqrt(dt) xi)   (FP32, the increment formed first;
 //             Bernoulli: X + ((b dt +- s_lo) +- s), gfk_device.cuh)
@@ -231,7 +230,6 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     float* const s_stage = s_dyn + 2 * kRing * 5 * nwarps + warp * 16 * kStageStride;
 
     PhiloxPre pre[WPT];
-    uint32_t carry[WPT][2];      // tag-1 words 2-3 of the even move, used by the odd one
     uint32_t lcg[WPT];           // Bernoulli mode: generator state before this move
     int64_t slot[WPT];
     bool valid[WPT];
@@ -249,7 +247,6 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         } else {
             lcg[k] = superduper_at(I.id0 + (uint32_t)id, I.stream, k0, k1, step0);
         }
-        carry[k][0] = carry[k][1] = 0u;
         slot[k] = I.off + id;
         sg[k] = 0;
         Lw[k] = -INFINITY;
@@ -514,16 +511,16 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     };
 
     int s = 0;
-    if (NOISE == 0 && (step0 & 1u) == 0u) {
-        // Gaussian noise from an even move: two moves per iteration.  The three
-        // Philox blocks of the pair index serve both moves (words 0-5 and 6-11),
-        // so they are drawn without a branch, and the second move's words and
-        // normals are independent of the first move's arithmetic, which the
-        // scheduler can interleave with them.  After the first move of a pair
-        // (an even s) there is no column sum, fold or end of launch.
+    if (NOISE == 0) {
+        // Gaussian noise: two moves per iteration.  Each move's Philox block is
+        // drawn without a branch, and the second move's words and normals are
+        // independent of the first move's arithmetic, which the scheduler can
+        // interleave with them.  s is even after the first move of a pair, so
+        // there is no column sum, fold or end of launch between the two.
         for (; s + 1 < nsteps; s += 2) {
             uint32_t wa[WPT][6], wb[WPT][6];
-            pair_words_both<WPT>(pre, (step0 + (uint32_t)s) >> 1, k0, k1, wa, wb);
+            move_words_all<WPT>(pre, step0 + (uint32_t)s, k0, k1, wa);
+            move_words_all<WPT>(pre, step0 + (uint32_t)s + 1u, k0, k1, wb);
             L xa[NG][6], xb[NG][6], xlo[NG][6];
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
@@ -537,12 +534,12 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     }
     for (; s < nsteps; ++s) {
         const uint32_t step = step0 + (uint32_t)s;
-        // Gaussian noise: the normals of all walkers first (the Philox words
-        // under one even / odd branch); the Bernoulli steps are drawn per group.
+        // Gaussian noise: the normals of all walkers first; the Bernoulli steps
+        // are drawn per group.
         L xi[NG][6], xlo[NG][6];
         if (NOISE == 0) {
             uint32_t words[WPT][6];
-            pair_move_words_all<WPT>(pre, carry, step, s == 0, k0, k1, words);
+            move_words_all<WPT>(pre, step, k0, k1, words);
 #pragma unroll
             for (int g = 0; g < NG; ++g) normals6_lanes<L>(&words[g * LW], xi[g], r2_fix);
         }

@@ -190,9 +190,9 @@ __global__ void normal_moments_kernel(int method, float r2_fix, double* __restri
         e_rho2 += rho * rho - exact;
     }
     double c2 = 0.0, s2 = 0.0, c1 = 0.0, s1 = 0.0;
-    for (uint64_t k = first; k < (1ull << 23); k += stride) {
+    for (uint64_t k = first; k < 1024u; k += stride) {
         float s, c;
-        gfk::angle_f32((uint32_t)k << 9, s, c);
+        gfk::angle_f32((uint32_t)k, s, c);
         c2 += (double)c * (double)c - 0.5;
         s2 += (double)s * (double)s - 0.5;
         c1 += (double)c;
@@ -232,7 +232,7 @@ extern "C" gfk_status gfk_normal_moments(int32_t method, void* cuda_stream, doub
         (void)cudaGetLastError();
         return GFK_ECUDA;
     }
-    const double n_radius = 4294967296.0, n_angle = 8388608.0;
+    const double n_radius = 4294967296.0, n_angle = 1024.0;
     moments[0] = h[0] / n_radius;
     moments[1] = h[1] / n_radius;
     for (int q = 2; q < kNumMoments; ++q) moments[q] = h[q] / n_angle;
