@@ -367,7 +367,7 @@ gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* lane_ops_per_
  * r2(w) the squared radius and rho = sqrt(r2) as the kernels compute them and
  * R2(w) = -2 ln((w + 1/2) 2^-32) in FP64:
  *   moments[0] = mean of r2 - R2,   moments[1] = mean of rho^2 - R2;
- * over all 2^23 angles of the grid, with c, s the kernels' cosine and sine:
+ * over the 1024 angles of the grid, with c, s the kernels' cosine and sine:
  *   moments[2] = mean c^2 - 1/2,    moments[3] = mean s^2 - 1/2,
  *   moments[4] = mean c,            moments[5] = mean s.
  * The normals' variances are (2 + moments[1]) (1/2 + moments[2]) and

@@ -144,7 +144,7 @@ extern "C" gfk_status gfk_measure_peak(int32_t op, void* cuda_stream, double* la
 
 // ---------------------------------------------------------------------------
 // gfk_normal_moments: the FP32 Box-Muller generator against FP64, summed over
-// every radius word (2^32) and every angle of the 23-bit grid.  One FP64
+// every radius word (2^32) and every angle of the 1024-point grid.  One FP64
 // partial per thread and quantity, one atomic add per block and quantity.
 // ---------------------------------------------------------------------------
 namespace {

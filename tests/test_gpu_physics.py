@@ -39,7 +39,7 @@ def test_triplet_energy_extrapolates_to_exact(gfk_lib):
 
 
 def test_fp32_box_muller_normals_have_unit_variance(gfk_lib):
-    """Exhaustive over the 2^32 radius words and the 2^23 angles: the mixed path's FP32
+    """Exhaustive over the 2^32 radius words and the 1024 grid angles: the mixed path's FP32
     normals xi_a = -rho cos, xi_b = -rho sin have variance (2 + E[rho^2 - R2]) (1/2 +
     E[cos^2 - 1/2]) = 1 to 5e-9 (the diffusion constant of the walk), with the radius
     constant the kernels use for an FP32 time step that needs no correction.  Beside
