@@ -100,15 +100,16 @@ LANES_PER_SM_CLK = 128
 # instructions per walker-step, the issue-active fraction and the busiest pipe (the
 # FMA-heavy pipe, which also runs the integer multiplies of the Philox rounds).
 WALK_PROFILE = {       # (state, noise) -> capture of that walk kernel
-    (0, 0): {"src_sha": "2ab73dc43b42b6b9", "bytes_per_walker_step": 0.19981,
-             "inst_per_walker_step": 243.8, "issue_active": 0.691, "fmaheavy_active": 0.759},
-    (0, 1): {"src_sha": "2ab73dc43b42b6b9", "bytes_per_walker_step": 0.19952,
+    (0, 0): {"src_sha": "a201b2c1efc7a8e1", "bytes_per_walker_step": 0.20044,
+             "inst_per_walker_step": 222.0, "issue_active": 0.712, "fmaheavy_active": 0.702},
+    (0, 1): {"src_sha": "a201b2c1efc7a8e1", "bytes_per_walker_step": 0.20000,
              "inst_per_walker_step": 155.2, "issue_active": 0.742, "fmaheavy_active": 0.694},
-    (1, 0): {"src_sha": "2ab73dc43b42b6b9", "bytes_per_walker_step": 0.20240,
-             "inst_per_walker_step": 279.1, "issue_active": 0.694, "fmaheavy_active": 0.716},
-    (2, 0): {"src_sha": "2ab73dc43b42b6b9", "bytes_per_walker_step": 0.20737,
-             "inst_per_walker_step": 314.9, "issue_active": 0.691, "fmaheavy_active": 0.718},
+    (1, 0): {"src_sha": "a201b2c1efc7a8e1", "bytes_per_walker_step": 0.19982,
+             "inst_per_walker_step": 260.7, "issue_active": 0.718, "fmaheavy_active": 0.680},
+    (2, 0): {"src_sha": "a201b2c1efc7a8e1", "bytes_per_walker_step": 0.20454,
+             "inst_per_walker_step": 295.7, "issue_active": 0.710, "fmaheavy_active": 0.685},
 }
+
 
 
 
