@@ -319,9 +319,14 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             }
             EvalLanes<L> ev;
             eval_lanes<KIND, L, PARAM, kPoly>(t, xn, ev);
-            // a non-finite position is a non-finite kill, then a sign change a
-            // node kill, then a non-finite drift or local energy
-            const L xs = ladd(ladd(ladd(xn[0], xn[1]), ladd(xn[2], xn[3])), ladd(xn[4], xn[5]));
+            // A walker dies on a sign change of psi (or a psi of exactly 0) or
+            // on a non-finite drift or local energy.  An infinite or NaN
+            // coordinate needs no test of its own here: every evaluation forms
+            // its directions from x rsqrt(s), s the squared distance, which is
+            // NaN for such a coordinate, so the drift is NaN too.  The position
+            // decides only how a kill is counted (a non-finite position is a
+            // non-finite kill, then a sign change a node kill, then the rest),
+            // which the rare branch below works out once per dead walker.
             const L fs = eval_check_sum(ev);
             L el = ev.el;
             bool stay[LW];
@@ -329,18 +334,19 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             for (int j = 0; j < LW; ++j) {
                 const int k = g * LW + j;
                 const bool alive = sg[k] != 0;
-                const bool node = (ev.sign[j] != sg[k]) & finite_(lane_at(xs, j));
-                const bool fin = finite_(lane_at(fs, j));
-                stay[j] = alive && !node && fin;
+                const bool flip = ev.sign[j] != sg[k];
+                stay[j] = alive && !flip && finite_(lane_at(fs, j));
                 n_coal += (alive && lane_at(ev.rmin, j) < 1e-5f) ? 1u : 0u;
-                n_node += (alive && node) ? 1u : 0u;
-                n_nonfinite += (alive && !node && !fin) ? 1u : 0u;
-                if (alive && !stay[j] && valid[k]) {
-                    // killed by this move: it stays here (rare; stored now)
+                if (alive && !stay[j]) {
+                    // killed by this move: counted, and it stays here (stored now)
                     float xk[6];
 #pragma unroll
                     for (int d = 0; d < 6; ++d) xk[d] = lane_at(xn[d], j);
-                    store_mixed(st, slot[k], xk, -INFINITY, 0);
+                    const float xs = ladd(ladd(ladd(xk[0], xk[1]), ladd(xk[2], xk[3])),
+                                          ladd(xk[4], xk[5]));
+                    if (flip && finite_(xs)) ++n_node;
+                    else ++n_nonfinite;
+                    if (valid[k]) store_mixed(st, slot[k], xk, -INFINITY, 0);
                 }
                 sg[k] = stay[j] ? sg[k] : 0;
                 if (!stay[j]) set_lane(el, j, et);
