@@ -180,6 +180,14 @@ init_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 // CKPT: the gradient's forward.  It writes the position checkpoints
 // (StateMixed::ckpt) at its folds, or the whole trajectory (StateMixed::traj)
 // at every move, whichever of the two is set.
+// Offset (floats) in a warp's staging area of the float4 of lane 16 half +
+// lane15 for move m4 of a group of four.  The half-planes are padded so that
+// the column sums' reads, which take one quantity of one move and half of the
+// lanes per warp lane, fall in 32 distinct banks (8 m4 + 4 half + quantity).
+__device__ __forceinline__ int stage_offset(int m4, int half, int lane15) {
+    return m4 * kStageMove + half * kStageHalf + 4 * lane15;
+}
+
 template <int KIND, int WPT, int NOISE, bool PARAM, bool CKPT = false>
 __global__ void __launch_bounds__(WPT == 4 ? kMaxThreadsWpt4 : kMaxThreads)
 walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
@@ -195,8 +203,9 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     // dynamic shared memory (walk_smem_bytes):
     //   ring  [2][kRing][4][nwarps] float:  per-warp sums (W, P, Q, R), double-buffered
     //   cnt   [2][kRing][nwarps] unsigned:   per-warp alive counts
-    //   stage [nwarps][16][kStageStride] float: each lane's four sums of up to four moves
-    extern __shared__ float s_dyn[];
+    //   stage [nwarps][4][2][kStageHalf] float: each lane's four sums of up to four
+    //         moves, as one float4 per lane and move (stage_offset)
+    extern __shared__ __align__(16) float s_dyn[];
     const int blk = blockIdx.x + blk0;       // a launch may cover a range of blocks
     const int inst = block_instance(bm, blk);
     const InstDev& I = insts[inst];
@@ -227,7 +236,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     const int nwarps = T >> 5;
     float* const s_ring = s_dyn;
     unsigned* const s_cnt = reinterpret_cast<unsigned*>(s_dyn + 2 * kRing * 4 * nwarps);
-    float* const s_stage = s_dyn + 2 * kRing * 5 * nwarps + warp * 16 * kStageStride;
+    float* const s_stage = s_dyn + 2 * kRing * 5 * nwarps + warp * 4 * kStageMove;
 
     PhiloxPre pre[WPT];
     uint32_t lcg[WPT];           // Bernoulli mode: generator state before this move
@@ -329,6 +338,17 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             // which the rare branch below works out once per dead walker.
             const L fs = eval_check_sum(ev);
             L el = ev.el;
+            // the coalescence diagnostic: walkers alive before the move that
+            // land within 1e-5 bohr of a nucleus or of the other electron
+            // (rare: counted per lane only when some lane of the thread did)
+            float rm = lane_at(ev.rmin, 0);
+#pragma unroll
+            for (int j = 1; j < LW; ++j) rm = fminf(rm, lane_at(ev.rmin, j));
+            if (rm < 1e-5f) {
+#pragma unroll
+                for (int j = 0; j < LW; ++j)
+                    n_coal += (sg[g * LW + j] != 0 && lane_at(ev.rmin, j) < 1e-5f) ? 1u : 0u;
+            }
             bool stay[LW];
 #pragma unroll
             for (int j = 0; j < LW; ++j) {
@@ -336,7 +356,6 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                 const bool alive = sg[k] != 0;
                 const bool flip = ev.sign[j] != sg[k];
                 stay[j] = alive && !flip && finite_(lane_at(fs, j));
-                n_coal += (alive && lane_at(ev.rmin, j) < 1e-5f) ? 1u : 0u;
                 if (alive && !stay[j]) {
                     // killed by this move: counted, and it stays here (stored now)
                     float xk[6];
@@ -347,8 +366,8 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                     if (flip && finite_(xs)) ++n_node;
                     else ++n_nonfinite;
                     if (valid[k]) store_mixed(st, slot[k], xk, -INFINITY, 0);
+                    sg[k] = 0;
                 }
-                sg[k] = stay[j] ? sg[k] : 0;
                 if (!stay[j]) set_lane(el, j, et);
                 na += stay[j] ? 1u : 0u;
             }
@@ -390,10 +409,8 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         // window, the warp adds the columns up (half a column per lane, the
         // halves joined by one shuffle) and writes them to the ring
         const int m4 = s & 3;
-        s_stage[(m4 * 4 + 0) * kStageStride + lane_id] = qs[0];
-        s_stage[(m4 * 4 + 1) * kStageStride + lane_id] = qs[1];
-        s_stage[(m4 * 4 + 2) * kStageStride + lane_id] = qs[2];
-        s_stage[(m4 * 4 + 3) * kStageStride + lane_id] = qs[3];
+        *reinterpret_cast<float4*>(s_stage + stage_offset(m4, lane_id >> 4, lane_id & 15)) =
+            make_float4(qs[0], qs[1], qs[2], qs[3]);
         na = __reduce_add_sync(0xffffffffu, na);
         const int r = s % kRing;
         if (lane_id == 0) s_cnt[(buf * kRing + r) * nwarps + warp] = na;
@@ -410,14 +427,15 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             const bool staged = (col >> 2) <= m4;
             float v = 0.f;
             if (staged) {
-                const float* src = s_stage + col * kStageStride + 16 * half;
+                // quantity col & 3 of move col >> 2, lanes 16 half + u
+                const float* src = s_stage + stage_offset(col >> 2, half, 0) + (col & 3);
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
                 for (int u = 0; u < 16; u += 4) {
-                    a0 += src[u];
-                    a1 += src[u + 1];
-                    a2 += src[u + 2];
-                    a3 += src[u + 3];
+                    a0 += src[4 * u];
+                    a1 += src[4 * (u + 1)];
+                    a2 += src[4 * (u + 2)];
+                    a3 += src[4 * (u + 3)];
                 }
                 v = (a0 + a1) + (a2 + a3);
             }
@@ -568,7 +586,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 // Dynamic shared memory of the walk kernel for `threads` threads per block.
 static size_t walk_smem_bytes(int threads) {
     const size_t nwarps = (size_t)threads / 32;
-    return 4 * (2 * kRing * 5 * nwarps + nwarps * 16 * kStageStride);
+    return 4 * (2 * kRing * 5 * nwarps + nwarps * 4 * kStageMove);
 }
 
 // run = false only prepares the kernel (the shared-memory opt-in), so that it

@@ -102,9 +102,12 @@ constexpr int kMaxWarps = kMaxThreads / 32;
 // dependency chains per thread) is compiled for blocks of at most 128 threads,
 // which lets it hold its state in up to 255 registers per thread.
 constexpr int kMaxThreadsWpt4 = 128;
-// Row stride (floats) of the mixed walk's per-warp staging rows: 32 lanes plus
-// one, so that reading a column across the warp hits 32 distinct banks.
-constexpr int kStageStride = 33;
+// The mixed walk's per-warp staging area: for each of four moves, two
+// half-planes of 16 lanes x 4 sums (64 floats) padded to kStageHalf, so a move
+// takes kStageMove floats; both are multiples of 4 (16-byte float4 stores) and
+// kStageMove = 8 mod 32 (conflict-free column reads).
+constexpr int kStageHalf = 68;
+constexpr int kStageMove = 2 * kStageHalf;
 
 // Counters per instance: [0] non-finite kills, [1] node kills, [2] coalescences.
 constexpr int kNumCounters = 3;
