@@ -32,6 +32,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "gfk_device.cuh"
 #include "gfk_types.h"
 
@@ -136,11 +138,13 @@ __device__ __forceinline__ void adj_move(float x[6], const float b[6], const flo
         x[d] = bern ? move_bern_f32(x[d], b[d], xi[d], xlo[d], dt)
                     : move_gauss_f32(x[d], b[d], xi[d], dt, sdt);
 }
-__device__ __forceinline__ void adj_normals(const uint32_t w[6], double xi[6], const InstDev*) {
+__device__ __forceinline__ void adj_normals(const uint32_t w[6], double xi[6], const InstDev*,
+                                            const float2*) {
     normals6_f64(w, xi);
 }
-__device__ __forceinline__ void adj_normals(const uint32_t w[6], float xi[6], const InstDev* inst) {
-    normals6_f32(w, xi, inst->r2_fix);
+__device__ __forceinline__ void adj_normals(const uint32_t w[6], float xi[6], const InstDev* inst,
+                                            const float2* cs) {
+    normals6_f32(w, xi, inst->r2_fix, cs);
 }
 __device__ __forceinline__ void adj_bernoulli(uint32_t& s, double, const InstDev*, double xi[6],
                                               double*) {
@@ -168,7 +172,7 @@ __device__ __forceinline__ void adj_steps(const InstDev* inst, float& dt, float&
 template <int NOISE, int POLY, typename T>
 __device__ __forceinline__ void adj_recompute(const TrialDev<T>& tp, const InstDev* inst,
                                               int64_t ns, int64_t i, int n_lo, int n_hi, T dt,
-                                              T sdt, T x[6], T* seg) {
+                                              T sdt, T x[6], T* seg, const float2* cs) {
     SegIO<T>::store(seg, ns, i, x);
     const uint32_t id = inst->id0 + (uint32_t)i;
     uint32_t lcg = 0u;
@@ -182,7 +186,7 @@ __device__ __forceinline__ void adj_recompute(const TrialDev<T>& tp, const InstD
         } else {
             uint32_t words[1][6];
             move_words_all<1>(pre, (uint32_t)m, inst->k0, inst->k1, words);
-            adj_normals(words[0], xi, inst);
+            adj_normals(words[0], xi, inst, cs);
         }
         EvalOut<T> ev;
         eval_kind0<T, TrialDev<T>, POLY>(tp, x, ev);
@@ -484,7 +488,11 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
     // Per-thread FP64 parameter adjoints, updated once per segment from the
     // segment's sums in T (kept here rather than in registers).
     __shared__ double s_theta[kNumTheta][kAdjThreads];
+    // the FP32 recompute's Box-Muller angle table (the forward walk's)
+    __shared__ float2 s_cs[std::is_same<T, float>::value ? kAngleGrid : 1];
     if (threadIdx.x == 0) load_trial<T>(inst->trial, inst->ee_on, s_trial);
+    if (std::is_same<T, float>::value && inst->noise != GFK_NOISE_BERNOULLI)
+        for (int k = threadIdx.x; k < kAngleGrid; k += blockDim.x) s_cs[k] = inst->angle_cs[k];
     __syncthreads();
     const TrialDev<T>& tp = s_trial;
     T dt, sdt;
@@ -523,11 +531,11 @@ adj_backward_kernel(const InstDev* __restrict__ inst, int64_t n, int S, int K, i
                     T x[6];
                     PosIO<T>::load(ckpt + (int64_t)j * PosIO<T>::kWords * n, n, i, x);
                     if (bern) {
-                        if (poly) adj_recompute<1, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
-                        else adj_recompute<1, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                        if (poly) adj_recompute<1, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg, s_cs);
+                        else adj_recompute<1, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg, s_cs);
                     } else {
-                        if (poly) adj_recompute<0, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
-                        else adj_recompute<0, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg);
+                        if (poly) adj_recompute<0, 1, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg, s_cs);
+                        else adj_recompute<0, 0, T>(tp, inst, ns, i, n_lo, n_hi, dt, sdt, x, seg, s_cs);
                     }
                     pos = seg;
                     p0 = n_lo;

@@ -34,6 +34,7 @@ struct gfk_ctx {
     std::vector<int64_t> off;     // first slot per instance
     int64_t n_slots = 0;
     InstDev* d_inst = nullptr;
+    float2* d_angle_cs = nullptr;   // mixed path: the Box-Muller angle table
     // state
     StateF64 s64{};
     StateMixed smx{};
@@ -345,6 +346,7 @@ gfk_status upload_instances(gfk_ctx* ctx) {
         v.et_f32 = mc.et;
         v.dt_log2e = mc.dt_log2e;
         v.et_fix = mc.et_fix;
+        v.angle_cs = ctx->d_angle_cs;
         v.trial = ctx->trial[i];
     }
     GFK_CK(ctx, cudaMemcpyAsync(ctx->d_inst, h.data(), sizeof(InstDev) * ctx->n_inst,
@@ -527,6 +529,7 @@ gfk_status check_inst(gfk_ctx* ctx, int32_t inst) {
 
 void free_all(gfk_ctx* ctx) {
     dev_free(ctx->d_inst);
+    dev_free(ctx->d_angle_cs);
     dev_free(ctx->s64.x);
     dev_free(ctx->s64.logw);
     dev_free(ctx->smx.p0);
@@ -722,10 +725,15 @@ gfk_status gfk_create(const gfk_instance_desc* inst, int32_t n_inst, void* cuda_
         ALLOC(ctx->smx.p0, float4*, sizeof(float4) * ctx->n_slots);
         ALLOC(ctx->smx.p1, float4*, sizeof(float4) * ctx->n_slots);
         ALLOC(ctx->smx.sgn, int8_t*, ctx->n_slots);
+        ALLOC(ctx->d_angle_cs, float2*, sizeof(float2) * kAngleGrid);
     }
 #undef ALLOC
     e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * n_inst, ctx->stream);
     if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaMemsetAsync"); goto fail; }
+    if (ctx->d_angle_cs) {
+        e = fill_angle_table(ctx->d_angle_cs, ctx->stream);
+        if (e != cudaSuccess) { st = cuda_fail(ctx, e, "fill_angle_table"); goto fail; }
+    }
     *out = ctx;
     return GFK_OK;
 fail:

@@ -146,20 +146,22 @@ __device__ __forceinline__ void move_words_all(const PhiloxPre (&pre)[WPT], uint
 // singularity), so the normals' variance -- the diffusion constant -- would be
 // low by that fraction and E(t) high by about that fraction of the kinetic
 // energy.  u_a is at least 2^-33 > 0; values that round to 1 give radius 0
-// (the square root of 0 is 0).  The angle uniform is the grid point
-// u_b - 1/2 = ((1 + k 2^-10) - 3/2) + 2^-11 of the 10-bit index k, built
-// exactly from the bit pattern 0x3F800000 | (k << 13) (= 1 + k 2^-10); on the
-// equally spaced grid cos^2 and sin^2 average to 1/2 exactly.  The radius takes the
-// hardware log2 with its mean error over the 2^32 words removed (radius2_f32
-// below).  Then the hardware square root, sine and cosine; the angle is taken as
-// 2 pi (u_b - 1/2) in (-pi, pi), where the hardware sine and cosine are most
-// accurate, and the signs flipped back: cos(2 pi u) = -cos(2 pi (u - 1/2)).
+// (the square root of 0 is 0).  The angle is the grid point
+// 2 pi (u_b - 1/2), u_b = (k + 1/2)/1024, of the 10-bit index k; its cosine
+// and sine come from a table of their correctly rounded FP32 values
+// (angle_cs_entry), and the signs are flipped back:
+// cos(2 pi u) = -cos(2 pi (u - 1/2)).  On the equally spaced grid cos^2 and
+// sin^2 average to 1/2 exactly, and the FP32 values keep the grid's
+// symmetries (the quarter-turn maps the grid onto itself), so their mean
+// squares are equal.  The radius takes the hardware log2 with its mean error
+// over the 2^32 words removed (radius2_f32 below), then the hardware square
+// root.
 // The squared Box-Muller radius -2 ln u_a of the FP32 path from its word w,
 // u_a = fl(fl(w) 2^-32 + 2^-33).  The logarithm is the hardware base-2 one
 // (a single MUFU operation) scaled by -2 ln 2, plus r2_fix.  The walk sees the
 // radius only through the normals' variance, and r2_fix (set per instance on
 // the host, gfk_mixed_consts.h) cancels the mean errors of this logarithm, of
-// the hardware square root and of the hardware cosine and sine, measured
+// the hardware square root and of the angle table's rounding, measured
 // exhaustively over all radius words and angles, and matches the variance to
 // the drift's FP32 time step.
 // The lane forms (one walker, or two in float2 lanes: the same rounded
@@ -191,54 +193,50 @@ __device__ __forceinline__ float radius_f32(float r2) {
     return rho;
 }
 
-// The angle 2 pi (u_b - 1/2) from the grid value 1 + k 2^-10 of its 10-bit
-// index k (the bit pattern 0x3F800000 | (k << 13)); then the hardware sine and
-// cosine.
-__device__ __forceinline__ float angle_grid(uint32_t k) {
-    return __int_as_float(0x3F800000 | (k << 13));
-}
-template <typename L>
-__device__ __forceinline__ L angle_lanes(L grid) {
-    constexpr float kHalfCell = 1.0f / 2048.0f;                           // 2^-11
-    constexpr float kTwoPi = 6.2831853071795865f;
-    return lmul(splat<L>(kTwoPi), ladd(lsub(grid, splat<L>(1.5f)), splat<L>(kHalfCell)));
-}
-__device__ __forceinline__ void angle_f32(uint32_t k, float& s, float& c) {
-    __sincosf(angle_lanes<float>(angle_grid(k)), &s, &c);
+// The angle of grid point k, theta_k = 2 pi ((k + 1/2)/1024 - 1/2) =
+// pi ((2k + 1)/1024 - 1), as the pair (cos theta_k, sin theta_k) rounded to
+// FP32.  The argument of sincospi is exact in FP64 (a dyadic rational), and
+// the FP64 library values round to the correctly rounded FP32 values for all
+// but ties closer than the FP64 error, so the FP32 angle carries no error of
+// its own beyond the final rounding.  The walk kernels gather these pairs from
+// a 1024-entry table (filled once per context by fill_angle_table)
+// instead of evaluating the hardware sine and cosine per normal.
+__device__ __forceinline__ float2 angle_cs_entry(uint32_t k) {
+    double s, c;
+    sincospi((double)(2u * k + 1u) * (1.0 / (double)kAngleGrid) - 1.0, &s, &c);
+    return make_float2((float)c, (float)s);
 }
 
 // Six N(0,1) variates per walker from its six words (block_words: Box-Muller
 // on (w0,k0), (w2,k1), (w4,k2)) for the walkers of a lane group (w[k]: lane
-// k's words).
+// k's words); cs is the angle table (kAngleGrid pairs, shared memory in the
+// kernels).
 template <typename L>
-__device__ __forceinline__ void normals6_lanes(const uint32_t (*w)[6], L xi[6], float r2_fix) {
+__device__ __forceinline__ void normals6_lanes(const uint32_t (*w)[6], L xi[6], float r2_fix,
+                                               const float2* __restrict__ cs) {
     constexpr int W = LaneCount<L>::value;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        L wf, grid;
+        L wf;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            set_lane(wf, k, (float)w[k][2 * j]);
-            set_lane(grid, k, angle_grid(w[k][2 * j + 1]));
-        }
+        for (int k = 0; k < W; ++k) set_lane(wf, k, (float)w[k][2 * j]);
         const L r2 = radius2_lanes<L>(wf, r2_fix);
-        const L ang = angle_lanes<L>(grid);
-        L rho, sn, cs;
+        L rho, sn, cn;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            float sv, cv;
-            __sincosf(lane_at(ang, k), &sv, &cv);
+            const float2 t = cs[w[k][2 * j + 1]];
             set_lane(rho, k, radius_f32(lane_at(r2, k)));
-            set_lane(sn, k, sv);
-            set_lane(cs, k, cv);
+            set_lane(cn, k, t.x);
+            set_lane(sn, k, t.y);
         }
         const L nrho = lneg(rho);
-        xi[2 * j] = lmul(nrho, cs);
+        xi[2 * j] = lmul(nrho, cn);
         xi[2 * j + 1] = lmul(nrho, sn);
     }
 }
-__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6], float r2_fix) {
-    normals6_lanes<float>(reinterpret_cast<const uint32_t(*)[6]>(w), xi, r2_fix);
+__device__ __forceinline__ void normals6_f32(const uint32_t w[6], float xi[6], float r2_fix,
+                                             const float2* __restrict__ cs) {
+    normals6_lanes<float>(reinterpret_cast<const uint32_t(*)[6]>(w), xi, r2_fix, cs);
 }
 
 // ---------------------------------------------------------------------------

@@ -15,6 +15,9 @@ cudaError_t launch_init_fp64(int kind, int threads, int nblk, const InstDev* ins
 cudaError_t launch_walk_fp64(int kind, int noise, int threads, int nblk, const InstDev* insts,
                              const BlockMap& bm, const StateF64& st, uint32_t step0, int nsteps,
                              PartialRec* part, unsigned long long* counters, cudaStream_t stream);
+// The Box-Muller angle table of the mixed path (kAngleGrid float2 pairs of
+// cos, sin; see angle_cs_entry), written on `stream`.
+cudaError_t fill_angle_table(float2* cs, cudaStream_t stream);
 cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
                               const BlockMap& bm, const StateMixed& st, PartialRec* part,
                               unsigned long long* counters, cudaStream_t stream);

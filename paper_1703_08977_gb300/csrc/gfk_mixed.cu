@@ -16,6 +16,16 @@ extern template void launch_walk_mixed_n<1>(int kind, int wpt, int threads, int 
                                             const TrialHost* one_trial, int ee_on,
                                             cudaStream_t stream, bool run);
 
+__global__ void fill_angle_table_kernel(float2* __restrict__ cs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < kAngleGrid) cs[k] = angle_cs_entry((uint32_t)k);
+}
+
+cudaError_t fill_angle_table(float2* cs, cudaStream_t stream) {
+    fill_angle_table_kernel<<<kAngleGrid / 256, 256, 0, stream>>>(cs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_mixed(int kind, int threads, int nblk, const InstDev* insts,
                               const BlockMap& bm, const StateMixed& st, PartialRec* part,
                               unsigned long long* counters, cudaStream_t stream) {

@@ -205,11 +205,18 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     //   cnt   [2][kRing][nwarps] unsigned:   per-warp alive counts
     //   stage [nwarps][4][2][kStageHalf] float: each lane's four sums of up to four
     //         moves, as one float4 per lane and move (stage_offset)
+    //   angle [kAngleGrid] float2: Gaussian noise: the Box-Muller angle table
     extern __shared__ __align__(16) float s_dyn[];
     const int blk = blockIdx.x + blk0;       // a launch may cover a range of blocks
     const int inst = block_instance(bm, blk);
     const InstDev& I = insts[inst];
     if (!PARAM && threadIdx.x == 0) load_trial<float>(I.trial, I.ee_on, s_trial);
+    float2* const s_cs = reinterpret_cast<float2*>(
+        s_dyn + (2 * kRing * 5 + 4 * kStageMove) * (blockDim.x >> 5));
+    if (NOISE == 0) {
+        const float2* __restrict__ src = I.angle_cs;
+        for (int i = threadIdx.x; i < kAngleGrid; i += blockDim.x) s_cs[i] = src[i];
+    }
     __syncthreads();
     TrialDev<float> t_local;
     if (!PARAM && KIND == 0) t_local = s_trial;
@@ -548,8 +555,8 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             L xa[NG][6], xb[NG][6], xlo[NG][6];
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                normals6_lanes<L>(&wa[g * LW], xa[g], r2_fix);
-                normals6_lanes<L>(&wb[g * LW], xb[g], r2_fix);
+                normals6_lanes<L>(&wa[g * LW], xa[g], r2_fix, s_cs);
+                normals6_lanes<L>(&wb[g * LW], xb[g], r2_fix, s_cs);
             }
             advance(s, xa, xlo);
             advance(s + 1, xb, xlo);
@@ -565,7 +572,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             uint32_t words[WPT][6];
             move_words_all<WPT>(pre, step, k0, k1, words);
 #pragma unroll
-            for (int g = 0; g < NG; ++g) normals6_lanes<L>(&words[g * LW], xi[g], r2_fix);
+            for (int g = 0; g < NG; ++g) normals6_lanes<L>(&words[g * LW], xi[g], r2_fix, s_cs);
         }
         advance(s, xi, xlo);
         after(s);
@@ -584,19 +591,20 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 }
 
 // Dynamic shared memory of the walk kernel for `threads` threads per block.
-static size_t walk_smem_bytes(int threads) {
+static size_t walk_smem_bytes(int threads, int noise) {
     const size_t nwarps = (size_t)threads / 32;
-    return 4 * (2 * kRing * 5 * nwarps + nwarps * 4 * kStageMove);
+    return 4 * (2 * kRing * 5 * nwarps + nwarps * 4 * kStageMove) +
+           (noise == 0 ? sizeof(float2) * kAngleGrid : 0);
 }
 
 // run = false only prepares the kernel (the shared-memory opt-in), so that it
 // can happen before a stream capture rather than inside it.
-template <typename K>
+template <int NOISE, typename K>
 static void launch_walk(K kernel, int nblk, int blk0, int grid, int threads, cudaStream_t stream,
                         const InstDev* insts, const BlockMap& bm, const StateMixed& st,
                         uint32_t step0, int nsteps, PartialRec* part,
                         unsigned long long* counters, const TrialDev<float>& tk, bool run) {
-    const size_t smem = walk_smem_bytes(threads);
+    const size_t smem = walk_smem_bytes(threads, NOISE);
     if (smem > 48 * 1024)       // above the default limit (512-thread blocks): opt in
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (run)
@@ -612,15 +620,15 @@ static void launch_walk_mixed_k(int wpt, int threads, int nblk, int blk0, int gr
                                 const TrialDev<float>& tk, cudaStream_t stream, bool run) {
     switch (wpt) {
         case 1:
-            launch_walk(walk_mixed_kernel<KIND, 1, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
+            launch_walk<NOISE>(walk_mixed_kernel<KIND, 1, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
                         insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
         case 2:
-            launch_walk(walk_mixed_kernel<KIND, 2, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
+            launch_walk<NOISE>(walk_mixed_kernel<KIND, 2, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
                         insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
         default:
-            launch_walk(walk_mixed_kernel<KIND, 4, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
+            launch_walk<NOISE>(walk_mixed_kernel<KIND, 4, NOISE, PARAM, CKPT>, nblk, blk0, grid, threads, stream,
                         insts, bm, st, step0, nsteps, part, counters, tk, run);
             break;
     }

@@ -13,12 +13,15 @@
 //   Var = (2 + e_r2 + e_sqrt) (1/2 + e_angle)
 // where e_r2 is the mean error of the squared radius r2 over the 2^32 radius
 // words, e_sqrt the mean change of r2 by the hardware square root, and
-// e_angle the mean error of cos^2 (and sin^2) over the 1024-point angle grid.
-// All three were measured exhaustively on sm_103a (gfk_normal_moments
-// re-measures them):
+// e_angle the mean error of cos^2 (and sin^2) over the 1024-point angle grid,
+// whose FP32 values come from a table (angle_cs_entry).  The first two were
+// measured exhaustively on sm_103a (gfk_normal_moments re-measures them):
 //   the hardware log2 scaled by -2 ln 2 has mean error  -1.630718e-7,
-//   the square root changes the mean of r2 by           -4.860740e-8,
-//   cos^2 and sin^2 average 1/2 + (-6.248252e-8, -6.546174e-8).
+//   the square root changes the mean of r2 by           -4.860740e-8;
+// the table holds the correctly rounded FP32 cosines and sines of the grid
+// angles, whose squares average 1/2 - 2.798833e-9 (cos^2 and sin^2 alike: the
+// quarter turn maps the grid onto itself), computed from the correctly
+// rounded values and re-measured from the table by gfk_normal_moments.
 // The additive constant of the r2 multiply-add (r2_fix) is set so that
 // dt_f32 = fl(dt) and Var * sdt_f32^2 = dt_f32 exactly (to first order in the
 // small terms): the noise then diffuses by exactly the drift's time step.
@@ -43,7 +46,7 @@ namespace gfk {
 
 constexpr double kLog2MeanError = -1.630718e-7;   // mean of -2 ln2 lg2.approx(u) + 2 ln u
 constexpr double kSqrtMeanShift = -4.860740e-8;   // mean of sqrt.approx(r2)^2 - r2
-constexpr double kAngleMeanError = -6.397213e-8;  // mean of (cos^2 + sin^2)/2 - 1/2
+constexpr double kAngleMeanError = -2.798833e-9;  // mean of cos^2 - 1/2 (= of sin^2 - 1/2), table
 
 struct MixedConsts {
     float dt, sdt, r2_fix;

@@ -40,10 +40,12 @@ using namespace gfk;
 
 namespace {
 
-// The scratch.  Layout: [0, 4096) the InstDev record; [4096, end) PartialRec
-// records of one chunk, [move][block].
-constexpr size_t kHeaderBytes = 4096;
-static_assert(sizeof(InstDev) <= kHeaderBytes, "instance record must fit the header");
+// The scratch.  Layout: [0, 4096) the InstDev record; [4096, 12288) the
+// Box-Muller angle table (kAngleGrid float2); [12288, end) PartialRec records
+// of one chunk, [move][block].
+constexpr size_t kInstBytes = 4096;
+constexpr size_t kHeaderBytes = kInstBytes + sizeof(float2) * kAngleGrid;
+static_assert(sizeof(InstDev) <= kInstBytes, "instance record must fit the header");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GFK_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kThreads = 256;   // launch shape of this entry point
@@ -133,6 +135,7 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     inst.dt_log2e = mc.dt_log2e;
     inst.et_fix = mc.et_fix;
     inst.trial = trial;
+    inst.angle_cs = (const float2*)(scratch + kInstBytes);
     InstDev* d_inst = (InstDev*)scratch;
     PartialRec* part = (PartialRec*)(scratch + kHeaderBytes);
 
@@ -175,6 +178,8 @@ extern "C" gfk_status gfk_propagate_noalloc(const gfk_instance_desc* desc, int32
     } while (0)
     put_instance_kernel<<<1, 1, 0, stream>>>(inst, d_inst);
     NA_CK(cudaGetLastError());
+    if (d.noise == GFK_NOISE_GAUSSIAN)
+        NA_CK(fill_angle_table((float2*)(scratch + kInstBytes), stream));
     if (init) {
         NA_CK(cudaMemsetAsync(dev_counters, 0, sizeof(unsigned long long) * kNumCounters, stream));
         NA_CK(launch_init_mixed(kind, kThreads, nblk, d_inst, bm, sm, part, dev_counters, stream));

@@ -191,8 +191,8 @@ __global__ void normal_moments_kernel(int method, float r2_fix, double* __restri
     }
     double c2 = 0.0, s2 = 0.0, c1 = 0.0, s1 = 0.0;
     for (uint64_t k = first; k < 1024u; k += stride) {
-        float s, c;
-        gfk::angle_f32((uint32_t)k, s, c);
+        const float2 cs = gfk::angle_cs_entry((uint32_t)k);   // the walk's angle table entry
+        const float c = cs.x, s = cs.y;
         c2 += (double)c * (double)c - 0.5;
         s2 += (double)s * (double)s - 0.5;
         c1 += (double)c;

@@ -4,6 +4,8 @@
 
 #include <cstdint>
 
+#include <vector_types.h>
+
 #include "gfk.h"   // include/ is on the include path
 #include "gfk_debug.h"
 
@@ -40,6 +42,7 @@ struct InstDev {
     float et_f32;       //   E_T in FP32,
     float dt_log2e;     //   dt log2(e) in FP32,
     double et_fix;      //   and et_f32 - E_T in FP64
+    const float2* angle_cs;   // mixed path, Gaussian noise: the Box-Muller angle table
     TrialHost trial;
 };
 
@@ -108,6 +111,10 @@ constexpr int kMaxThreadsWpt4 = 128;
 // kStageMove = 8 mod 32 (conflict-free column reads).
 constexpr int kStageHalf = 68;
 constexpr int kStageMove = 2 * kStageHalf;
+
+// Points of the Box-Muller angle grid (the 10-bit angle fields of a move's
+// Philox block), and so entries of the mixed path's angle table.
+constexpr int kAngleGrid = 1024;
 
 // Counters per instance: [0] non-finite kills, [1] node kills, [2] coalescences.
 constexpr int kNumCounters = 3;

@@ -100,3 +100,22 @@ def test_energy_and_weight_constants(consts):
         assert et == float(np.float32(-2.9037))
         assert etfix == et - (-2.9037)
         assert dtl == float(np.float32(dt * 1.4426950408889634))
+
+
+def test_angle_constant_is_the_mean_over_the_rounded_table(consts):
+    """kAngleMeanError is the mean of c^2 - 1/2 over the walk's angle table: the
+    correctly rounded FP32 cosines of the grid angles pi ((2k + 1)/1024 - 1),
+    k = 0..1023 (computed here in 120-bit arithmetic).  The sines give the same
+    mean, and the cosines and sines both sum to exactly 0."""
+    mpmath = pytest.importorskip("mpmath")
+    _, (_, _, e_angle) = consts
+    mpmath.mp.prec = 120
+    ang = [mpmath.mpf(2 * k + 1) / 1024 - 1 for k in range(1024)]
+    c = [float(np.float32(float(mpmath.cospi(a)))) for a in ang]
+    s = [float(np.float32(float(mpmath.sinpi(a)))) for a in ang]
+    # x * x of an FP32 value is exact in FP64; fsum adds exactly
+    mc = (math.fsum(x * x for x in c) - 512.0) / 1024.0
+    ms = (math.fsum(x * x for x in s) - 512.0) / 1024.0
+    assert mc == ms
+    assert math.fsum(c) == 0.0 and math.fsum(s) == 0.0
+    assert abs(mc - e_angle) < 1e-15, (mc, e_angle)
