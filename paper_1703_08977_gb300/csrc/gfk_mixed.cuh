@@ -291,9 +291,14 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         if (sg[k] != 0) lmaxw = fmax(lmaxw, Lw[k]);
     double c = warp_max(lmaxw);
     c = isfinite(c) ? floor(c) : 0.0;      // integer-valued shift
+    // a dead walker's shift is -inf, so its weight 2^(-inf) is exactly 0
+    // (its Kahan sum stays finite: its local energy is replaced by E_T)
+    unsigned na_t = 0;             // the thread's walkers alive
 #pragma unroll
-    for (int k = 0; k < WPT; ++k)
-        set_lane(dsh[k / LW], k % LW, sg[k] != 0 ? (float)(Lw[k] - c) * kLog2e : 0.f);
+    for (int k = 0; k < WPT; ++k) {
+        set_lane(dsh[k / LW], k % LW, sg[k] != 0 ? (float)(Lw[k] - c) * kLog2e : -INFINITY);
+        na_t += sg[k] != 0 ? 1u : 0u;
+    }
     int fold_len = 0;
     int buf = 0;
 
@@ -301,7 +306,6 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     // Bernoulli steps' sub-ulp parts xlo), then its sums to the warp's staging
     // rows and the alive count to the ring.
     auto advance = [&](int s, L (&xi)[NG][6], L (&xlo)[NG][6]) {
-        unsigned na = 0;
         L q[4];
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
@@ -374,9 +378,10 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
                     else ++n_nonfinite;
                     if (valid[k]) store_mixed(st, slot[k], xk, -INFINITY, 0);
                     sg[k] = 0;
+                    set_lane(dsh[g], j, -INFINITY);
+                    --na_t;
                 }
                 if (!stay[j]) set_lane(el, j, et);
-                na += stay[j] ? 1u : 0u;
             }
 #pragma unroll
             for (int d = 0; d < 6; ++d) {
@@ -388,10 +393,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             const L tsum = ladd(S[g], y);
             comp[g] = lsub(lsub(tsum, S[g]), y);
             S[g] = tsum;
-            L w = lex2(lfma(lneg(S[g]), dtl2eL, dsh[g]));
-#pragma unroll
-            for (int j = 0; j < LW; ++j)
-                if (!stay[j]) set_lane(w, j, 0.f);
+            const L w = lex2(lfma(lneg(S[g]), dtl2eL, dsh[g]));   // 0 for the dead
             const L we = lmul(w, el);
             const L ww = lmul(w, w);
             const L wee = lmul(we, el);
@@ -418,7 +420,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
         const int m4 = s & 3;
         *reinterpret_cast<float4*>(s_stage + stage_offset(m4, lane_id >> 4, lane_id & 15)) =
             make_float4(qs[0], qs[1], qs[2], qs[3]);
-        na = __reduce_add_sync(0xffffffffu, na);
+        const unsigned na = __reduce_add_sync(0xffffffffu, na_t);
         const int r = s % kRing;
         if (lane_id == 0) s_cnt[(buf * kRing + r) * nwarps + warp] = na;
         ++fold_len;
@@ -475,7 +477,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             c = isfinite(c) ? floor(c) : 0.0;
 #pragma unroll
             for (int k = 0; k < WPT; ++k)
-                set_lane(dsh[k / LW], k % LW, sg[k] != 0 ? (float)(Lw[k] - c) * kLog2e : 0.f);
+                set_lane(dsh[k / LW], k % LW, sg[k] != 0 ? (float)(Lw[k] - c) * kLog2e : -INFINITY);
             // position checkpoint (StateMixed::ckpt) after move s, in the
             // gradient's forward kernels (CKPT) when it is set.  Walkers that are
             // dead by then keep moving and write meaningless positions, which the
