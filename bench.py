@@ -100,14 +100,14 @@ LANES_PER_SM_CLK = 128
 # instructions per walker-step, the issue-active fraction and the busiest pipe (the
 # FMA-heavy pipe, which also runs the integer multiplies of the Philox rounds).
 WALK_PROFILE = {       # (state, noise) -> capture of that walk kernel
-    (0, 0): {"src_sha": "a201b2c1efc7a8e1", "bytes_per_walker_step": 0.20044,
-             "inst_per_walker_step": 222.0, "issue_active": 0.712, "fmaheavy_active": 0.702},
-    (0, 1): {"src_sha": "a201b2c1efc7a8e1", "bytes_per_walker_step": 0.20000,
-             "inst_per_walker_step": 155.2, "issue_active": 0.742, "fmaheavy_active": 0.694},
-    (1, 0): {"src_sha": "a201b2c1efc7a8e1", "bytes_per_walker_step": 0.19982,
-             "inst_per_walker_step": 260.7, "issue_active": 0.718, "fmaheavy_active": 0.680},
-    (2, 0): {"src_sha": "a201b2c1efc7a8e1", "bytes_per_walker_step": 0.20454,
-             "inst_per_walker_step": 295.7, "issue_active": 0.710, "fmaheavy_active": 0.685},
+    (0, 0): {"src_sha": "3a49e7f284cc792c", "bytes_per_walker_step": 0.19946,
+             "inst_per_walker_step": 189.1, "issue_active": 0.695, "fmaheavy_active": 0.694},
+    (0, 1): {"src_sha": "3a49e7f284cc792c", "bytes_per_walker_step": 0.19918,
+             "inst_per_walker_step": 132.2, "issue_active": 0.696, "fmaheavy_active": 0.656},
+    (1, 0): {"src_sha": "3a49e7f284cc792c", "bytes_per_walker_step": 0.19992,
+             "inst_per_walker_step": 227.2, "issue_active": 0.695, "fmaheavy_active": 0.690},
+    (2, 0): {"src_sha": "3a49e7f284cc792c", "bytes_per_walker_step": 0.20754,
+             "inst_per_walker_step": 258.7, "issue_active": 0.692, "fmaheavy_active": 0.706},
 }
 
 
