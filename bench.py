@@ -96,17 +96,18 @@ LANES_PER_SM_CLK = 128
 # 1024 moves, 128 threads x 2 walkers; one capture per (state, noise) kernel:
 # `bench.py --profile-case --profile-walkers 1048576 --profile-moves 1024
 # --profile-state S --noise N`), valid only for the kernel sources they were taken
-# on (sha256 prefix of WALK_SOURCES): DRAM bytes (read + write) and executed thread
+# on (sha256 prefix of WALK_SOURCES' code, comments and layout aside: _src_sha):
+# DRAM bytes (read + write) and executed thread
 # instructions per walker-step, the issue-active fraction and the busiest pipe (the
 # FMA-heavy pipe, which also runs the integer multiplies of the Philox rounds).
 WALK_PROFILE = {       # (state, noise) -> capture of that walk kernel
-    (0, 0): {"src_sha": "3a49e7f284cc792c", "bytes_per_walker_step": 0.19946,
+    (0, 0): {"src_sha": "7d123826b4cbae54", "bytes_per_walker_step": 0.19946,
              "inst_per_walker_step": 189.1, "issue_active": 0.695, "fmaheavy_active": 0.694},
-    (0, 1): {"src_sha": "3a49e7f284cc792c", "bytes_per_walker_step": 0.19918,
+    (0, 1): {"src_sha": "7d123826b4cbae54", "bytes_per_walker_step": 0.19918,
              "inst_per_walker_step": 132.2, "issue_active": 0.696, "fmaheavy_active": 0.656},
-    (1, 0): {"src_sha": "3a49e7f284cc792c", "bytes_per_walker_step": 0.19992,
+    (1, 0): {"src_sha": "7d123826b4cbae54", "bytes_per_walker_step": 0.19992,
              "inst_per_walker_step": 227.2, "issue_active": 0.695, "fmaheavy_active": 0.690},
-    (2, 0): {"src_sha": "3a49e7f284cc792c", "bytes_per_walker_step": 0.20754,
+    (2, 0): {"src_sha": "7d123826b4cbae54", "bytes_per_walker_step": 0.20754,
              "inst_per_walker_step": 258.7, "issue_active": 0.692, "fmaheavy_active": 0.706},
 }
 
@@ -114,17 +115,43 @@ WALK_PROFILE = {       # (state, noise) -> capture of that walk kernel
 
 
 # Sources the mixed walk kernel is compiled from (the kernels and the device
-# code they include); a captured figure holds only while they are unchanged.
+# code they include); a captured figure holds only while their code is
+# unchanged (comments and layout aside).
 WALK_SOURCES = tuple("paper_1703_08977_gb300/csrc/" + f for f in (
     "gfk_mixed.cuh", "gfk_mixed.cu", "gfk_mixed_bern.cu", "gfk_device.cuh", "gfk_block.cuh",
     "gfk_types.h", "gfk_lanes.cuh", "gfk_eval_f32.cuh", "gfk_debug.h"))
 
 
+def _code_tokens(text: str) -> str:
+    """C++ source without its comments, each run of whitespace one space (string and
+    character literals, such as inline PTX, kept as written)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def _src_sha() -> str:
     h = hashlib.sha256()
     for f in WALK_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(_code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -252,7 +252,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
     double Lw[WPT];              // FP64 log-weight base
     int sg[WPT];
     L x[NG][6], b[NG][6];
-    L S[NG], comp[NG], dsh[NG];  // dsh: (L - c) log2(e), formed at each fold
+    L S[NG], comp[NG], dsh[NG];  // dsh: (L - c) log2(e), formed at each fold (-inf: dead)
 #pragma unroll
     for (int k = 0; k < WPT; ++k) {
         const int64_t id = (int64_t)(blk - bm.begin[inst]) * T * WPT + (int64_t)k * T + threadIdx.x;
@@ -413,10 +413,11 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             for (int j = 1; j < LW; ++j) v = v + lane_at(q[u], j);
             qs[u] = v;
         }
-        // the lane's four sums go to the warp's staging rows (column = move of
-        // the group x 4 + quantity); every fourth move, and at the end of a
-        // window, the warp adds the columns up (half a column per lane, the
-        // halves joined by one shuffle) and writes them to the ring
+        // the lane's four sums go to the warp's staging area as one float4
+        // (stage_offset: move of the group of four, half-warp, lane); every
+        // fourth move, and at the end of a window, the warp adds each quantity
+        // of each move over the lanes (half of the lanes per warp lane, the
+        // halves joined by one shuffle) and writes the sums to the ring
         const int m4 = s & 3;
         *reinterpret_cast<float4*>(s_stage + stage_offset(m4, lane_id >> 4, lane_id & 15)) =
             make_float4(qs[0], qs[1], qs[2], qs[3]);
@@ -451,7 +452,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
             v += __shfl_xor_sync(0xffffffffu, v, 16);
             if (half == 0 && staged)
                 s_ring[((buf * kRing + r - m4 + (col >> 2)) * 4 + (col & 3)) * nwarps + warp] = v;
-            __syncwarp();                        // the staging rows are rewritten next move
+            __syncwarp();                        // the staging area is rewritten next move
         }
         if (r == kRing - 1 || s == nsteps - 1) {
             if (lane_id == 0) s_shift[buf][warp] = c;

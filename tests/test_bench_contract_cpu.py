@@ -32,3 +32,19 @@ def test_warmup_below_three_is_refused():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
                         "--warmup", "2"], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode != 0
+
+
+def test_walk_profile_key_ignores_comments_only():
+    """The key of the captured walk-kernel figures (bench._src_sha) hashes the
+    sources' code: comments and layout do not change it, code and string
+    literals (inline PTX) do."""
+    sys.path.insert(0, ROOT)
+    import bench
+    base = 'asm("add.rn.f32 %0, %1, %2;" : "=f"(r));  // one add\nint x = 1; /* c */\n'
+    same = '/* a note */ asm("add.rn.f32 %0, %1, %2;"   :  "=f"(r));\n\nint x = 1;\n'
+    code = 'asm("add.rn.f32 %0, %1, %2;" : "=f"(r));\nint x = 2;\n'
+    ptx = 'asm("sub.rn.f32 %0, %1, %2;" : "=f"(r));\nint x = 1;\n'
+    t = bench._code_tokens
+    assert t(base) == t(same)
+    assert t(base) != t(code) and t(base) != t(ptx)
+    assert t('char c = \'/\'; // x\n') == "char c = '/';"
