@@ -2,7 +2,7 @@
 
 - The mixed-precision path's energy on the same walkers and noise as the FP64
   path differs from it by less than 1.5e-8 hartree, for both noise modes and
-  several time steps (measured within 5.3e-9 on larger samples).
+  several time steps (measured within 5.2e-9 on larger samples).
 - The GFK energy of the nodeless 1^1S state and of the 2^3S state (whose node
   r1 = r2 is exact) extrapolated to dt -> 0 reproduces the exact variational
   energies printed in the paper's summary table (-2.9037243770 and
