@@ -304,7 +304,7 @@ walk_mixed_kernel(const InstDev* __restrict__ insts, BlockMap bm, StateMixed st,
 
     // One move of every walker of the thread from its increments xi (and the
     // Bernoulli steps' sub-ulp parts xlo), then its sums to the warp's staging
-    // rows and the alive count to the ring.
+    // area and the warp's alive count to the ring.
     auto advance = [&](int s, L (&xi)[NG][6], L (&xlo)[NG][6]) {
         L q[4];
 #pragma unroll
