@@ -101,14 +101,14 @@ LANES_PER_SM_CLK = 128
 # instructions per walker-step, the issue-active fraction and the busiest pipe (the
 # FMA-heavy pipe, which also runs the integer multiplies of the Philox rounds).
 WALK_PROFILE = {       # (state, noise) -> capture of that walk kernel
-    (0, 0): {"src_sha": "7d123826b4cbae54", "bytes_per_walker_step": 0.19946,
+    (0, 0): {"src_sha": "8c28c12f7806baf6", "bytes_per_walker_step": 0.19932,
              "inst_per_walker_step": 189.1, "issue_active": 0.695, "fmaheavy_active": 0.694},
-    (0, 1): {"src_sha": "7d123826b4cbae54", "bytes_per_walker_step": 0.19918,
+    (0, 1): {"src_sha": "8c28c12f7806baf6", "bytes_per_walker_step": 0.19865,
              "inst_per_walker_step": 132.2, "issue_active": 0.696, "fmaheavy_active": 0.656},
-    (1, 0): {"src_sha": "7d123826b4cbae54", "bytes_per_walker_step": 0.19992,
+    (1, 0): {"src_sha": "8c28c12f7806baf6", "bytes_per_walker_step": 0.19963,
              "inst_per_walker_step": 227.2, "issue_active": 0.695, "fmaheavy_active": 0.690},
-    (2, 0): {"src_sha": "7d123826b4cbae54", "bytes_per_walker_step": 0.20754,
-             "inst_per_walker_step": 258.7, "issue_active": 0.692, "fmaheavy_active": 0.706},
+    (2, 0): {"src_sha": "8c28c12f7806baf6", "bytes_per_walker_step": 0.19973,
+             "inst_per_walker_step": 252.5, "issue_active": 0.681, "fmaheavy_active": 0.717},
 }
 
 

@@ -196,10 +196,11 @@ __device__ __forceinline__ void kind1_term_lanes(const TrialDev<float>& t, int k
 //   b_1 = grad_1 Phi / Phi + u' e12,  b_2 = grad_2 Phi / Phi - u' e12
 //   E_L = T / Phi - u' (grad_1 Phi - grad_2 Phi) . e12 / Phi - u'' - u'^2
 //         + (ee - 2u')/r12,   T = sum_t s_t [K_A p_B + p_A K_B] g_A g_B.
-// UNROLL: the term loops run to GFK_MAX_TERMS with a uniform early exit (every
-// parameter index a compile-time constant, for a trial held in the kernel's
-// parameter bank); otherwise they run to t.nterms.
-template <typename L, bool UNROLL, bool PLAIN, int POLY>
+// UNROLL: the term loops run to NT (at most GFK_MAX_TERMS) with a uniform
+// early exit (every parameter index a compile-time constant, for a trial held
+// in the kernel's parameter bank); otherwise they run to t.nterms.  A trial of
+// NT terms gets the same operations from any NT >= its term count.
+template <typename L, bool UNROLL, bool PLAIN, int POLY, int NT = GFK_MAX_TERMS>
 __device__ __forceinline__ void eval1_lanes(const TrialDev<float>& t, const L x[6],
                                             EvalLanes<L>& o) {
     L s1, s2, s12, d[3];
@@ -219,18 +220,18 @@ __device__ __forceinline__ void eval1_lanes(const TrialDev<float>& t, const L x[
     for (int d = 0; d < 3; ++d) acc.G1[d] = acc.G2[d] = splat<L>(0.0f);
     if constexpr (UNROLL) {
         // every term's exponent once, then the largest of them
-        L arg[GFK_MAX_TERMS];
+        L arg[NT];
         arg[0] = term_exponent(t, 0, r1, r2);
         L emax = arg[0];
 #pragma unroll
-        for (int k = 1; k < GFK_MAX_TERMS; ++k) {
+        for (int k = 1; k < NT; ++k) {
             if (k >= t.nterms) break;
             arg[k] = term_exponent(t, k, r1, r2);
             emax = lmax(emax, arg[k]);
         }
         kind1_term_lanes<L, PLAIN>(t, 0, arg[0], r1, r2, ir, zz, h1, h2, emax, acc);
 #pragma unroll
-        for (int k = 1; k < GFK_MAX_TERMS; ++k) {
+        for (int k = 1; k < NT; ++k) {
             if (k >= t.nterms) break;
             kind1_term_lanes<L, PLAIN>(t, k, arg[k], r1, r2, ir, zz, h1, h2, emax, acc);
         }
@@ -266,6 +267,8 @@ __device__ __forceinline__ void eval1_lanes(const TrialDev<float>& t, const L x[
 }
 
 // KIND 0 / 1 / 3 as for eval_trial (3: orbital pairs without prefactor terms);
+// KIND 4 is KIND 1 for a two-term trial in the kernel's parameter bank (the
+// term loops fixed at two: the same operations, fewer live registers);
 // KIND 2 dispatches on t.kind.  POLY < 0 decides on the Jastrow polynomial at
 // run time (one branch at the top).  An orbital-pair function whose orbitals
 // all lack the prefactor terms (t.plain) is evaluated in the PLAIN form by
@@ -287,6 +290,8 @@ __device__ __forceinline__ void eval_lanes(const TrialDev<float>& t, const L x[6
             eval1_lanes<L, UNROLL, true, POLY>(t, x, o);
         } else if (KIND == 1 && UNROLL) {
             eval1_lanes<L, true, false, POLY>(t, x, o);
+        } else if (KIND == 4) {
+            eval1_lanes<L, true, false, POLY, 2>(t, x, o);
         } else if (KIND == 2 && t.kind == 0) {
             eval0_lanes<L, TrialDev<float>, POLY>(t, x, o);
         } else if (t.plain != 0) {

@@ -661,9 +661,16 @@ void launch_walk_mixed_n(int kind, int wpt, int threads, int nblk, int blk0, int
     if (one_trial && kind == 0 && NOISE == 0)
         launch_walk_mixed_k<0, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                             part, counters, tk, stream, run);
-    else if (one_trial && kind == 1)
-        launch_walk_mixed_k<1, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
-                                            part, counters, tk, stream, run);
+    else if (one_trial && kind == 1) {
+        // a two-term trial (the P_z pair) takes the kernel whose term loops are
+        // fixed at two; preparing (run = false) readies both kernels
+        if (one_trial->nterms == 2 || !run)
+            launch_walk_mixed_k<4, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0,
+                                                nsteps, part, counters, tk, stream, run);
+        if (one_trial->nterms != 2 || !run)
+            launch_walk_mixed_k<1, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0,
+                                                nsteps, part, counters, tk, stream, run);
+    }
     else if (one_trial && kind == 3)
         launch_walk_mixed_k<3, NOISE, true>(wpt, threads, nblk, blk0, grid, insts, bm, st, step0, nsteps,
                                             part, counters, tk, stream, run);
